@@ -1,0 +1,420 @@
+"""Pins for the CPU oracle (no GPU).
+
+Every check here fixes the oracle against something other than itself: a
+brute-force count, a second counting method, a closed form, an invariant, a
+fact the paper states (``tests/golden/``) or a hand-worked case.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.conftest import read_golden
+
+SEED = synth.SEED_BASE
+
+
+def brute_hist(x):
+    """Count each bin by comparing every pixel with it (O(256 n))."""
+    return [sum(1 for xi in x if xi == b) for b in range(256)]
+
+
+# ------------------------------------------------------------ histogram ----
+
+@pytest.mark.parametrize("n", [0, 1, 2, 15, 16, 17, 31, 64])
+def test_hist_brute_force_tiny(n):
+    rng = np.random.default_rng(n + 7)
+    for trial in range(5):
+        x = rng.integers(0, 256, n, dtype=np.uint8)
+        assert oracle.hist(x).tolist() == brute_hist(x.tolist())
+
+
+def test_hist_brute_force_skewed_tiny():
+    x = np.array([0, 255, 255, 3, 3, 3, 128, 0, 255], np.uint8)
+    assert oracle.hist(x).tolist() == brute_hist(x.tolist())
+
+
+def test_hist_matches_bincount_and_sort_count():
+    x = synth.host(1 << 20, synth.normal(128, 8), SEED + 1)
+    h = oracle.hist(x)
+    assert np.array_equal(h, np.bincount(x, minlength=256).astype(np.uint64))
+    vals, counts = np.unique(np.sort(x), return_counts=True)
+    ref = np.zeros(256, np.uint64)
+    ref[vals] = counts
+    assert np.array_equal(h, ref)
+
+
+def test_hist_table2_closed_forms():
+    for name, n, rule in read_golden("table2_inputs.txt"):
+        n = int(n)
+        if rule.startswith("const:"):
+            v = int(rule.split(":")[1])
+            x = np.full(n, v, np.uint8)
+            h = oracle.hist(x)
+            assert int(h[v]) == n
+            assert int(h.sum()) == n and np.count_nonzero(h) == 1
+        elif rule == "ramp":
+            x = synth.host_ramp(n)
+            h = oracle.hist(x)
+            assert (h == n // 256).all()
+        elif rule == "sum":
+            x = synth.host(n, synth.uniform(), SEED, threads=8)
+            h = oracle.hist(x)
+            assert int(h.sum()) == n
+        else:
+            raise AssertionError(rule)
+
+
+def test_hist_ramp_with_ragged_tail():
+    n = 256 * 5 + 17
+    h = oracle.hist(synth.host_ramp(n, counter0=3))
+    # values 3..(3+n-1) mod 256: 5 full turns plus 17 values starting at 3
+    expect = np.full(256, 5, np.uint64)
+    expect[3:20] += 1
+    assert np.array_equal(h, expect)
+
+
+def test_hist_empty():
+    assert not oracle.hist(np.zeros(0, np.uint8)).any()
+    assert not oracle.hist_u32(np.zeros(0, np.uint8)).any()
+
+
+def test_hist_sum_is_n_and_chunks_add_up():
+    x = synth.host(3 * 65536 + 11, synth.mixture([0.3, 0.7], [60, 180], [5, 20]), SEED + 4)
+    h = oracle.hist(x)
+    assert int(h.sum()) == x.size
+    rng = np.random.default_rng(3)
+    cuts = np.sort(rng.integers(0, x.size, 6))
+    parts = np.split(x, cuts)
+    acc = np.zeros(256, np.uint64)
+    for p in parts:
+        acc += oracle.hist(p)
+    assert np.array_equal(acc, h)
+
+
+def test_hist_u32_rejects_n_at_2_pow_32():
+    import ctypes
+
+    h = np.zeros(256, np.uint32)
+    # the size check happens before any pixel is read, so a null pointer is safe
+    rc = oracle.lib().oracle_hist_u32(None, ctypes.c_size_t(1 << 32), h.ctypes.data)
+    assert rc == -1 and not h.any()
+
+
+def test_hist_unaligned_views():
+    base = synth.host(4096 + 32, synth.uniform(), SEED + 9)
+    for off in range(16):
+        x = base[off:off + 4096 - off]
+        assert np.array_equal(oracle.hist(x), np.bincount(x, minlength=256).astype(np.uint64))
+
+
+# ----------------------------------------------------------- degeneracy ----
+
+def _h(pixels):
+    h = np.zeros(256, np.uint64)
+    for p in pixels:
+        h[p] += 1
+    return h
+
+
+@pytest.mark.parametrize(
+    "pixels,expect",
+    [
+        # hand-computed: max bin share of Sec. III.C
+        ([5, 5, 5, 7], (5, 3, 4)),
+        ([], (0, 0, 0)),
+        ([9], (9, 1, 1)),
+        ([3, 3, 7, 7], (3, 2, 4)),  # tie: lowest bin index
+        ([200, 7, 7, 200, 200], (200, 3, 5)),
+        ([0, 255, 255], (255, 2, 3)),
+    ],
+)
+def test_degeneracy_hand_cases(pixels, expect):
+    assert oracle.degeneracy(_h(pixels)) == expect
+
+
+def test_switch_threshold_band_from_paper():
+    rows = {r[0]: int(r[1]) for r in read_golden("switch_threshold.txt")}
+    assert rows["theta_low_milli"] <= oracle.THETA_MILLI_DEFAULT <= rows["theta_high_milli"]
+
+
+def _hist_with_max(mx, total):
+    """A histogram with max bin count mx (at bin 17) and the given total."""
+    h = np.zeros(256, np.uint64)
+    h[17] = mx
+    rest = total - mx
+    others = [b for b in range(256) if b != 17]
+    i = 0
+    while rest > 0:
+        b = others[i % 255]
+        if h[b] < mx:
+            h[b] += 1
+            rest -= 1
+        i += 1
+        assert i < 1_000_000
+    return h
+
+
+@pytest.mark.parametrize(
+    "mx,total,theta,flag",
+    [
+        (45, 100, 450, 1),  # exactly at the threshold: >= switches
+        (44, 100, 450, 0),
+        (46, 100, 450, 1),
+        (1, 2, 500, 1),
+        (499, 1000, 500, 0),
+        (500, 1000, 500, 1),
+        (0, 0, 450, 0),  # empty histogram never switches
+        (10, 10, 1000, 1),
+        (9, 10, 1000, 0),
+        (4, 1000, 0, 1),  # theta 0: any non-empty histogram
+    ],
+)
+def test_switch_boundary(mx, total, theta, flag):
+    h = _hist_with_max(mx, total)
+    _, m, t = oracle.degeneracy(h)
+    assert m == mx and t == total
+    assert oracle.switch(h, theta) == flag
+
+
+def test_switch_large_counts_exact():
+    # products beyond 2^64: max * 1000 and total * theta must be compared exactly
+    h = np.zeros(256, np.uint64)
+    h[0] = np.uint64(9_000_000_000_000_000_000)
+    h[1] = np.uint64(9_000_000_000_000_000_000)
+    # share exactly 1/2
+    assert oracle.switch(h, 500) == 1
+    assert oracle.switch(h, 501) == 0
+
+
+@pytest.mark.parametrize("d", [0.0, 0.3, 0.6, 0.95, 1.0])
+def test_degeneracy_of_paper_mixture(d):
+    # Sec. III.C mixture: a share d of the pixels equals one value, the rest is
+    # uniform.  Expected degeneracy d + (1 - d)/256, within binomial error.
+    n = 1 << 18
+    x = synth.host(n, synth.degenerate(90, d), SEED + 3)
+    arg, m, t = oracle.degeneracy(oracle.hist(x))
+    assert t == n
+    p = d + (1 - d) / 256
+    if d >= 0.3:
+        assert arg == 90
+        sd = np.sqrt(p * (1 - p) / n)
+        assert abs(m / n - p) <= 6 * sd + 1e-12
+    else:
+        assert m / n < 0.01
+    expect_flag = 1 if p >= 0.45 else 0
+    assert oracle.switch(oracle.hist(x)) == expect_flag
+
+
+# -------------------------------------------------------------- patterns ----
+
+def _check_pattern_invariants(p, budget):
+    k = p.k
+    assert ((k >= 1) & (k <= 32)).all()
+    assert (k & (k - 1) == 0).all()  # powers of two
+    assert p.used == int(k.sum()) <= budget
+    assert p.budget == budget
+    # sub-bin ranges are disjoint, inside [0, used), each aligned to its size
+    occ = np.zeros(p.used, np.int32)
+    for b in range(256):
+        o = int(p.off[b])
+        assert o % int(k[b]) == 0
+        occ[o:o + int(k[b])] += 1
+    assert (occ == 1).all()
+
+
+def test_default_pattern_paper_facts():
+    facts = {r[0]: int(r[1]) for r in read_golden("default_pattern.txt")}
+    p = oracle.default_pattern(facts["table_length"])
+    assert p.used == facts["table_length"]
+    assert len(p.off) == facts["bins"]
+    assert int(p.k.max()) == facts["k_max"]
+    assert int(p.k[127]) == facts["k_at_127"]
+    assert int(p.k[0]) == facts["k_at_first_bin"] and int(p.k[1]) == facts["k_at_first_bin"]
+    _check_pattern_invariants(p, 960)
+
+
+def test_default_pattern_regions_and_scaling():
+    p = oracle.default_pattern(960)
+    assert p.k.tolist() == [k for k in (1, 2, 4, 8, 8, 4, 2, 1) for _ in range(32)]
+    # scale 8 at the full table, capped at 32 sub-bins per bin
+    p8 = oracle.default_pattern(8192)
+    assert p8.k.tolist() == [k for k in (8, 16, 32, 32, 32, 32, 16, 8) for _ in range(32)]
+    assert p8.used == 32 * (8 + 16 + 32 * 4 + 16 + 8) == 5632
+    # scale 2 for budgets in [1920, 3840)
+    assert oracle.default_pattern(1920).used == 1920
+    assert oracle.default_pattern(3839).used == 1920
+    # below 960: one sub-bin per bin
+    p1 = oracle.default_pattern(959)
+    assert (p1.k == 1).all() and p1.used == 256
+    for b in (256, 300, 959, 960, 1000, 2048, 4096, 8192):
+        _check_pattern_invariants(oracle.default_pattern(b), b)
+    with pytest.raises(ValueError):
+        oracle.default_pattern(255)
+    with pytest.raises(ValueError):
+        oracle.default_pattern(8193)
+
+
+def test_layout_order_and_alignment():
+    lk = np.zeros(256, np.uint8)
+    lk[10] = 3  # k = 8
+    lk[4] = 5  # k = 32
+    lk[200] = 5
+    lk[5] = 1  # k = 2
+    off, used = oracle.pattern_layout(lk)
+    # 32-groups first in bin order, then 8, then 2, then the k=1 bins in bin order
+    assert off[4] == 0 and off[200] == 32 and off[10] == 64 and off[5] == 72
+    ones = [b for b in range(256) if lk[b] == 0]
+    assert [int(off[b]) for b in ones] == list(range(74, 74 + 252))
+    assert used == 32 + 32 + 8 + 2 + 252
+
+
+def test_binning_pattern_uniform_histogram():
+    h = np.full(256, 1000, np.uint32)
+    # want = 1 + floor(7936 * 1000 / 256000) = 32 -> every bin 32, the full table
+    p = oracle.binning_pattern(h, 8192)
+    assert (p.k == 32).all() and p.used == 8192
+    assert np.array_equal(p.off, np.arange(256, dtype=np.uint16) * 32)
+    # budget 960: want = 1 + floor(704/256) = 3 -> 2; floor f=2 fits (512), f=4 does not (1024)
+    p = oracle.binning_pattern(h, 960)
+    assert (p.k == 2).all() and p.used == 512
+    assert np.array_equal(p.off, np.arange(256, dtype=np.uint16) * 2)
+
+
+def test_binning_pattern_constant_histogram():
+    h = np.zeros(256, np.uint32)
+    h[90] = 12345
+    # budget 960: bin 90 wants 1 + 704 -> 32; the others want 1.
+    # floor 2: 32 + 255*2 = 542 fits; floor 4: 32 + 1020 = 1052 does not.
+    p = oracle.binning_pattern(h, 960)
+    assert int(p.k[90]) == 32
+    assert int((p.k == 2).sum()) == 255 and p.used == 542
+    assert int(p.off[90]) == 0
+    _check_pattern_invariants(p, 960)
+    # budget 256: no spare at all, every bin gets one sub-bin
+    p = oracle.binning_pattern(h, 256)
+    assert (p.k == 1).all() and p.used == 256
+
+
+def test_binning_pattern_hand_worked_power_of_two_edges():
+    # budget 496 -> spare 240; with total 240 the proportional want is 1 + h[b]
+    h = np.zeros(256, np.uint32)
+    h[0], h[1], h[2], h[3], h[4], h[5], h[7] = 14, 15, 30, 31, 100, 1, 49
+    assert int(h.sum()) == 240
+    p = oracle.binning_pattern(h, 496)
+    # want: 15 -> 8, 16 -> 16, 31 -> 16, 32 -> 32, 101 -> 32 (cap), 2 -> 2, 50 -> 32, 1 -> 1
+    # proportional total: 8+16+16+32+32+2+32 + 249*1 = 387; floor 2 would add
+    # 248 more (the 249 ones become 2, bin 5 stays 2): 635 > 496, so f = 1.
+    expect = np.ones(256, np.uint32)
+    expect[[0, 1, 2, 3, 4, 5, 7]] = [8, 16, 16, 32, 32, 2, 32]
+    assert np.array_equal(p.k, expect)
+    assert p.used == 387
+    # offsets: 32s (bins 3, 4, 7), then 16s (1, 2), then 8 (0), then 2 (5), then ones
+    assert [int(p.off[b]) for b in (3, 4, 7, 1, 2, 0, 5)] == [0, 32, 64, 96, 112, 128, 136]
+    assert int(p.off[6]) == 138 and int(p.off[8]) == 139 and int(p.off[255]) == 138 + 248
+
+
+def test_binning_pattern_floor_raise_hand_worked():
+    # budget 1024, spare 768, one hot bin: h[128] = 768, h[b] = 1 for 0..255 except 128 (255 ones)
+    h = np.ones(256, np.uint32)
+    h[128] = 768
+    total = 768 + 255
+    want_hot = 1 + (768 * 768) // total  # 577 -> 32
+    want_one = 1 + 768 // total  # 1
+    assert want_hot == 577 and want_one == 1
+    p = oracle.binning_pattern(h, 1024)
+    # floor 2: 32 + 510 = 542; floor 4: 32 + 1020 = 1052 > 1024 -> f = 2
+    assert int(p.k[128]) == 32 and int((p.k == 2).sum()) == 255 and p.used == 542
+
+
+def test_binning_pattern_empty_is_default():
+    for b in (256, 960, 8192):
+        assert oracle.binning_pattern(np.zeros(256, np.uint32), b) == oracle.default_pattern(b)
+
+
+def test_binning_pattern_full_budget_is_full_table():
+    # at the largest budget the floor always reaches 32: the lane-private table
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        h = rng.integers(0, 1 << 20, 256).astype(np.uint32)
+        h[rng.integers(0, 256, 100)] = 0
+        p = oracle.binning_pattern(h, 8192)
+        assert (p.k == 32).all() and p.used == 8192
+
+
+@pytest.mark.parametrize("budget", [256, 257, 511, 960, 1500, 2048, 4095, 4096, 6000, 8191, 8192])
+def test_binning_pattern_invariants_random(budget):
+    rng = np.random.default_rng(budget)
+    for trial in range(30):
+        kind = trial % 3
+        if kind == 0:
+            h = rng.integers(0, 1000, 256)
+        elif kind == 1:
+            x = synth.host(1 << 14, synth.normal(rng.uniform(20, 235), rng.uniform(2, 40)), SEED + trial)
+            h = np.bincount(x, minlength=256)
+        else:
+            h = np.zeros(256, np.int64)
+            h[rng.integers(0, 256, 3)] = rng.integers(1, 1 << 30, 3)
+        h = h.astype(np.uint32)
+        p = oracle.binning_pattern(h, budget)
+        _check_pattern_invariants(p, budget)
+        # monotone: a bin with a larger count never gets fewer sub-bins
+        k = p.k.astype(np.int64)
+        order = np.argsort(h, kind="stable")
+        assert (np.diff(k[order]) >= 0).all()
+
+
+def test_binning_pattern_rejects_budget():
+    for h in (np.zeros(256, np.uint32), np.arange(256, dtype=np.uint32)):
+        for budget in (0, 100, 255, 8193, 9000):
+            with pytest.raises(ValueError):
+                oracle.binning_pattern(h, budget)
+
+
+def test_pattern_bytes_layout():
+    p = oracle.default_pattern(960)
+    b = p.to_bytes()
+    assert len(b) == 776
+    assert int.from_bytes(b[2 * 127:2 * 128], "little") == int(p.off[127])
+    assert b[512 + 127] == 3  # log2(8)
+    assert int.from_bytes(b[768:772], "little") == 960
+    assert int.from_bytes(b[772:776], "little") == 960
+
+
+# ---------------------------------------------------------------- stream ----
+
+def test_stream_oracle_totals_and_first_chunk():
+    st = oracle.StreamOracle(budget=960)
+    whole = []
+    for c in range(5):
+        x = synth.host(5000 + 333 * c, synth.uniform(), SEED + 2, counter0=10_000 * c)
+        whole.append(x)
+        rec = st.push(x)
+        if c == 0:
+            assert rec.kernel == oracle.FLAG_PLAIN
+            assert rec.pattern == oracle.default_pattern(960)
+    assert np.array_equal(st.totals, oracle.hist(np.concatenate(whole)))
+    assert st.chunks == 5
+
+
+def test_stream_oracle_switches_one_chunk_after_each_phase():
+    # degenerate phases (95 % = 90) alternate with uniform phases every 4 chunks;
+    # the kernel follows the previous chunk's degeneracy (Sec. III.C)
+    st = oracle.StreamOracle(budget=8192)
+    kernels = []
+    for c in range(16):
+        thr = synth.degenerate(90, 0.95) if (c // 4) % 2 == 0 else synth.uniform()
+        x = synth.host(1 << 14, thr, SEED + 3, counter0=c << 14)
+        kernels.append(st.push(x).kernel)
+    expect = [0] + [1] * 4 + [0] * 4 + [1] * 4 + [0] * 3
+    assert kernels == expect
+
+
+def test_stream_oracle_forced_modes_refresh_pattern():
+    st = oracle.StreamOracle(budget=960, mode=oracle.MODE_ADAPTIVE)
+    x0 = synth.host(1 << 12, synth.degenerate(7, 1.0), SEED, 0)
+    r0 = st.push(x0)
+    r1 = st.push(synth.host(1 << 12, synth.uniform(), SEED, 1 << 12))
+    assert r0.kernel == r1.kernel == oracle.FLAG_ADAPTIVE
+    assert r1.pattern == oracle.binning_pattern(oracle.hist_u32(x0), 960)
+    assert int(r1.pattern.k[7]) == 32
