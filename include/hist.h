@@ -1,0 +1,216 @@
+/*
+ * hist.h -- C ABI of the GB300 (sm_103a) library for exact 256-bin histograms
+ * of 8-bit pixel streams, after "Fast Histograms using Adaptive CUDA Streams"
+ * (Koppaka, Mudigere, Narasimhan, Narayanan; arXiv 1011.0235).
+ *
+ * The paper has three parts (Sec. III, Sec. IV):
+ *   - a plain per-warp kernel (the NVIDIA SDK kernel it compares against,
+ *     "NVHist") and an adaptive kernel ("AHist") that splits bins into
+ *     sub-bins following a binning pattern (Sec. III.A);
+ *   - a chunked stream that refreshes the binning pattern from the stream's
+ *     own past histograms (Sec. III.B);
+ *   - switching between the two kernels by the degeneracy of the last
+ *     histogram (Sec. III.C).
+ * Here all three run on the device: the pattern and the switch for chunk i+1
+ * are computed by the kernels from chunk i's histogram, with no host round
+ * trip.
+ *
+ * Conventions for every call below.
+ *   - Pointers named d_* are device pointers (cudaMalloc, or any memory the
+ *     device can address); h_* are host pointers.  The caller owns every
+ *     buffer it passes; the library keeps no pointer past the call except
+ *     where a call says so (stream and server objects).
+ *   - `s` is a cudaStream_t.  Calls are asynchronous on `s` unless their name
+ *     or comment says they synchronize.  Results are valid once `s` has
+ *     reached the point of the call.
+ *   - Return value: HIST_OK (0) or a negative HIST_E* code.  On an error
+ *     nothing has been enqueued and no output has been written, except
+ *     HIST_ECUDA, which reports a CUDA error raised while enqueuing
+ *     (hist_last_cuda_error() returns it).
+ *   - Histograms are uint32_t[256] (one chunk: n < 2^32 pixels) or
+ *     uint64_t[256] (stream totals).  Bin b counts the pixels equal to b.
+ *   - Input pointers may have any alignment and n may be any size (0
+ *     included).
+ */
+#ifndef HIST_H
+#define HIST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hist_cuda_stream; /* the same type as cudaStream_t */
+
+/* ---------------------------------------------------------------- codes -- */
+#define HIST_OK 0
+#define HIST_EINVAL (-1)    /* bad argument (null pointer, size, budget, mode ...) */
+#define HIST_ENOMEM (-2)    /* a device or host allocation failed */
+#define HIST_EBUDGET (-3)   /* admission: a request exceeds the server's byte budget */
+#define HIST_ETIMEDOUT (-4) /* a bounded device or host wait ran out */
+#define HIST_ECUDA (-5)     /* a CUDA call failed; see hist_last_cuda_error() */
+#define HIST_EBUSY (-6)     /* no free slot right now; retry after a poll */
+#define HIST_ESTATE (-7)    /* object in the wrong state for this call */
+
+#define HIST_BINS 256
+#define HIST_KMAX 32          /* sub-bins per bin: at most one per warp lane */
+#define HIST_BUDGET_MIN 256   /* sub-bin table slots: one per bin ... */
+#define HIST_BUDGET_MAX 8192  /* ... up to 32 per bin (a 32 KiB table) */
+#define HIST_THETA_MILLI_DEFAULT 450 /* Sec. III.C: critical degeneracy 40-50 % */
+
+#define HIST_FLAG_PLAIN 0u    /* the per-warp kernel (NVHist) */
+#define HIST_FLAG_ADAPTIVE 1u /* the sub-binned kernel (AHist) */
+
+const char* hist_strerror(int code);
+/* The cudaError_t behind the last HIST_ECUDA returned on this thread. */
+int hist_last_cuda_error(void);
+/* Number of SMs the library sizes its grids for on the current device. */
+int hist_device_sms(void);
+
+/* ------------------------------------------------------ binning pattern -- */
+/* Binning pattern (Sec. III.A, Figure 1): the sub-histogram table of the
+ * adaptive kernel holds `used` slots; bin b owns the k_b = 2^log2k[b] slots
+ * off[b] .. off[b]+k_b-1, and a pixel of value b read by warp lane l is
+ * counted in slot off[b] + (l mod k_b) (sub-bins allotted to the lanes of a
+ * warp cyclically, Sec. III.A).  The histogram is the per-bin sum of its
+ * slots, so any valid pattern gives the exact histogram; the pattern only
+ * changes speed.  Valid: log2k[b] <= 5, off[b] a multiple of k_b, the ranges
+ * disjoint, used = sum k_b <= budget <= HIST_BUDGET_MAX.  776 bytes. */
+typedef struct hist_pattern {
+  uint16_t off[HIST_BINS];
+  uint8_t log2k[HIST_BINS];
+  uint32_t budget;
+  uint32_t used;
+} hist_pattern;
+
+/* Host check of a host-resident pattern: HIST_OK or HIST_EINVAL. */
+int hist_pattern_check(const hist_pattern* h_pat);
+
+/* Device-side binning pattern from the previous histogram (Sec. III.B: the
+ * sub-histogram indices are recomputed from the stream's past histograms; the
+ * paper gives no formula, so the rule is this library's reading):
+ *   T = sum h.  T = 0 gives default_pattern(budget).
+ *   want_b = 1 + floor((budget - 256) * h_b / T)
+ *   k0_b   = min(32, largest power of two <= want_b)
+ *   f      = largest power of two <= 32 with sum_b max(f, k0_b) <= budget
+ *   k_b    = max(f, k0_b)
+ *   offsets: bins in order of decreasing k_b, ties by increasing b, packed
+ *   from slot 0 (so off[b] is a multiple of k_b).
+ * d_prev_hist: uint32_t[256] on the device.  d_pat: written.
+ * budget outside [HIST_BUDGET_MIN, HIST_BUDGET_MAX] -> HIST_EINVAL. */
+int binning_pattern(const uint32_t* d_prev_hist, uint32_t budget, hist_pattern* d_pat,
+                    hist_cuda_stream s);
+
+/* Default pattern for a stream's first chunk: the reading of Figure 1 as
+ * eight regions of 32 bins with 1,2,4,8,8,4,2,1 sub-bins (960 slots, Sec.
+ * III.A: 960 entries, 8 sub-bins at 127, 1 at the first bins), scaled by the
+ * largest power of two s with 960 s <= budget (at most 32 per bin), or one
+ * sub-bin per bin when budget < 960.  Written to d_pat on the device. */
+int default_pattern(uint32_t budget, hist_pattern* d_pat, hist_cuda_stream s);
+
+/* ------------------------------------------------------------ degeneracy -- */
+/* Sec. III.C: degeneracy of a histogram = its largest bin over its total.
+ * flag = HIST_FLAG_ADAPTIVE iff total > 0 and max * 1000 >= theta_milli *
+ * total (exact integer compare), else HIST_FLAG_PLAIN.  maxbin is the lowest
+ * bin holding the maximum (0 for an empty histogram). */
+typedef struct hist_degeneracy_result {
+  uint64_t max;
+  uint64_t total;
+  uint32_t maxbin;
+  uint32_t flag;
+} hist_degeneracy_result;
+
+/* d_hist: uint32_t[256] / uint64_t[256] on the device; d_res written on the
+ * device.  theta_milli > 1000 -> HIST_EINVAL. */
+int degeneracy(const uint32_t* d_hist, uint32_t theta_milli, hist_degeneracy_result* d_res,
+               hist_cuda_stream s);
+int degeneracy_u64(const uint64_t* d_hist, uint32_t theta_milli, hist_degeneracy_result* d_res,
+                   hist_cuda_stream s);
+
+/* --------------------------------------------------------- one-shot kernels -- */
+/* Plain per-warp kernel (NVHist, Sec. I and Table 2: one sub-histogram of 256
+ * bins per warp in shared memory, merged per bin).  d_out: uint32_t[256],
+ * overwritten.  n >= 2^32 -> HIST_EINVAL.  d_in may be null only if n == 0. */
+int hist_plain(const uint8_t* d_in, size_t n, uint32_t* d_out, hist_cuda_stream s);
+
+/* Adaptive kernel (AHist, Sec. III.A) with the device-resident pattern d_pat.
+ * Same contract as hist_plain.  The pattern must be valid (as written by
+ * binning_pattern / default_pattern, or checked with hist_pattern_check);
+ * the kernel never addresses memory outside its own table whatever d_pat
+ * holds, but an invalid pattern gives an unspecified histogram. */
+int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t* d_out,
+                  hist_cuda_stream s);
+
+/* ------------------------------------------------------------- stream -- */
+/* Chunked stream (Sec. III.B) with kernel switching (Sec. III.C).  The
+ * stream keeps its state on the device: the running totals (the paper's
+ * "Accumulator"), the last chunk's histogram, the pattern and the kernel the
+ * next chunk will use.  Chunk i+1 uses the pattern and the switch computed
+ * from chunk i's histogram (a moving window of one chunk).  The first chunk
+ * runs the plain kernel with default_pattern(budget). */
+#define HIST_MODE_AUTO 0u     /* kernel chosen by the degeneracy switch */
+#define HIST_MODE_PLAIN 1u    /* always the plain kernel (pattern still refreshed) */
+#define HIST_MODE_ADAPTIVE 2u /* always the adaptive kernel */
+
+typedef struct hist_config {
+  uint32_t budget;      /* sub-bin table slots, HIST_BUDGET_MIN..MAX (default MAX) */
+  uint32_t theta_milli; /* critical degeneracy per mille, 0..1000 (default 450) */
+  uint32_t mode;        /* HIST_MODE_* (default AUTO) */
+  uint32_t grid;        /* CTAs per chunk launch; 0 = one per SM */
+  uint32_t reserved[4]; /* zero */
+} hist_config;
+
+void hist_config_init(hist_config* cfg);
+
+typedef struct hist_stream hist_stream;
+
+/* Allocates the stream's device state (about 56 KiB, cudaMalloc on the
+ * current device) and initialises it; synchronous (the device is
+ * synchronized), so call it outside stream capture. */
+int hist_stream_create(const hist_config* cfg, hist_stream** out);
+/* Waits for the stream's work, frees its device state. */
+int hist_stream_destroy(hist_stream* st);
+
+/* Push one chunk (d_chunk, n pixels, n < 2^32).  d_chunk_out: optional
+ * uint32_t[256] that receives the chunk's histogram, or null.  The chunk's
+ * results (d_chunk_out, the totals, the next pattern and switch) are
+ * completed by the next push on the stream or by hist_stream_flush, both in
+ * order on `s`: the epilogue of chunk i runs at the head of chunk i+1's
+ * kernel.  The caller keeps d_chunk and d_chunk_out alive until then.
+ * Consecutive calls on one stream object must use the same `s`. */
+int hist_stream_push(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t* d_chunk_out,
+                     hist_cuda_stream s);
+/* Push `count` chunks in order; d_chunk_outs may be null (no per-chunk
+ * outputs) or hold null entries. */
+int hist_stream_push_many(hist_stream* st, uint32_t count, const uint8_t* const* d_chunks,
+                          const size_t* sizes, uint32_t* const* d_chunk_outs, hist_cuda_stream s);
+/* Complete the last pushed chunk's epilogue (no-op if none is pending). */
+int hist_stream_flush(hist_stream* st, hist_cuda_stream s);
+/* Flush, then copy the running totals (uint64_t[256]) to d_totals. */
+int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s);
+
+/* Stream state, for inspection and for checkpoint / resume. */
+typedef struct hist_stream_state {
+  uint64_t totals[HIST_BINS];   /* sum of all chunk histograms */
+  uint32_t last_hist[HIST_BINS];/* histogram of the last chunk */
+  hist_pattern pattern;         /* pattern the next chunk will be given */
+  hist_pattern last_pattern;    /* pattern the last chunk was given */
+  uint64_t chunks;              /* chunks completed */
+  uint32_t flag;                /* switch from the last chunk (next kernel in AUTO) */
+  uint32_t last_kernel;         /* kernel the last chunk ran */
+  uint32_t status;              /* 0, or a device-side error code */
+  uint32_t reserved[7];
+} hist_stream_state;
+
+/* Flush, copy the state to the host and synchronize `s`. */
+int hist_stream_get_state(hist_stream* st, hist_stream_state* h_state, hist_cuda_stream s);
+/* Replace the stream's state (resume from a checkpoint); synchronizes `s`.
+ * HIST_EINVAL if the state's patterns are invalid for this stream's budget. */
+int hist_stream_set_state(hist_stream* st, const hist_stream_state* h_state, hist_cuda_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,203 @@
+"""GB300 (sm_103a) exact 256-bin histograms of 8-bit pixel streams.
+
+Python binding of the C ABI in ``include/hist.h`` ("Fast Histograms using
+Adaptive CUDA Streams": per-warp and adaptive sub-binned kernels, the binning
+pattern, the degeneracy switch and the chunked stream, all on the device).
+
+Tensors are ``torch`` CUDA tensors; the work is enqueued on the current torch
+stream.  PyTorch only provides device memory and streams: every step runs in
+``libhist.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import (  # noqa: F401
+    BINS, BUDGET_MAX, BUDGET_MIN, FLAG_ADAPTIVE, FLAG_PLAIN, KMAX, MODE_ADAPTIVE, MODE_AUTO,
+    MODE_PLAIN, THETA_MILLI_DEFAULT, HistError, HistPattern, StreamState,
+)
+
+PATTERN_BYTES = ctypes.sizeof(HistPattern)  # 776
+
+
+def lib() -> ctypes.CDLL:
+    return _abi.load()
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream] = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev_u8(x: torch.Tensor) -> torch.Tensor:
+    if not x.is_cuda or x.dtype != torch.uint8:
+        raise TypeError("pixels must be a uint8 CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("pixels must be contiguous")
+    return x
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def empty_hist(device=None, dtype=torch.int32) -> torch.Tensor:
+    """A 256-entry device buffer for a u32 histogram (torch has no uint32 ops; the
+    bits are read as int32 / converted by ``as_u32``)."""
+    return torch.empty(BINS, dtype=dtype, device=device or "cuda")
+
+
+def as_u32(h: torch.Tensor):
+    """Host numpy uint32 view of a 256-entry u32 histogram tensor."""
+    import numpy as np
+
+    return h.detach().cpu().numpy().view(np.uint32)
+
+
+def as_u64(h: torch.Tensor):
+    import numpy as np
+
+    return h.detach().cpu().numpy().view(np.uint64)
+
+
+# ---------------------------------------------------------------- one-shot --
+
+def hist_plain(x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Per-warp kernel (NVHist).  Returns a 256-entry int32 tensor holding u32 counts."""
+    x = _dev_u8(x)
+    out = empty_hist(x.device) if out is None else out
+    _abi.check("hist_plain", lib().hist_plain(x.data_ptr(), x.numel(), out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def hist_adaptive(x: torch.Tensor, pattern: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """Adaptive sub-binned kernel (AHist) with a device pattern buffer (776 bytes)."""
+    x = _dev_u8(x)
+    _check_pattern_buf(pattern)
+    out = empty_hist(x.device) if out is None else out
+    _abi.check("hist_adaptive", lib().hist_adaptive(x.data_ptr(), x.numel(), pattern.data_ptr(), out.data_ptr(),
+                                                    _stream_ptr(stream)))
+    return out
+
+
+def _check_pattern_buf(p: torch.Tensor) -> None:
+    if not p.is_cuda or p.dtype != torch.uint8 or p.numel() != PATTERN_BYTES:
+        raise TypeError("a pattern is a uint8 CUDA tensor of %d bytes" % PATTERN_BYTES)
+
+
+def empty_pattern(device=None) -> torch.Tensor:
+    return torch.empty(PATTERN_BYTES, dtype=torch.uint8, device=device or "cuda")
+
+
+def binning_pattern(prev_hist: torch.Tensor, budget: int, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    out = empty_pattern(prev_hist.device) if out is None else out
+    _check_pattern_buf(out)
+    _abi.check("binning_pattern", lib().binning_pattern(prev_hist.data_ptr(), budget, out.data_ptr(),
+                                                        _stream_ptr(stream)))
+    return out
+
+
+def default_pattern(budget: int, out: Optional[torch.Tensor] = None, device=None, stream=None) -> torch.Tensor:
+    out = empty_pattern(device) if out is None else out
+    _check_pattern_buf(out)
+    _abi.check("default_pattern", lib().default_pattern(budget, out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def pattern_from_host(off, log2k, budget: int, used: int, device=None) -> torch.Tensor:
+    """Upload a host pattern after checking it with hist_pattern_check."""
+    p = HistPattern()
+    for b in range(BINS):
+        p.off[b] = int(off[b])
+        p.log2k[b] = int(log2k[b])
+    p.budget, p.used = budget, used
+    _abi.check("hist_pattern_check", lib().hist_pattern_check(ctypes.byref(p)))
+    buf = torch.frombuffer(bytearray(bytes(p)), dtype=torch.uint8)
+    return buf.to(device or "cuda")
+
+
+def pattern_to_host(p: torch.Tensor) -> HistPattern:
+    raw = bytes(p.detach().cpu().numpy().tobytes())
+    return HistPattern.from_buffer_copy(raw)
+
+
+def degeneracy(hist: torch.Tensor, theta_milli: int = THETA_MILLI_DEFAULT, stream=None) -> torch.Tensor:
+    """Degeneracy of a u32 (int32-typed) or u64 (int64-typed) histogram: a 24-byte
+    device buffer holding {u64 max, u64 total, u32 maxbin, u32 flag}."""
+    res = torch.empty(24, dtype=torch.uint8, device=hist.device)
+    if hist.element_size() == 4:
+        rc = lib().degeneracy(hist.data_ptr(), theta_milli, res.data_ptr(), _stream_ptr(stream))
+    else:
+        rc = lib().degeneracy_u64(hist.data_ptr(), theta_milli, res.data_ptr(), _stream_ptr(stream))
+    _abi.check("degeneracy", rc)
+    return res
+
+
+def degeneracy_to_host(res: torch.Tensor) -> tuple[int, int, int, int]:
+    r = _abi.DegeneracyResult.from_buffer_copy(bytes(res.cpu().numpy().tobytes()))
+    return int(r.maxbin), int(r.max), int(r.total), int(r.flag)
+
+
+# ------------------------------------------------------------------ stream --
+
+class Stream:
+    """Chunked stream with device-resident adaptive state (Sec. III.B / III.C)."""
+
+    def __init__(self, budget: int = BUDGET_MAX, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO,
+                 grid: int = 0):
+        cfg = _abi.HistConfig()
+        lib().hist_config_init(ctypes.byref(cfg))
+        cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid = budget, theta_milli, mode, grid
+        h = ctypes.c_void_p()
+        _abi.check("hist_stream_create", lib().hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.budget, self.theta_milli, self.mode = budget, theta_milli, mode
+
+    def close(self) -> None:
+        if self._h:
+            _abi.check("hist_stream_destroy", lib().hist_stream_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, chunk: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> None:
+        chunk = _dev_u8(chunk)
+        _abi.check("hist_stream_push", lib().hist_stream_push(self._h, chunk.data_ptr(), chunk.numel(), _ptr(out),
+                                                              _stream_ptr(stream)))
+
+    def push_ptr(self, ptr: int, n: int, out_ptr: Optional[int] = None, stream=None) -> None:
+        _abi.check("hist_stream_push", lib().hist_stream_push(self._h, ptr, n, out_ptr, _stream_ptr(stream)))
+
+    def push_many(self, ptrs: Sequence[int], sizes: Sequence[int], outs: Optional[Sequence[Optional[int]]] = None,
+                  stream=None) -> None:
+        n = len(ptrs)
+        P = (ctypes.c_void_p * n)(*ptrs)
+        Z = (ctypes.c_size_t * n)(*sizes)
+        O = (ctypes.c_void_p * n)(*outs) if outs is not None else None
+        _abi.check("hist_stream_push_many", lib().hist_stream_push_many(self._h, n, P, Z, O, _stream_ptr(stream)))
+
+    def flush(self, stream=None) -> None:
+        _abi.check("hist_stream_flush", lib().hist_stream_flush(self._h, _stream_ptr(stream)))
+
+    def totals(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
+        _abi.check("hist_stream_totals", lib().hist_stream_totals(self._h, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def state(self, stream=None) -> StreamState:
+        s = StreamState()
+        _abi.check("hist_stream_get_state", lib().hist_stream_get_state(self._h, ctypes.byref(s), _stream_ptr(stream)))
+        return s
+
+    def set_state(self, s: StreamState, stream=None) -> None:
+        _abi.check("hist_stream_set_state", lib().hist_stream_set_state(self._h, ctypes.byref(s), _stream_ptr(stream)))

@@ -1,0 +1,136 @@
+"""ctypes declarations of the C ABI in include/hist.h (libhist.so).
+
+Argument marshalling only: every step of the histogram path runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhist.so")
+
+BINS = 256
+KMAX = 32
+BUDGET_MIN = 256
+BUDGET_MAX = 8192
+THETA_MILLI_DEFAULT = 450
+FLAG_PLAIN = 0
+FLAG_ADAPTIVE = 1
+MODE_AUTO = 0
+MODE_PLAIN = 1
+MODE_ADAPTIVE = 2
+
+OK = 0
+EINVAL = -1
+ENOMEM = -2
+EBUDGET = -3
+ETIMEDOUT = -4
+ECUDA = -5
+EBUSY = -6
+ESTATE = -7
+
+
+class HistPattern(ctypes.Structure):
+    _fields_ = [
+        ("off", ctypes.c_uint16 * BINS),
+        ("log2k", ctypes.c_uint8 * BINS),
+        ("budget", ctypes.c_uint32),
+        ("used", ctypes.c_uint32),
+    ]
+
+
+class DegeneracyResult(ctypes.Structure):
+    _fields_ = [
+        ("max", ctypes.c_uint64),
+        ("total", ctypes.c_uint64),
+        ("maxbin", ctypes.c_uint32),
+        ("flag", ctypes.c_uint32),
+    ]
+
+
+class HistConfig(ctypes.Structure):
+    _fields_ = [
+        ("budget", ctypes.c_uint32),
+        ("theta_milli", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
+        ("grid", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class StreamState(ctypes.Structure):
+    _fields_ = [
+        ("totals", ctypes.c_uint64 * BINS),
+        ("last_hist", ctypes.c_uint32 * BINS),
+        ("pattern", HistPattern),
+        ("last_pattern", HistPattern),
+        ("chunks", ctypes.c_uint64),
+        ("flag", ctypes.c_uint32),
+        ("last_kernel", ctypes.c_uint32),
+        ("status", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 7),
+    ]
+
+
+# (name, restype, argtypes) of every exported entry point
+_P, _Z, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = [
+    ("hist_strerror", ctypes.c_char_p, [_I]),
+    ("hist_last_cuda_error", _I, []),
+    ("hist_device_sms", _I, []),
+    ("hist_pattern_check", _I, [ctypes.POINTER(HistPattern)]),
+    ("binning_pattern", _I, [_P, _U32, _P, _P]),
+    ("default_pattern", _I, [_U32, _P, _P]),
+    ("degeneracy", _I, [_P, _U32, _P, _P]),
+    ("degeneracy_u64", _I, [_P, _U32, _P, _P]),
+    ("hist_plain", _I, [_P, _Z, _P, _P]),
+    ("hist_adaptive", _I, [_P, _Z, _P, _P, _P]),
+    ("hist_config_init", None, [ctypes.POINTER(HistConfig)]),
+    ("hist_stream_create", _I, [ctypes.POINTER(HistConfig), ctypes.POINTER(_P)]),
+    ("hist_stream_destroy", _I, [_P]),
+    ("hist_stream_push", _I, [_P, _P, _Z, _P, _P]),
+    ("hist_stream_push_many", _I, [_P, _U32, _P, _P, _P, _P]),
+    ("hist_stream_flush", _I, [_P, _P]),
+    ("hist_stream_totals", _I, [_P, _P, _P]),
+    ("hist_stream_get_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
+    ("hist_stream_set_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhist.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libhist.so is not built (%s); run paper_1011_0235_gb300.build.build() -- "
+            "there is no CPU fallback" % path
+        )
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HistError(RuntimeError):
+    def __init__(self, call: str, code: int):
+        lib = load()
+        msg = lib.hist_strerror(code).decode()
+        if code == ECUDA:
+            msg += " (cudaError %d)" % lib.hist_last_cuda_error()
+        super().__init__("%s failed: %s [%d]" % (call, msg, code))
+        self.code = code
+
+
+def check(call: str, code: int) -> None:
+    if code != OK:
+        raise HistError(call, code)

@@ -1,0 +1,168 @@
+"""GPU parity of the chunked stream (Sec. III.B / III.C) against the oracle's
+StreamOracle: per-chunk histograms, kernel choices, patterns, totals; bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1011_0235_gb300 as hl
+import synth
+from tests.gpu_util import dev, u32, u64
+
+pytestmark = pytest.mark.gpu
+SEED = synth.SEED_BASE
+MiB = 1 << 20
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    from paper_1011_0235_gb300 import build
+
+    build.build()
+    hl.lib()
+
+
+def _pat_bytes(p) -> bytes:
+    return bytes(p)
+
+
+def _check_state(s, ref: oracle.StreamOracle, rec: oracle.ChunkRecord):
+    assert np.array_equal(np.array(s.last_hist, np.uint32), rec.hist)
+    assert s.last_kernel == rec.kernel
+    assert _pat_bytes(s.last_pattern) == rec.pattern.to_bytes()
+    assert np.array_equal(np.array(s.totals, np.uint64), ref.totals)
+    assert _pat_bytes(s.pattern) == ref.pattern.to_bytes()
+    assert s.flag == ref.flag
+    assert s.chunks == ref.chunks
+    assert s.status == 0
+
+
+def _phase_chunks(count, size_fn, phase_len, seed):
+    chunks, c0 = [], 0
+    for c in range(count):
+        n = size_fn(c)
+        thr = synth.degenerate(90, 0.95) if (c // phase_len) % 2 == 0 else synth.uniform()
+        chunks.append(synth.host(n, thr, seed, c0))
+        c0 += n
+    return chunks
+
+
+@pytest.mark.parametrize("budget", [8192, 960, 2048])
+@pytest.mark.parametrize("mode", [hl.MODE_AUTO, hl.MODE_ADAPTIVE, hl.MODE_PLAIN])
+def test_stream_step_by_step(budget, mode):
+    chunks = _phase_chunks(9, lambda c: 300_000 + 7919 * c, 3, SEED + 3)
+    ref = oracle.StreamOracle(budget, mode=mode)
+    st = hl.Stream(budget=budget, mode=mode)
+    base = dev(np.concatenate([np.zeros(16, np.uint8)] + [np.concatenate([ch, np.zeros(16, np.uint8)]) for ch in chunks]))
+    off = 16
+    for c, ch in enumerate(chunks):
+        off_c = off
+        off += ch.size + 16
+        x = base[off_c:off_c + ch.size]
+        out = torch.full((256,), -1, dtype=torch.int32, device="cuda")
+        st.push(x, out)
+        rec = ref.push(ch)
+        s = st.state()
+        _check_state(s, ref, rec)
+        assert np.array_equal(u32(out), rec.hist)
+    st.close()
+
+
+def test_stream_batched_matches_step_by_step_and_outputs():
+    chunks = _phase_chunks(14, lambda c: [0, 1, 17, 1 << 20, 123457, 64 * 1024][c % 6] + c, 2, SEED + 5)
+    ref = oracle.StreamOracle(8192)
+    recs = [ref.push(ch) for ch in chunks]
+    # each chunk at a different alignment inside one buffer
+    offs, pos = [], 0
+    for c, ch in enumerate(chunks):
+        pos += c % 16
+        offs.append(pos)
+        pos += ch.size
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192)
+    st.push_many([bd.data_ptr() + o for o in offs], [ch.size for ch in chunks],
+                 [outs[i].data_ptr() for i in range(len(chunks))])
+    s = st.state()
+    _check_state(s, ref, recs[-1])
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for i, r in enumerate(recs):
+        assert np.array_equal(got[i], r.hist), i
+    tot = st.totals()
+    assert np.array_equal(u64(tot), ref.totals)
+    st.close()
+
+
+def test_stream_checkpoint_resume():
+    chunks = _phase_chunks(10, lambda c: 200_000 + c, 3, SEED + 6)
+    ref = oracle.StreamOracle(960)
+    for ch in chunks:
+        ref.push(ch)
+    a = hl.Stream(budget=960)
+    for ch in chunks[:6]:
+        a.push(dev(ch))
+    saved = a.state()
+    a.close()
+    b = hl.Stream(budget=960)
+    b.set_state(saved)
+    for ch in chunks[6:]:
+        b.push(dev(ch))
+    s = b.state()
+    assert np.array_equal(np.array(s.totals, np.uint64), ref.totals)
+    assert bytes(s.pattern) == ref.pattern.to_bytes() and s.flag == ref.flag and s.chunks == 10
+    b.close()
+
+
+def test_stream_rejects_bad_state_and_chunk():
+    st = hl.Stream(budget=960)
+    s = st.state()
+    s.pattern.log2k[0] = 9
+    with pytest.raises(hl.HistError):
+        st.set_state(s)
+    s = st.state()
+    s.pattern.budget = 8192  # a pattern for another budget
+    with pytest.raises(hl.HistError):
+        st.set_state(s)
+    with pytest.raises(hl.HistError):
+        st.push_ptr(0, 10)
+    st.close()
+
+
+def _full_stream(thr_fn, mode, budget, seed):
+    n_chunks, csize = 64, 16 * MiB
+    host = np.empty(n_chunks * csize, np.uint8)
+    for c in range(n_chunks):
+        host[c * csize:(c + 1) * csize] = synth.host(csize, thr_fn(c), seed, c * csize, threads=16)
+    xd = dev(host)
+    outs = torch.empty((n_chunks, 256), dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=budget, mode=mode)
+    st.push_many([xd.data_ptr() + c * csize for c in range(n_chunks)], [csize] * n_chunks,
+                 [outs[c].data_ptr() for c in range(n_chunks)])
+    s = st.state()
+    ref = oracle.StreamOracle(budget, mode=mode)
+    recs = [ref.push(host[c * csize:(c + 1) * csize]) for c in range(n_chunks)]
+    got = u32(outs.reshape(-1)).reshape(n_chunks, 256)
+    for c in range(n_chunks):
+        assert np.array_equal(got[c], recs[c].hist), c
+    _check_state(s, ref, recs[-1])
+    st.close()
+    return recs
+
+
+def test_full_size_normal_sigma8_adaptive():
+    # 1 GiB in 16 MiB chunks of clamp(round(N(128, 8))), adaptive kernel, pattern
+    # refreshed per chunk
+    _full_stream(lambda c: synth.normal(128, 8), hl.MODE_ADAPTIVE, 8192, SEED + 2)
+
+
+def test_full_size_degenerate_switching():
+    # 1 GiB in 16 MiB chunks, 95 % = 90 + 5 % uniform, switching to uniform every
+    # 8 chunks; the switch must follow one chunk behind each phase change
+    recs = _full_stream(lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform(),
+                        hl.MODE_AUTO, 8192, SEED + 3)
+    kernels = [r.kernel for r in recs]
+    expect = [0] + [1 if ((c - 1) // 8) % 2 == 0 else 0 for c in range(1, 64)]
+    assert kernels == expect
