@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive histogram stream on GB300.
+
+Workload (one step): a 1 GiB uint8 stream of clamp(round(N(128, 8))) pixels
+(the X-ray-like peaked distribution) cut into 64 chunks of 16 MiB, pushed
+through the chunked stream with the adaptive kernel, the binning pattern of
+each chunk refreshed on the device from the previous chunk's histogram, the
+degeneracy switch evaluated and the totals accumulated (every step of the hot
+path).  Inputs are generated on the device and resident in HBM before the
+timed region; at 1 GiB they are larger than the 129 MB L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MiB = 1 << 20
+CHUNK = 16 * MiB
+METRIC = "input GB/s (% of HBM peak), adaptive vs plain kernel; p50/p99 request latency"
+UNIT = "GB/s"
+CPU_SAMPLE_SECONDS = 10.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
+    ap.add_argument("--profile", action="store_true",
+                    help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
+    return ap.parse_args()
+
+
+def workload_config(chunks):
+    return {
+        "workload": "stream of %d MiB uint8 in 16 MiB chunks, clamp(round(N(128, sigma=8))), adaptive kernel, "
+                    "binning pattern refreshed per chunk on the device" % (chunks * 16),
+        "bytes_per_step": chunks * CHUNK,
+        "chunk_bytes": CHUNK,
+        "chunks": chunks,
+        "budget": 8192,
+        "theta_milli": 450,
+        "l2": "inputs larger than L2 (1 GiB vs 129 MB); no flush needed" if chunks * CHUNK > 256 * MiB
+        else "inputs smaller than 2x L2: numbers include L2 reuse",
+    }
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+        self.t0 = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.06)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None] or [0])}
+
+
+# ------------------------------------------------------------ helpers ----
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1011_0235_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    k = rec.get(kernel)
+    if not k or k.get("csrc_hash") != csrc_hash():
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+def gen_workload_device(torch, synth, chunks, seed, thr_fn):
+    x = torch.empty(chunks * CHUNK, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for c in range(chunks):
+        synth.device_fill(x.data_ptr() + c * CHUNK, CHUNK, thr_fn(c), seed, c * CHUNK, s)
+    torch.cuda.synchronize()
+    return x
+
+
+def time_steps(torch, step, warmup, steps, barrier=None):
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return e0.elapsed_time(e1) / 1e3  # seconds
+
+
+def cpu_oracle_rate(host_chunks, seconds):
+    """Time the oracle's stream (hist + switch + pattern per chunk) on host cores
+    over the given chunks, repeated until `seconds` have passed."""
+    import oracle
+
+    oracle.lib()
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        so = oracle.StreamOracle(8192, mode=oracle.MODE_ADAPTIVE)
+        for ch in host_chunks:
+            so.push(ch)
+            done += ch.size
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return done / el / 1e9, done, el
+
+
+# ---------------------------------------------------------- reference ----
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synth
+
+    oracle.build()
+    synth.build_host()
+    thr = synth.normal(128, 8)
+    sample_chunks = 4  # 64 MiB of the workload per step
+    chunks = [synth.host(CHUNK, thr, synth.SEED_BASE + 2, c * CHUNK, threads=os.cpu_count() or 1)
+              for c in range(sample_chunks)]
+    so = oracle.StreamOracle(8192, mode=oracle.MODE_ADAPTIVE)
+
+    def step():
+        for ch in chunks:
+            so.push(ch)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    nbytes = sample_chunks * CHUNK * args.steps
+    val = nbytes / el / 1e9
+    cfg = workload_config(args.chunks)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d of the workload's 16 MiB chunks (%d MiB) per step, single-threaded plain C "
+                                   "counting loop + degeneracy + binning pattern per chunk"
+                                   % (sample_chunks, sample_chunks * 16)},
+        "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# -------------------------------------------------------------- native ----
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    barrier = None
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+
+    import synth
+    import paper_1011_0235_gb300 as hl
+    from paper_1011_0235_gb300 import build as hbuild
+
+    hbuild.build()
+    synth.build()
+    hl.lib()
+
+    chunks = args.chunks
+    nbytes = chunks * CHUNK
+    thr = synth.normal(128, 8)
+    seed = synth.SEED_BASE + 2
+    x = gen_workload_device(torch, synth, chunks, seed, lambda c: thr)
+    ptrs = [x.data_ptr() + c * CHUNK for c in range(chunks)]
+    sizes = [CHUNK] * chunks
+
+    def stream_step(st):
+        def step():
+            st.push_many(ptrs, sizes)
+            st.flush()
+        return step
+
+    st_ad = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+    sampler = ClockSampler(local)
+    step = stream_step(st_ad)
+    if not args.profile:
+        sampler.start()
+        # settle clocks for at least one second before the timed region
+        t_settle = time.time()
+        while time.time() - t_settle < 1.0:
+            step()
+            torch.cuda.synchronize()
+    el = time_steps(torch, step, args.warmup, args.steps, barrier)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([el], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    value = world * nbytes * args.steps / el / 1e9
+    launches_per_step = chunks + 1  # chunk kernels + the finish kernel
+
+    extras = {}
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+
+    # dominant kernel: the decoupled batch kernel, 64 chunks of 16 MiB per launch
+    avg_launch_s = el / (args.steps * chunks)
+    achieved = CHUNK / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": recorded_traffic("batch_decoupled_kernel"),
+                "kernel": "batch_decoupled_kernel", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": CHUNK}
+
+    if not args.profile:
+        # plain kernel on the same stream of data
+        st_pl = hl.Stream(budget=8192, mode=hl.MODE_PLAIN)
+        el_pl = time_steps(torch, stream_step(st_pl), args.warmup, args.steps, barrier)
+        extras["plain_stream_gbs"] = round(world * nbytes * args.steps / el_pl / 1e9, 2)
+        extras["adaptive_stream_gbs"] = round(value, 2)
+        extras["adaptive_frac_of_hbm"] = round(value / world / hbm, 4)
+        extras["plain_frac_of_hbm"] = round(extras["plain_stream_gbs"] / world / hbm, 4)
+        # degenerate workload: 95 % = 90 + 5 % uniform, switching to uniform every 8 chunks
+        xdg = gen_workload_device(torch, synth, chunks, synth.SEED_BASE + 3,
+                                  lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform())
+        pd = [xdg.data_ptr() + c * CHUNK for c in range(chunks)]
+        for name, mode in (("auto", hl.MODE_AUTO), ("plain", hl.MODE_PLAIN), ("adaptive", hl.MODE_ADAPTIVE)):
+            s2 = hl.Stream(budget=8192, mode=mode)
+
+            def st2(s2=s2):
+                s2.push_many(pd, sizes)
+                s2.flush()
+            e2 = time_steps(torch, st2, args.warmup, args.steps, barrier)
+            extras["degenerate_%s_gbs" % name] = round(world * nbytes * args.steps / e2 / 1e9, 2)
+            s2.close()
+        del xdg
+        # one-shot kernels on the whole 1 GiB at once (no stream)
+        full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
+        o = hl.empty_hist()
+        e3 = time_steps(torch, lambda: hl.hist_adaptive(x, full, o), 2, 10)
+        extras["oneshot_adaptive_full_table_gbs"] = round(nbytes * 10 / e3 / 1e9, 2)
+        e4 = time_steps(torch, lambda: hl.hist_plain(x, o), 2, 10)
+        extras["oneshot_plain_gbs"] = round(nbytes * 10 / e4 / 1e9, 2)
+        st_pl.close()
+
+    # end to end: host buffers through hist_stream_push_host, H2D inside the timed region
+    e2e = None
+    try:
+        if args.profile:
+            raise RuntimeError("skipped (--profile)")
+        hx = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        synth._host_lib().synth_fill_host_mt(hx.data_ptr(), nbytes, np.ascontiguousarray(thr).ctypes.data,
+                                             seed, 0, os.cpu_count() or 1)
+        st_e = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+        st_e.attach_staging(CHUNK, 3)
+        tot_d = torch.empty(256, dtype=torch.int64, device="cuda")
+        tot_h = torch.empty(256, dtype=torch.int64, pin_memory=True)
+
+        def e2e_step():
+            for c in range(chunks):
+                st_e.push_host(hx.data_ptr() + c * CHUNK, CHUNK)
+            st_e.totals(tot_d)
+            tot_h.copy_(tot_d, non_blocking=True)
+
+        ksteps = max(3, min(args.steps, 20))
+        el_e = time_steps(torch, e2e_step, max(args.warmup, 3), ksteps, barrier)
+        if world > 1:
+            t = torch.tensor([el_e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el_e = float(t.item())
+        e2e = {"value": round(world * nbytes * ksteps / el_e / 1e9, 2), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 256 * 8, "steps": ksteps,
+               "path": "hist_stream_push_host: pinned host -> 3 staging buffers, copies overlapped with kernels"}
+        st_e.close()
+        del hx
+    except Exception as exc:  # report, do not hide
+        e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.profile:
+        import oracle
+
+        oracle.build()
+        sample = 8
+        host_chunks = [synth.host(CHUNK, thr, seed, c * CHUNK, threads=os.cpu_count() or 1) for c in range(sample)]
+        rate, done, secs = cpu_oracle_rate(host_chunks, CPU_SAMPLE_SECONDS)
+        cpu = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the first %d chunks (%d MiB) of the workload, repeated for %.1f s (%d MiB processed); "
+                         "single-threaded C counting loop + degeneracy + binning pattern per chunk"
+                         % (sample, sample * 16, secs, done // MiB)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(chunks), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": launches_per_step * args.steps, "extras": extras,
+        }
+        print(json.dumps(out))
+    st_ad.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

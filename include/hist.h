@@ -149,7 +149,17 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  * "Accumulator"), the last chunk's histogram, the pattern and the kernel the
  * next chunk will use.  Chunk i+1 uses the pattern and the switch computed
  * from chunk i's histogram (a moving window of one chunk).  The first chunk
- * runs the plain kernel with default_pattern(budget). */
+ * runs the plain kernel with default_pattern(budget).
+ *
+ * A batch of pushed chunks runs in one cooperative launch.  In AUTO mode, and
+ * in ADAPTIVE mode below the full budget, chunk i+1's kernel or layout
+ * depends on chunk i's histogram, so the CTAs wait for it between chunks.
+ * In PLAIN mode (no pattern used) and in ADAPTIVE mode at HIST_BUDGET_MAX
+ * (the rule then gives the full table after every non-empty chunk and the
+ * default pattern after an empty one) the layouts are known in advance: the
+ * chunks are counted back to back and each one's switch and pattern are
+ * computed from its histogram afterwards, and checked against the layout
+ * that was used (status bit 8 otherwise). */
 #define HIST_MODE_AUTO 0u     /* kernel chosen by the degeneracy switch */
 #define HIST_MODE_PLAIN 1u    /* always the plain kernel (pattern still refreshed) */
 #define HIST_MODE_ADAPTIVE 2u /* always the adaptive kernel */
@@ -191,6 +201,28 @@ int hist_stream_flush(hist_stream* st, hist_cuda_stream s);
 /* Flush, then copy the running totals (uint64_t[256]) to d_totals. */
 int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s);
 
+/* Host-fed chunks (Sec. III.B: double-buffered transfers to the GPU overlapped
+ * with the kernels).  attach_staging allocates `depth` (2..4) device staging
+ * buffers of max_chunk bytes, an internal copy stream and events; call it
+ * once, outside stream capture.  push_host copies h_chunk (n <= max_chunk; pin
+ * it with cudaHostAlloc for the copy to overlap) into the next staging buffer
+ * on the copy stream once the kernel that last read that buffer has finished,
+ * makes `s` wait for the copy and pushes the staged chunk.  The caller may
+ * reuse h_chunk once `s` has passed this call.  HIST_ESTATE without staging. */
+int hist_stream_attach_staging(hist_stream* st, size_t max_chunk, uint32_t depth);
+int hist_stream_push_host(hist_stream* st, const uint8_t* h_chunk, size_t n, uint32_t* d_chunk_out,
+                          hist_cuda_stream s);
+
+/* Tracing: the kernels record %globaltimer (ns) at eight phase boundaries of
+ * every chunk -- start, previous histogram complete, pattern ready, chunk
+ * counted by warp 0, counted by all warps, table reduced, partial sums
+ * published, end -- for three CTAs (the first, middle and last) into
+ * d_trace, a uint64_t array laid out [chunk][3][8] for
+ * capacity_chunks chunks counted from this call; later chunks are not
+ * recorded.  d_trace null turns tracing off.  The caller keeps d_trace alive
+ * while tracing is on. */
+int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chunks);
+
 /* Stream state, for inspection and for checkpoint / resume. */
 typedef struct hist_stream_state {
   uint64_t totals[HIST_BINS];   /* sum of all chunk histograms */
@@ -200,7 +232,9 @@ typedef struct hist_stream_state {
   uint64_t chunks;              /* chunks completed */
   uint32_t flag;                /* switch from the last chunk (next kernel in AUTO) */
   uint32_t last_kernel;         /* kernel the last chunk ran */
-  uint32_t status;              /* 0, or a device-side error code */
+  uint32_t status;              /* 0, or device-side error bits: 4 = a bounded wait
+                                   ran out, 8 = a chunk's layout differed from the
+                                   pattern rule (never expected) */
   uint32_t reserved[7];
 } hist_stream_state;
 

@@ -186,6 +186,26 @@ class Stream:
         O = (ctypes.c_void_p * n)(*outs) if outs is not None else None
         _abi.check("hist_stream_push_many", lib().hist_stream_push_many(self._h, n, P, Z, O, _stream_ptr(stream)))
 
+    TRACE_PHASES = ("start", "hist_ready", "pattern_ready", "counted_warp0", "counted_all", "reduced",
+                    "published", "end")
+
+    def trace(self, capacity_chunks: int) -> torch.Tensor:
+        """Start tracing into a new [capacity, 3, 8] int64 device tensor (ns)."""
+        buf = torch.zeros((capacity_chunks, 3, len(self.TRACE_PHASES)), dtype=torch.int64, device="cuda")
+        _abi.check("hist_stream_trace", lib().hist_stream_trace(self._h, buf.data_ptr(), capacity_chunks))
+        self._trace = buf
+        return buf
+
+    def trace_off(self) -> None:
+        _abi.check("hist_stream_trace", lib().hist_stream_trace(self._h, None, 0))
+
+    def attach_staging(self, max_chunk: int, depth: int = 2) -> None:
+        _abi.check("hist_stream_attach_staging", lib().hist_stream_attach_staging(self._h, max_chunk, depth))
+
+    def push_host(self, ptr: int, n: int, out_ptr: Optional[int] = None, stream=None) -> None:
+        """Push a chunk held in host memory at `ptr` (pinned for overlap)."""
+        _abi.check("hist_stream_push_host", lib().hist_stream_push_host(self._h, ptr, n, out_ptr, _stream_ptr(stream)))
+
     def flush(self, stream=None) -> None:
         _abi.check("hist_stream_flush", lib().hist_stream_flush(self._h, _stream_ptr(stream)))
 

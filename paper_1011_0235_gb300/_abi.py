@@ -94,6 +94,9 @@ SIGNATURES = [
     ("hist_stream_push", _I, [_P, _P, _Z, _P, _P]),
     ("hist_stream_push_many", _I, [_P, _U32, _P, _P, _P, _P]),
     ("hist_stream_flush", _I, [_P, _P]),
+    ("hist_stream_trace", _I, [_P, _P, _U32]),
+    ("hist_stream_attach_staging", _I, [_P, _Z, _U32]),
+    ("hist_stream_push_host", _I, [_P, _P, _Z, _P, _P]),
     ("hist_stream_totals", _I, [_P, _P, _P]),
     ("hist_stream_get_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_set_state", _I, [_P, ctypes.POINTER(StreamState), _P]),

@@ -52,22 +52,28 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x]) atomicAdd(out + threadIdx.x, cs.res[threadIdx.x]);
 }
 
-__global__ void __launch_bounds__(256) pattern_kernel(const uint32_t* __restrict__ h, uint32_t budget,
-                                                      hist_pattern* __restrict__ out) {
-  __shared__ CtaShared cs;
-  if (h) binning_pattern_block([&](int b) { return h[b]; }, budget, cs.pat, cs);
-  else default_pattern_block(budget, cs.pat, cs);
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(&cs.pat);
+// One warp: the binning pattern of h (or the default pattern if h is null).
+__global__ void __launch_bounds__(32) pattern_kernel(const uint32_t* __restrict__ h, uint32_t budget,
+                                                     hist_pattern* __restrict__ out) {
+  __shared__ hist_pattern P;
+  __shared__ uint32_t hs[HIST_BINS];
+  for (int i = threadIdx.x; i < HIST_BINS; i += 32) hs[i] = h ? h[i] : 0u;
+  __syncwarp();
+  warp_epilogue(hs, budget, HIST_THETA_MILLI_DEFAULT, P);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&P);
   uint32_t* dst = reinterpret_cast<uint32_t*>(out);
-  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += 32) dst[i] = src[i];
 }
 
+// One warp: the degeneracy of h.
 template <class T>
-__global__ void __launch_bounds__(256) degeneracy_kernel(const T* __restrict__ h, uint32_t theta,
-                                                         hist_degeneracy_result* __restrict__ res) {
-  __shared__ CtaShared cs;
-  const hist_degeneracy_result r =
-      degeneracy_block([&](int b) { return (unsigned long long)h[b]; }, theta, cs);
+__global__ void __launch_bounds__(32) degeneracy_kernel(const T* __restrict__ h, uint32_t theta,
+                                                        hist_degeneracy_result* __restrict__ res) {
+  __shared__ hist_pattern P;
+  __shared__ T hs[HIST_BINS];
+  for (int i = threadIdx.x; i < HIST_BINS; i += 32) hs[i] = h[i];
+  __syncwarp();
+  const hist_degeneracy_result r = warp_epilogue(hs, HIST_BUDGET_MAX, theta, P);
   if (threadIdx.x == 0) *res = r;
 }
 
@@ -173,14 +179,14 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
 
 int binning_pattern(const uint32_t* d_prev_hist, uint32_t budget, hist_pattern* d_pat, hist_cuda_stream s) {
   if (!d_prev_hist || !d_pat || budget < HIST_BUDGET_MIN || budget > HIST_BUDGET_MAX) return HIST_EINVAL;
-  pattern_kernel<<<1, 256, 0, (cudaStream_t)s>>>(d_prev_hist, budget, d_pat);
+  pattern_kernel<<<1, 32, 0, (cudaStream_t)s>>>(d_prev_hist, budget, d_pat);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 
 int default_pattern(uint32_t budget, hist_pattern* d_pat, hist_cuda_stream s) {
   if (!d_pat || budget < HIST_BUDGET_MIN || budget > HIST_BUDGET_MAX) return HIST_EINVAL;
-  pattern_kernel<<<1, 256, 0, (cudaStream_t)s>>>(nullptr, budget, d_pat);
+  pattern_kernel<<<1, 32, 0, (cudaStream_t)s>>>(nullptr, budget, d_pat);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
@@ -188,7 +194,7 @@ int default_pattern(uint32_t budget, hist_pattern* d_pat, hist_cuda_stream s) {
 int degeneracy(const uint32_t* d_hist, uint32_t theta_milli, hist_degeneracy_result* d_res,
                hist_cuda_stream s) {
   if (!d_hist || !d_res || theta_milli > 1000) return HIST_EINVAL;
-  degeneracy_kernel<uint32_t><<<1, 256, 0, (cudaStream_t)s>>>(d_hist, theta_milli, d_res);
+  degeneracy_kernel<uint32_t><<<1, 32, 0, (cudaStream_t)s>>>(d_hist, theta_milli, d_res);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
@@ -196,7 +202,7 @@ int degeneracy(const uint32_t* d_hist, uint32_t theta_milli, hist_degeneracy_res
 int degeneracy_u64(const uint64_t* d_hist, uint32_t theta_milli, hist_degeneracy_result* d_res,
                    hist_cuda_stream s) {
   if (!d_hist || !d_res || theta_milli > 1000) return HIST_EINVAL;
-  degeneracy_kernel<unsigned long long><<<1, 256, 0, (cudaStream_t)s>>>(
+  degeneracy_kernel<unsigned long long><<<1, 32, 0, (cudaStream_t)s>>>(
       reinterpret_cast<const unsigned long long*>(d_hist), theta_milli, d_res);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);

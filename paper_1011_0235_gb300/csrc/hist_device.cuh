@@ -37,7 +37,6 @@ struct CtaShared {
   uint32_t hist[HIST_BINS];  // a histogram being reduced (epilogues)
   uint32_t res[HIST_BINS];   // this CTA's partial result
   unsigned long long red[kWarps];
-  uint32_t cls[8][8];        // per-warp class counts for the pattern layout
   int path;
   int lk;
   uint32_t flag;
@@ -62,51 +61,67 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-__device__ __forceinline__ void shared_add(uint32_t* p, uint32_t v) {
-  uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One increment of the shared-memory word at byte address `a`.
+__device__ __forceinline__ void shared_inc(uint32_t a) {
+  asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ uint32_t shared_ld(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
 }
 
 // ------------------------------------------------------------- counting --
+// Addresses are 32-bit byte offsets in the shared window: `base` is this
+// thread's first slot (PLAIN: its warp's table; SHIFT: lane & (K-1)), `lutb`
+// its lane's column of the slot table, `table` the table itself.
 
 template <int PATH, int LK>
-__device__ __forceinline__ void count_word(uint32_t w, uint32_t* base, const uint32_t* lutb,
-                                           uint32_t* table) {
+__device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t lutb, uint32_t table) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const uint32_t v = (w >> (8 * k)) & 0xffu;
-    if (PATH == PATH_LUT) shared_add(table + lutb[v << 5], 1u);
-    else shared_add(base + (v << LK), 1u);
+    if (PATH == PATH_LUT) shared_inc(table + (shared_ld(lutb + (v << 7)) << 2));
+    else shared_inc(base + (v << (LK + 2)));
   }
 }
 
 template <int PATH, int LK>
-__device__ __forceinline__ void count_vec(const uint4& q, uint32_t* base, const uint32_t* lutb,
-                                          uint32_t* table) {
+__device__ __forceinline__ void count_vec(const uint4& q, uint32_t base, uint32_t lutb, uint32_t table) {
   count_word<PATH, LK>(q.x, base, lutb, table);
   count_word<PATH, LK>(q.y, base, lutb, table);
   count_word<PATH, LK>(q.z, base, lutb, table);
   count_word<PATH, LK>(q.w, base, lutb, table);
 }
 
+// Shared-window addresses of this thread's slots for a layout.
+template <int PATH, int LK>
+__device__ __forceinline__ void thread_bases(const uint32_t* table, const uint32_t* lut, uint32_t& base,
+                                             uint32_t& lutb, uint32_t& tab) {
+  const uint32_t lane = threadIdx.x & 31;
+  tab = smem_addr(table);
+  if (PATH == PATH_PLAIN) base = tab + (threadIdx.x >> 5) * HIST_BINS * 4;
+  else base = tab + ((lane & ((1u << LK) - 1u)) << 2);
+  lutb = smem_addr(lut) + (lane << 2);
+}
+
 // Count the 16-byte vectors [begin, end) of p, this CTA's slice: thread t takes
 // vectors begin + t, begin + t + kThreads, ... (coalesced), two loads in flight.
 template <int PATH, int LK>
 static __device__ void count_slice(const uint4* __restrict__ p, size_t begin, size_t end, uint32_t* table,
-                            const uint32_t* lut) {
-  const int lane = threadIdx.x & 31;
-  uint32_t* base;
-  if (PATH == PATH_PLAIN) base = table + (threadIdx.x >> 5) * HIST_BINS;
-  else base = table + (lane & ((1 << LK) - 1));
-  const uint32_t* lutb = lut + lane;
+                                   const uint32_t* lut) {
+  uint32_t base, lutb, tab;
+  thread_bases<PATH, LK>(table, lut, base, lutb, tab);
   size_t i = begin + threadIdx.x;
   for (; i + kThreads < end; i += 2 * kThreads) {
     const uint4 a = ldg_stream(p + i);
     const uint4 b = ldg_stream(p + i + kThreads);
-    count_vec<PATH, LK>(a, base, lutb, table);
-    count_vec<PATH, LK>(b, base, lutb, table);
+    count_vec<PATH, LK>(a, base, lutb, tab);
+    count_vec<PATH, LK>(b, base, lutb, tab);
   }
-  if (i < end) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, table);
+  if (i < end) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, tab);
 }
 
 __device__ __forceinline__ void count_dispatch(int path, int lk, const uint4* p, size_t begin,
@@ -177,28 +192,6 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// Sum of v over threads 0..255 (others must pass 0); every thread gets it.
-static __device__ unsigned long long sum256(unsigned long long v, CtaShared& cs) {
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0 && threadIdx.x < HIST_BINS) cs.red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  unsigned long long t = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) t += cs.red[i];
-  __syncthreads();
-  return t;
-}
-static __device__ unsigned long long max256(unsigned long long v, CtaShared& cs) {
-  v = warp_max(v);
-  if ((threadIdx.x & 31) == 0 && threadIdx.x < HIST_BINS) cs.red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  unsigned long long t = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) t = cs.red[i] > t ? cs.red[i] : t;
-  __syncthreads();
-  return t;
-}
-
 // ------------------------------------------------------------ degeneracy --
 
 // max * 1000 >= theta * total, exactly (128-bit products).
@@ -211,66 +204,9 @@ __device__ __forceinline__ bool reaches_theta(unsigned long long mx, unsigned lo
   return lhi > rhi || (lhi == rhi && llo >= rlo);
 }
 
-// Degeneracy (Sec. III.C) of a 256-bin histogram; value(b) is called by threads
-// 0..255.  All threads call; all get the result.
-template <class F>
-__device__ hist_degeneracy_result degeneracy_block(F value, uint32_t theta_milli, CtaShared& cs) {
-  const bool act = threadIdx.x < HIST_BINS;
-  const unsigned long long h = act ? value(threadIdx.x) : 0ull;
-  const unsigned long long total = sum256(h, cs);
-  const unsigned long long mx = max256(h, cs);
-  // lowest bin holding the maximum
-  const unsigned long long key = (act && h == mx) ? (unsigned long long)(255 - threadIdx.x) : 0ull;
-  const unsigned long long k = max256(act && h == mx ? key + 1 : 0ull, cs);
-  hist_degeneracy_result r;
-  r.max = mx;
-  r.total = total;
-  r.maxbin = (mx == 0) ? 0u : (uint32_t)(255 - (k - 1));
-  r.flag = reaches_theta(mx, total, theta_milli) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-  return r;
-}
-
 // -------------------------------------------------------- binning pattern --
 
 __device__ __forceinline__ uint32_t ilog2_u64(unsigned long long v) { return 63u - __clzll(v); }
-
-// Offsets for the sub-bin counts lk (thread b < 256 holds lk of bin b): bins in
-// order of decreasing k, ties by increasing bin index.  All threads call.
-static __device__ void pattern_layout(uint32_t lk, uint32_t budget, hist_pattern& P, CtaShared& cs) {
-  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const bool act = t < HIST_BINS;
-  uint32_t my_rank = 0;
-#pragma unroll
-  for (uint32_t c = 0; c < 6; ++c) {
-    const unsigned m = __ballot_sync(0xffffffffu, act && lk == c);
-    if (act && lk == c) my_rank = __popc(m & ((1u << lane) - 1u));
-    if (act && lane == 0) cs.cls[w][c] = __popc(m);
-  }
-  __syncthreads();
-  if (act) {
-    uint32_t before = 0;
-    for (int w2 = 0; w2 < w; ++w2) before += cs.cls[w2][lk];
-    uint32_t base = 0;
-    for (uint32_t c = 5; c > lk; --c) {
-      uint32_t cnt = 0;
-      for (int w2 = 0; w2 < 8; ++w2) cnt += cs.cls[w2][c];
-      base += cnt << c;
-    }
-    P.off[t] = (uint16_t)(base + ((my_rank + before) << lk));
-    P.log2k[t] = (uint8_t)lk;
-    if (t == 0) {
-      uint32_t used = 0;
-      for (uint32_t c = 0; c < 6; ++c) {
-        uint32_t cnt = 0;
-        for (int w2 = 0; w2 < 8; ++w2) cnt += cs.cls[w2][c];
-        used += cnt << c;
-      }
-      P.used = used;
-      P.budget = budget;
-    }
-  }
-  __syncthreads();
-}
 
 // Default pattern (reading of Figure 1), log2 of the sub-bins of bin b.
 __device__ __forceinline__ uint32_t default_lk(uint32_t b, uint32_t budget) {
@@ -280,36 +216,6 @@ __device__ __forceinline__ uint32_t default_lk(uint32_t b, uint32_t budget) {
   const uint32_t rlk = (r < 4) ? r : 7 - r;  // 0,1,2,3,3,2,1,0
   const uint32_t lk = rlk + ls;
   return lk > 5 ? 5 : lk;
-}
-
-static __device__ void default_pattern_block(uint32_t budget, hist_pattern& P, CtaShared& cs) {
-  const uint32_t lk = threadIdx.x < HIST_BINS ? default_lk(threadIdx.x, budget) : 0;
-  pattern_layout(lk, budget, P, cs);
-}
-
-// Binning pattern from a histogram (Sec. III.B; rule stated in hist.h).
-// value(b) is called by threads 0..255.  All threads call.
-template <class F>
-static __device__ void binning_pattern_block(F value, uint32_t budget, hist_pattern& P, CtaShared& cs) {
-  const bool act = threadIdx.x < HIST_BINS;
-  const unsigned long long h = act ? (unsigned long long)value(threadIdx.x) : 0ull;
-  const unsigned long long total = sum256(h, cs);
-  if (total == 0) {
-    default_pattern_block(budget, P, cs);
-    return;
-  }
-  const unsigned long long spare = budget - HIST_BINS;
-  const unsigned long long want = 1ull + (spare * h) / total;
-  uint32_t lk0 = ilog2_u64(want);
-  lk0 = lk0 > 5 ? 5 : lk0;
-  uint32_t lf = 0;
-  for (uint32_t f = 1; f <= 5; ++f) {
-    const uint32_t kk = act ? (1u << (lk0 > f ? lk0 : f)) : 0u;
-    const unsigned long long s = sum256(kk, cs);
-    if (s <= budget) lf = f;
-  }
-  const uint32_t lk = lk0 > lf ? lk0 : lf;
-  pattern_layout(lk, budget, P, cs);
 }
 
 // ------------------------------------------------- pattern classification --
@@ -364,6 +270,233 @@ __device__ __forceinline__ void count_edges(const uint8_t* a, const Split& sp, C
   const int t = threadIdx.x;
   if (t < (int)sp.head) atomicAdd(&cs.res[a[t]], 1u);
   else if (t >= 16 && t < 16 + (int)sp.tail) atomicAdd(&cs.res[a[sp.head + sp.nvec * 16 + (t - 16)]], 1u);
+}
+
+}  // namespace histdev
+
+namespace histdev {
+
+// ------------------------------------------------- single-warp epilogue --
+
+// floor(a / b) for 0 < b < 2^32 and a / b < 2^20, exactly: an FP32 estimate
+// (relative error below 2^-22, so within 1/4 of a quotient below 2^20)
+// corrected by one integer step each way.  Other operands take the integer
+// division.
+__device__ __forceinline__ unsigned long long div_floor(unsigned long long a, unsigned long long b, float rb) {
+  if (b < (1ull << 32) && a < (b << 20)) {
+    unsigned long long q = (unsigned long long)(uint32_t)((float)a * rb);
+    if (q * b > a) q -= 1;
+    else if ((q + 1) * b <= a) q += 1;
+    return q;
+  }
+  return a / b;
+}
+
+// One warp computes the degeneracy (Sec. III.C) and the binning pattern (the
+// rule stated in hist.h) of the 256-bin histogram `hist`.  Lane l holds bins
+// l + 32 i, i = 0..7.  Writes P (off, log2k, budget, used) and returns the
+// degeneracy to every lane.
+template <class T>
+__device__ hist_degeneracy_result warp_epilogue(const T* hist, uint32_t budget, uint32_t theta_milli,
+                                                hist_pattern& P) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long h[8];
+  unsigned long long tot = 0, mx = 0;
+  int arg = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[i] = (unsigned long long)hist[lane + 32 * i];
+    tot += h[i];
+    if (h[i] > mx) {  // bins of one lane rise with i: the first maximum is the lowest
+      mx = h[i];
+      arg = lane + 32 * i;
+    }
+  }
+  tot = warp_sum(tot);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (m2 > mx || (m2 == mx && a2 < arg)) {
+      mx = m2;
+      arg = a2;
+    }
+  }
+  hist_degeneracy_result r;
+  r.max = mx;
+  r.total = tot;
+  r.maxbin = mx == 0 ? 0u : (uint32_t)arg;
+  r.flag = reaches_theta(mx, tot, theta_milli) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+
+  uint32_t lk[8];
+  if (tot == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) lk[i] = default_lk(lane + 32 * i, budget);
+  } else {
+    const unsigned long long spare = budget - HIST_BINS;
+    const float rt = 1.0f / (float)tot;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      // spare < 2^13 and h <= tot, so the quotient is below 2^13
+      const unsigned long long want = 1ull + div_floor(spare * h[i], tot, rt);
+      const uint32_t l0 = ilog2_u64(want);
+      lk[i] = l0 > 5 ? 5 : l0;
+    }
+    uint32_t lf = 0;
+    for (uint32_t f = 1; f <= 5; ++f) {
+      unsigned long long s = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s += 1ull << (lk[i] > f ? lk[i] : f);
+      s = warp_sum(s);
+      if (s <= budget) lf = f;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) lk[i] = lk[i] > lf ? lk[i] : lf;
+  }
+  // layout: classes of decreasing k, bins of one class in increasing index
+  // (index lane + 32 i orders by i, then lane)
+  uint32_t cnt[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) cnt[c] = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cnt[c] += __popc(__ballot_sync(0xffffffffu, lk[i] == (uint32_t)c));
+  uint32_t base[6];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int c = 5; c >= 0; --c) {
+    base[c] = acc;
+    acc += cnt[c] << c;
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t run[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) run[c] = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const unsigned m = __ballot_sync(0xffffffffu, lk[i] == (uint32_t)c);
+      if (lk[i] == (uint32_t)c) {
+        P.off[lane + 32 * i] = (uint16_t)(base[c] + ((run[c] + __popc(m & lt)) << c));
+        P.log2k[lane + 32 * i] = (uint8_t)c;
+      }
+      run[c] += __popc(m);
+    }
+  }
+  if (lane == 0) {
+    P.used = acc;
+    P.budget = budget;
+  }
+  __syncwarp();
+  return r;
+}
+
+}  // namespace histdev
+
+namespace histdev {
+
+// Shared scratch of block_epilogue.
+struct EpiShared {
+  uint32_t wmax[8];     // per-warp largest count
+  uint32_t warg[8];     // per-warp lowest bin holding it
+  uint32_t fsum[8][5];  // per-warp sums of max(k0, 2^f), f = 1..5
+  uint32_t cls[8][6];   // per-warp bins of each sub-bin class
+};
+
+// Degeneracy (Sec. III.C) and binning pattern (rule in hist.h) of the 256-bin
+// histogram `hist` whose total is known to be `total`, by threads 0..255 (one
+// bin each, warp reductions in hardware); all threads of the CTA call (two
+// barriers).  Writes P; returns the degeneracy to threads 0..255.
+static __device__ hist_degeneracy_result block_epilogue(const uint32_t* hist, unsigned long long total,
+                                                        uint32_t budget, uint32_t theta_milli, hist_pattern& P,
+                                                        EpiShared& es) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const bool act = t < HIST_BINS;
+  const unsigned full = 0xffffffffu;
+  const uint32_t h = act ? hist[t] : 0u;
+  uint32_t lk0 = 0;
+  if (act) {
+    if (total == 0) {
+      lk0 = default_lk(t, budget);
+    } else {
+      const unsigned long long spare = budget - HIST_BINS;
+      const float rt = 1.0f / (float)total;
+      const unsigned long long want = 1ull + div_floor(spare * (unsigned long long)h, total, rt);
+      const uint32_t l0 = ilog2_u64(want);
+      lk0 = l0 > 5 ? 5 : l0;
+    }
+  }
+  if (w < 8) {
+    const uint32_t wm = __reduce_max_sync(full, h);
+    const uint32_t wa = __reduce_min_sync(full, h == wm ? (uint32_t)t : 0xffffffffu);
+    uint32_t fs[5];
+#pragma unroll
+    for (int f = 1; f <= 5; ++f) fs[f - 1] = __reduce_add_sync(full, 1u << (lk0 > (uint32_t)f ? lk0 : (uint32_t)f));
+    if (lane == 0) {
+      es.wmax[w] = wm;
+      es.warg[w] = wa;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) es.fsum[w][f] = fs[f];
+    }
+  }
+  __syncthreads();
+  uint32_t lk = lk0;
+  hist_degeneracy_result r;
+  if (act) {
+    uint32_t mx = 0, arg = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mx = es.wmax[i] > mx ? es.wmax[i] : mx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (es.wmax[i] == mx && es.warg[i] < arg) arg = es.warg[i];
+    r.max = mx;
+    r.total = total;
+    r.maxbin = mx == 0 ? 0u : arg;
+    r.flag = reaches_theta(mx, total, theta_milli) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    if (total != 0) {
+      uint32_t lf = 0;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += es.fsum[i][f];
+        if (s <= budget) lf = (uint32_t)f + 1;
+      }
+      lk = lk0 > lf ? lk0 : lf;
+    }
+  }
+  // layout: classes of decreasing k, ties by increasing bin index
+  uint32_t rank = 0;
+  if (w < 8) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const unsigned m = __ballot_sync(full, lk == (uint32_t)c);
+      if (lk == (uint32_t)c) rank = __popc(m & ((1u << lane) - 1u));
+      if (lane == 0) es.cls[w][c] = __popc(m);
+    }
+  }
+  __syncthreads();
+  if (act) {
+    uint32_t base = 0, used = 0, before = 0;
+#pragma unroll
+    for (int c = 5; c >= 0; --c) {
+      uint32_t cnt = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) cnt += es.cls[i][c];
+      if ((uint32_t)c > lk) base += cnt << c;
+      used += cnt << c;
+    }
+    for (int i = 0; i < w; ++i) before += es.cls[i][lk];
+    P.off[t] = (uint16_t)(base + ((before + rank) << lk));
+    P.log2k[t] = (uint8_t)lk;
+    if (t == 0) {
+      P.used = used;
+      P.budget = budget;
+    }
+  }
+  return r;
 }
 
 }  // namespace histdev

@@ -1,14 +1,22 @@
 // hist_stream.cu -- the chunked stream of Sec. III.B with the kernel switch of
 // Sec. III.C, all on the device.
 //
-// One kernel launch per chunk, chained with programmatic dependent launch:
-// chunk i+1's CTAs start while chunk i still runs, zero their tables and pull
-// their slice of chunk i+1 into L2, then wait for chunk i to finish.  Each
-// CTA then sums chunk i's partial histograms (16 replicas in global memory),
-// derives chunk i+1's switch and binning pattern from them (every CTA computes
-// the same values), and CTA 0 folds chunk i into the stream state (totals,
-// last histogram, chunk output).  So chunk i's epilogue runs at the head of
-// chunk i+1, and a finish kernel runs it for the last chunk on flush.
+// A batch of chunks runs in one cooperative launch with one 1024-thread CTA
+// per SM.  For each chunk every CTA
+//   1. waits until the previous chunk's histogram is complete: each CTA adds
+//      its per-bin sums into 4 global replicas, then (after a fence) its pixel
+//      count into one counter word; the histogram is complete exactly when the
+//      counter equals the previous chunk's size.  One thread per CTA polls the
+//      counter (bounded), then the CTA reads the replicas once;
+//   2. derives this chunk's switch and binning pattern from that histogram in
+//      one warp (every CTA computes the same values); CTA 0 folds the previous
+//      chunk into the stream state (totals, last histogram, output);
+//   3. counts its slice of the chunk with the chosen kernel from registers
+//      that were loaded while the previous chunk was still being counted, and
+//      loads the next chunk's slice as it goes;
+//   4. adds its per-bin sums into the chunk's replicas.
+// The last chunk of a batch stays pending: its epilogue runs at the head of
+// the next batch or in the finish kernel (hist_stream_flush).
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -24,9 +32,19 @@ using namespace histlib;
 
 namespace {
 
+constexpr int kWin = 8;              // 16-byte vectors per thread per round (held in registers)
+constexpr int kStreamReplicas = 4;   // global partial histograms per chunk
+constexpr uint32_t kMaxBatch = 128;  // chunks per launch
+constexpr uint32_t kPollLimit = 1u << 22;  // bounded wait: about a second
+constexpr uint32_t kStatusTimeout = 4;     // device status: a wait ran out
+constexpr uint32_t kStatusPattern = 8;     // device status: a layout differed from the rule's pattern
+
 // Device-resident stream state.
 struct StreamDev {
-  uint32_t rep[3][kReplicas][HIST_BINS];  // chunk partials, triple-buffered by launch
+  uint32_t rep[3][kStreamReplicas][HIST_BINS];  // chunk partials, by chunk index mod 3
+  uint32_t cnt[3][32];  // pixels added into rep[i] so far (one 128-byte line each)
+  uint32_t brep[2][kMaxBatch][kStreamReplicas][HIST_BINS];  // decoupled batches: partials per chunk, two sets
+  uint32_t bcnt[2][kMaxBatch][32];
   unsigned long long totals[HIST_BINS];
   uint32_t last_hist[HIST_BINS];
   hist_pattern pattern;       // pattern for the next chunk
@@ -34,22 +52,47 @@ struct StreamDev {
   unsigned long long chunks;  // completed chunks
   uint32_t flag;              // switch computed from the last completed chunk
   uint32_t last_kernel;       // kernel the last completed chunk ran
-  uint32_t status;
+  uint32_t status;            // 0, or kStatusTimeout
+  uint32_t abort;             // set by a CTA whose wait ran out
+};
+
+struct ChunkDesc {
+  const uint8_t* in;
+  uint32_t* out;
+  uint32_t n;
   uint32_t pad;
 };
 
-struct ChunkArgs {
+struct BatchArgs {
   StreamDev* st;
-  const uint8_t* in;
-  size_t n;
-  uint32_t* prev_out;  // output of the pending previous chunk (nullable)
-  uint32_t cur;        // replica buffer this chunk adds into
-  uint32_t prev;       // replica buffer of the pending previous chunk
-  uint32_t has_prev;   // the previous chunk's epilogue runs here
+  uint32_t count;
+  uint32_t has_prev;   // the chunk before this batch is pending: its epilogue runs here
+  uint32_t* prev_out;
+  uint32_t prev_n;
+  uint32_t prev_buf;
+  uint32_t first_buf;  // replica buffer of this batch's first chunk
   uint32_t budget;
   uint32_t theta;
   uint32_t mode;
+  uint32_t trace_first;             // index of this batch's first chunk in the trace
+  unsigned long long* trace;        // optional phase timestamps (see hist_stream_trace)
+  uint32_t trace_cap;               // chunks the trace holds
+  uint32_t pad2;
+  ChunkDesc c[kMaxBatch];
 };
+
+// Phase timestamps (%globaltimer, ns) of chunk j by CTA slot k (0: the first
+// CTA, 1: the middle one, 2: the last one).
+// start, histogram ready, pattern ready, counted (warp 0), counted (all warps),
+// table reduced, published, end
+constexpr int kTracePhases = 8;
+constexpr int kTraceCtas = 3;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t kernel_for(uint32_t mode, uint32_t flag) {
   return mode == HIST_MODE_AUTO ? flag : (mode == HIST_MODE_PLAIN ? HIST_FLAG_PLAIN : HIST_FLAG_ADAPTIVE);
@@ -61,94 +104,138 @@ __device__ __forceinline__ void copy_pattern(hist_pattern* dst, const hist_patte
   for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-// Sum the replicas of buffer `buf` into cs.hist (all threads call; `part` is
-// 1024 words of free shared memory).
-__device__ void gather_partials(const StreamDev* st, uint32_t buf, uint32_t* part, CtaShared& cs) {
-  const int b = threadIdx.x & 255, q = threadIdx.x >> 8;
-  uint32_t s = 0;
-  for (int r = q; r < kReplicas; r += (int)(blockDim.x >> 8)) s += __ldcg(&st->rep[buf][r][b]);
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x < HIST_BINS) {
-    uint32_t t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 8); ++k) t += part[k * HIST_BINS + threadIdx.x];
-    cs.hist[threadIdx.x] = t;
-  }
-  __syncthreads();
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// From the previous chunk's histogram in cs.hist: the next switch and pattern
-// (into cs.flag / cs.pat).  With `writer`, also fold the previous chunk into
-// the stream state.  All threads call.
-__device__ void epilogue(StreamDev* st, uint32_t* prev_out, uint32_t budget, uint32_t theta,
-                         uint32_t mode, bool writer, CtaShared& cs) {
-  const hist_degeneracy_result r =
-      degeneracy_block([&](int b) { return (unsigned long long)cs.hist[b]; }, theta, cs);
-  binning_pattern_block([&](int b) { return cs.hist[b]; }, budget, cs.pat, cs);
+// Wait until the pixels added into buffer `buf` reach n, then leave the
+// histogram in cs.hist.  All threads call.  Returns false if the wait ran out
+// or another CTA aborted (the stream status is set).
+__device__ bool poll_gather(StreamDev* st, const uint32_t* rep, const uint32_t* cnt, uint32_t n, uint32_t* part,
+                            CtaShared& cs, uint32_t* table_to_zero) {
+  const int t = threadIdx.x;
+  if (table_to_zero && t >= 32) {
+    // the other warps clear the counting table while warp 0 waits
+    uint4* t4 = reinterpret_cast<uint4*>(table_to_zero);
+    for (int i = t - 32; i < kTableWords / 4; i += kThreads - 32) t4[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (t == 0) {
+    uint32_t state = 0;
+    for (uint32_t it = 0;; ++it) {
+      if (ld_acquire(cnt) == n) {
+        state = 1;
+        break;
+      }
+      if (it >= kPollLimit) {
+        atomicExch(&st->abort, 1u);
+        atomicExch(&st->status, kStatusTimeout);
+        break;
+      }
+      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
+      __nanosleep(32);
+    }
+    cs.kernel = state;
+  }
+  __syncthreads();
+  if (cs.kernel != 1u) return false;
+  __threadfence();
+  const int b = t & 255, q = t >> 8;  // 1024 threads: one word of the 4 x 256 replicas each
+  part[t] = (q < kStreamReplicas) ? __ldcg(rep + q * HIST_BINS + b) : 0u;
+  __syncthreads();
+  if (t < HIST_BINS) {
+    uint32_t h = 0;
+    for (int r = 0; r < kStreamReplicas; ++r) h += part[r * HIST_BINS + t];
+    cs.hist[t] = h;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Fold the chunk whose histogram is in cs.hist into the stream state.  The
+// work is split over the CTAs: CTA k writes the bins and pattern words whose
+// index is k modulo the CTA count (every CTA holds the same histogram and
+// pattern); CTA 0 writes the scalar fields.  No barrier inside.
+__device__ void write_epilogue(StreamDev* st, uint32_t* out, uint32_t mode, uint32_t flag, const CtaShared& cs,
+                               uint32_t k, uint32_t ctas) {
+  const uint32_t t = threadIdx.x;
+  const uint32_t bin = k + t * ctas;
+  if (bin < HIST_BINS) {
+    const uint32_t h = cs.hist[bin];
+    st->totals[bin] += h;
+    st->last_hist[bin] = h;
+    if (out) out[bin] = h;
+  }
+  constexpr uint32_t words = sizeof(hist_pattern) / 4;
+  const uint32_t wd = k + (t - 256) * ctas;  // threads 256.. copy pattern words
+  if (t >= 256 && wd < words) {
+    uint32_t* cur = reinterpret_cast<uint32_t*>(&st->pattern);
+    uint32_t* last = reinterpret_cast<uint32_t*>(&st->last_pattern);
+    last[wd] = cur[wd];
+    cur[wd] = reinterpret_cast<const uint32_t*>(&cs.pat)[wd];
+  }
+  if (k == 0 && t == 1023) {
+    st->last_kernel = kernel_for(mode, st->flag);
+    st->flag = flag;
+    st->chunks += 1;
+  }
+}
+
+// Switch and pattern for the next chunk from cs.hist (total known), into
+// cs.flag / cs.pat.  All threads call.
+__device__ void epilogue(uint32_t total, uint32_t budget, uint32_t theta, CtaShared& cs, EpiShared& es) {
+  const hist_degeneracy_result r = block_epilogue(cs.hist, total, budget, theta, cs.pat, es);
   if (threadIdx.x == 0) cs.flag = r.flag;
-  if (writer) {
-    const uint32_t old_flag = st->flag;  // every thread reads before thread 0 writes (sync below)
-    copy_pattern(&st->last_pattern, &st->pattern);
-    __syncthreads();
-    copy_pattern(&st->pattern, &cs.pat);
-    if (threadIdx.x < HIST_BINS) {
-      const uint32_t h = cs.hist[threadIdx.x];
-      st->totals[threadIdx.x] += h;
-      st->last_hist[threadIdx.x] = h;
-      if (prev_out) prev_out[threadIdx.x] = h;
-    }
-    if (threadIdx.x == 0) {
-      st->last_kernel = kernel_for(mode, old_flag);
-      st->flag = r.flag;
-      st->chunks += 1;
-    }
-  }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) chunk_kernel(ChunkArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;
-  __shared__ CtaShared cs;
+struct Geo {
+  const uint4* body;
+  uint32_t begin, end;  // this CTA's 16-byte vectors (a chunk is below 2^32 bytes)
+};
 
-  pdl_launch_dependents();
-  // Before the previous chunk has finished: nothing read here depends on it.
-  zero_table(table);
-  const Split sp = split_bytes(a.in, a.n);
-  const uint4* body = reinterpret_cast<const uint4*>(a.in + sp.head);
-  const size_t per = (sp.nvec + gridDim.x - 1) / gridDim.x;
-  const size_t begin = per * blockIdx.x;
-  const size_t end = begin + per < sp.nvec ? begin + per : sp.nvec;
-  if (threadIdx.x == 0 && end > begin) {
-    // bulk L2 prefetch of this CTA's slice, in pieces of at most 1 MiB
-    const uint8_t* p = reinterpret_cast<const uint8_t*>(body + begin);
-    size_t bytes = (end - begin) * 16;
-    while (bytes) {
-      const uint32_t c = bytes > (1u << 20) ? (1u << 20) : (uint32_t)bytes;
-      prefetch_l2(p, c);
-      p += c;
-      bytes -= c;
-    }
-  }
-  pdl_wait();
+__device__ __forceinline__ Geo chunk_geo(const ChunkDesc& d) {
+  const Split sp = split_bytes(d.in, d.n);
+  Geo g;
+  g.body = reinterpret_cast<const uint4*>(d.in + sp.head);
+  const uint32_t nvec = (uint32_t)sp.nvec;
+  const uint32_t per = (nvec + gridDim.x - 1) / gridDim.x;
+  const uint32_t b = per * blockIdx.x;
+  g.end = b + per < nvec ? b + per : nvec;
+  g.begin = b < g.end ? b : g.end;
+  return g;
+}
 
-  StreamDev* st = a.st;
-  if (a.has_prev) {
-    gather_partials(st, a.prev, lut, cs);
-    epilogue(st, a.prev_out, a.budget, a.theta, a.mode, blockIdx.x == 0, cs);
-  } else {
-    copy_pattern(&cs.pat, &st->pattern);
-    if (threadIdx.x == 0) cs.flag = st->flag;
-    __syncthreads();
+// Bulk prefetch of this CTA's slice of chunk d into L2 (thread 0).
+__device__ __forceinline__ void prefetch_slice(const ChunkDesc& d) {
+  if (threadIdx.x != 0) return;
+  const Geo g = chunk_geo(d);
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(g.body + g.begin);
+  size_t bytes = (size_t)(g.end - g.begin) * 16;
+  while (bytes) {
+    const uint32_t c = bytes > (1u << 20) ? (1u << 20) : (uint32_t)bytes;
+    prefetch_l2(p, c);
+    p += c;
+    bytes -= c;
   }
-  if (blockIdx.x == 0) {
-    // the buffer the next chunk adds into; its last reader finished before this launch
-    uint32_t* nb = &st->rep[(a.cur + 1) % 3][0][0];
-    for (int i = threadIdx.x; i < kReplicas * HIST_BINS; i += kThreads) nb[i] = 0;
-  }
-  const uint32_t kern = kernel_for(a.mode, cs.flag);
-  if (kern == HIST_FLAG_ADAPTIVE) {
+}
+
+__device__ __forceinline__ void count_geo(int path, int lk, const Geo& g, uint32_t* table, const uint32_t* lut) {
+  count_dispatch(path, lk, g.body, g.begin, g.end, table, lut);
+}
+
+// Set the CTA's layout for a chunk run by `kernel` with pattern cs.pat.
+__device__ __forceinline__ void set_layout(uint32_t kernel, uint32_t* lut, CtaShared& cs) {
+  if (kernel == HIST_FLAG_ADAPTIVE) {
     classify_pattern(cs.pat, lut, cs);
   } else {
     if (threadIdx.x == 0) {
@@ -157,85 +244,346 @@ __global__ void __launch_bounds__(kThreads, 2) chunk_kernel(ChunkArgs a) {
     }
     __syncthreads();
   }
-  count_dispatch(cs.path, cs.lk, body, begin, end, table, lut);
-  flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
-  if (blockIdx.x == 0) {
-    count_edges(a.in, sp, cs);
-    __syncthreads();
-  }
-  if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x])
-    atomicAdd(&st->rep[a.cur][blockIdx.x % kReplicas][threadIdx.x], cs.res[threadIdx.x]);
 }
 
-// Epilogue of the last pushed chunk (one CTA).
-__global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t prev, uint32_t* prev_out,
+// Reduce the table, add the chunk's edge bytes (CTA 0) and add the per-bin sums
+// into `rep`.  Returns this CTA's pixel count to warp 0.  With `fence`, each
+// adding thread makes its writes visible before the closing barrier.
+__device__ __forceinline__ uint32_t publish_partials(CtaShared& cs, const ChunkDesc& d, uint32_t* table,
+                                                     uint32_t* lut, uint32_t* rep, bool fence) {
+  flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
+  if (blockIdx.x == 0) {
+    count_edges(d.in, split_bytes(d.in, d.n), cs);
+    __syncthreads();
+  }
+  if (threadIdx.x < HIST_BINS) {
+    if (cs.res[threadIdx.x]) atomicAdd(rep + threadIdx.x, cs.res[threadIdx.x]);
+    if (fence) __threadfence();
+  }
+  uint32_t c = 0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < HIST_BINS; i += 32) c += cs.res[i];
+    c = (uint32_t)warp_sum(c);
+  }
+  __syncthreads();
+  return c;
+}
+
+// Synchronised batch: chunk j+1's kernel and pattern come from chunk j's
+// histogram, so every CTA waits for it (see the file comment).
+__global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;
+  __shared__ CtaShared cs;
+  __shared__ EpiShared es;
+  StreamDev* st = a.st;
+  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
+  auto mark = [&](uint32_t j, int phase) {
+    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
+      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
+  };
+
+  prefetch_slice(a.c[0]);
+  zero_table(table);
+  __syncthreads();
+
+  for (uint32_t j = 0; j < a.count; ++j) {
+    const uint32_t buf = (a.first_buf + j) % 3;
+    mark(j, 0);
+    // 1. switch and pattern for chunk j from chunk j-1
+    const bool fold = j > 0 || a.has_prev;  // chunk j-1 is folded into the state in this iteration
+    uint32_t* pout = j == 0 ? a.prev_out : a.c[j - 1].out;
+    if (!fold) {
+      copy_pattern(&cs.pat, &st->pattern);
+      if (threadIdx.x == 0) cs.flag = st->flag;
+      __syncthreads();
+      mark(j, 1);
+    } else {
+      const uint32_t pbuf = j == 0 ? a.prev_buf : (a.first_buf + j - 1) % 3;
+      const uint32_t pn = j == 0 ? a.prev_n : a.c[j - 1].n;
+      if (!poll_gather(st, &st->rep[pbuf][0][0], &st->cnt[pbuf][0], pn, lut, cs, j == 0 ? nullptr : table)) return;
+      mark(j, 1);
+      epilogue(pn, a.budget, a.theta, cs, es);
+    }
+    mark(j, 2);
+    {
+      // chunk j+1's buffer, a slice per CTA; its last readers gathered chunk
+      // j-2 before adding chunk j-1, which every CTA has now seen complete
+      uint32_t* nb = &st->rep[(buf + 1) % 3][0][0];
+      const uint32_t i = blockIdx.x + threadIdx.x * gridDim.x;
+      if (i < kStreamReplicas * HIST_BINS) nb[i] = 0;
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[(buf + 1) % 3][0] = 0;
+    }
+    // 2. layout for the chosen kernel; the next chunk streams into L2 meanwhile
+    set_layout(kernel_for(a.mode, cs.flag), lut, cs);
+    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+    // 3. count this CTA's slice (from L2)
+    count_geo(cs.path, cs.lk, chunk_geo(a.c[j]), table, lut);
+    mark(j, 3);
+    __syncthreads();
+    mark(j, 4);
+    // 4. per-bin sums into the replicas, then the pixel count
+    const uint32_t c = publish_partials(cs, a.c[j], table, lut, &st->rep[buf][blockIdx.x % kStreamReplicas][0], true);
+    mark(j, 5);
+    if (threadIdx.x == 0) red_release_add(&st->cnt[buf][0], c);
+    mark(j, 6);
+    // fold chunk j-1 into the state, off the path the other CTAs wait on
+    if (fold) write_epilogue(st, pout, a.mode, cs.flag, cs, blockIdx.x, gridDim.x);
+    mark(j, 7);
+  }
+}
+
+// Layout the adaptive kernel uses at the full budget after a chunk of n
+// pixels: binning_pattern() of a non-empty histogram is then the full table
+// (the floor reaches 32: 256 x 32 = HIST_BUDGET_MAX), of an empty one the
+// default pattern.
+__device__ void saturated_pattern(uint32_t prev_n, uint32_t budget, CtaShared& cs, EpiShared& es) {
+  if (prev_n) {
+    if (threadIdx.x < HIST_BINS) {
+      cs.pat.off[threadIdx.x] = (uint16_t)(threadIdx.x * HIST_KMAX);
+      cs.pat.log2k[threadIdx.x] = 5;
+    }
+    if (threadIdx.x == 0) {
+      cs.pat.budget = budget;
+      cs.pat.used = HIST_BINS * HIST_KMAX;
+    }
+  } else {
+    if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
+    __syncthreads();
+    block_epilogue(cs.hist, 0, budget, HIST_THETA_MILLI_DEFAULT, cs.pat, es);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_pattern& y) {
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(&x);
+  const uint32_t* b = reinterpret_cast<const uint32_t*>(&y);
+  bool ok = true;
+  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) ok &= a[i] == b[i];
+  return __syncthreads_and(ok);
+}
+
+// Decoupled batch, for the modes in which chunk j+1's kernel and layout do not
+// depend on chunk j's histogram: the plain mode (the plain kernel uses no
+// pattern) and the adaptive mode at the full budget (the pattern rule then
+// gives the full table for every non-empty chunk, the default pattern after
+// an empty one).  Phase 1: the CTAs count the chunks back to back into
+// per-chunk partial buffers (one set per batch, two sets used alternately).
+// Phase 2: chunk k is folded by CTA k mod the CTA count, which computes its
+// switch and pattern from its own histogram, checks that the layout used for
+// chunk k+1 is the one the rule gives (stream status otherwise) and, for the
+// last chunk, writes the stream state.  Such a stream never leaves a chunk
+// pending.
+__global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;
+  __shared__ CtaShared cs;
+  __shared__ EpiShared es;
+  __shared__ uint32_t counts[kMaxBatch];
+  __shared__ hist_pattern used0;  // the pattern chunk 0 was given
+  __shared__ hist_pattern next;   // a pattern computed in phase 2
+  StreamDev* st = a.st;
+  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
+  auto mark = [&](uint32_t j, int phase) {
+    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
+      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
+  };
+  const bool adaptive = a.mode != HIST_MODE_PLAIN;
+  const uint32_t kern = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  const uint32_t set = a.first_buf & 1;  // partial-buffer set of this batch
+
+  prefetch_slice(a.c[0]);
+  zero_table(table);
+  copy_pattern(&cs.pat, &st->pattern);
+  copy_pattern(&used0, &st->pattern);
+  __syncthreads();
+
+  // phase 1: count every chunk
+  for (uint32_t j = 0; j < a.count; ++j) {
+    mark(j, 0);
+    if (j > 0 && adaptive) saturated_pattern(a.c[j - 1].n, a.budget, cs, es);
+    set_layout(kern, lut, cs);
+    mark(j, 2);
+    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+    count_geo(cs.path, cs.lk, chunk_geo(a.c[j]), table, lut);
+    mark(j, 3);
+    __syncthreads();
+    mark(j, 4);
+    const uint32_t c =
+        publish_partials(cs, a.c[j], table, lut, &st->brep[set][j][blockIdx.x % kStreamReplicas][0], false);
+    if (threadIdx.x == 0) counts[j] = c;
+    mark(j, 5);
+    zero_table(table);
+    __syncthreads();
+    mark(j, 7);
+  }
+  // publish every chunk count after one fence
+  __threadfence();
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < a.count; j += kThreads)
+    if (counts[j]) red_release_add(&st->bcnt[set][j][0], counts[j]);
+
+  // clear the other set (the previous batch's), a slice per CTA
+  for (uint32_t b = blockIdx.x; b < kMaxBatch; b += gridDim.x) {
+    uint32_t* r = &st->brep[set ^ 1][b][0][0];
+    for (int w = threadIdx.x; w < kStreamReplicas * HIST_BINS; w += kThreads) r[w] = 0;
+    if (threadIdx.x == 0) st->bcnt[set ^ 1][b][0] = 0;
+  }
+
+  // phase 2: fold chunk k in CTA k mod the CTA count
+  for (uint32_t k = blockIdx.x; k < a.count; k += gridDim.x) {
+    const uint32_t n = a.c[k].n;
+    if (!poll_gather(st, &st->brep[set][k][0][0], &st->bcnt[set][k][0], n, lut, cs, nullptr)) return;
+    const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
+    if (threadIdx.x == 0) cs.flag = r.flag;
+    __syncthreads();
+    if (threadIdx.x < HIST_BINS) {
+      const uint32_t h = cs.hist[threadIdx.x];
+      if (a.c[k].out) a.c[k].out[threadIdx.x] = h;
+      if (h) atomicAdd(&st->totals[threadIdx.x], (unsigned long long)h);
+      if (k + 1 == a.count) st->last_hist[threadIdx.x] = h;
+    }
+    if (adaptive && k + 1 < a.count) {
+      // the layout chunk k+1 counted with must be binning_pattern(chunk k)
+      saturated_pattern(n, a.budget, cs, es);
+      if (!same_pattern(next, cs.pat) && threadIdx.x == 0) atomicExch(&st->status, kStatusPattern);
+    }
+    if (k + 1 == a.count) {
+      // last chunk: the pattern it was given, then the state
+      if (k == 0) {
+        copy_pattern(&cs.pat, &used0);
+      } else if (adaptive) {
+        saturated_pattern(a.c[k - 1].n, a.budget, cs, es);
+      } else {
+        // plain mode records binning_pattern(chunk k-1) as chunk k's pattern
+        if (!poll_gather(st, &st->brep[set][k - 1][0][0], &st->bcnt[set][k - 1][0], a.c[k - 1].n, lut, cs, nullptr))
+          return;
+        block_epilogue(cs.hist, a.c[k - 1].n, a.budget, a.theta, cs.pat, es);
+      }
+      __syncthreads();
+      copy_pattern(&st->last_pattern, &cs.pat);
+      copy_pattern(&st->pattern, &next);
+      if (threadIdx.x == 0) {
+        st->last_kernel = kern;
+        st->flag = r.flag;
+        st->chunks += a.count;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Epilogue of the last pushed chunk (one CTA of 1024 threads).
+__global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t* out,
                                                           uint32_t budget, uint32_t theta, uint32_t mode) {
   __shared__ uint32_t part[kThreads];
   __shared__ CtaShared cs;
-  gather_partials(st, prev, part, cs);
-  epilogue(st, prev_out, budget, theta, mode, true, cs);
+  __shared__ EpiShared es;
+  if (!poll_gather(st, &st->rep[buf][0][0], &st->cnt[buf][0], n, part, cs, nullptr)) return;
+  epilogue(n, budget, theta, cs, es);
+  write_epilogue(st, out, mode, cs.flag, cs, 0, 1);
 }
 
 __global__ void init_kernel(StreamDev* st, uint32_t budget) {
   __shared__ CtaShared cs;
-  default_pattern_block(budget, cs.pat, cs);
+  __shared__ uint32_t zero[HIST_BINS];
+  for (int i = threadIdx.x; i < HIST_BINS; i += blockDim.x) zero[i] = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) warp_epilogue(zero, budget, HIST_THETA_MILLI_DEFAULT, cs.pat);
+  __syncthreads();
   copy_pattern(&st->pattern, &cs.pat);
   copy_pattern(&st->last_pattern, &cs.pat);
 }
 
 }  // namespace
 
+constexpr uint32_t kMaxStaging = 4;
+
 struct hist_stream {
   hist_config cfg;
   StreamDev* d;
   int sms;
   int grid;
-  unsigned long long launches;
+  unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
+  unsigned long long decoupled_launches;  // decoupled batches -> partial-buffer set (parity)
+  bool decoupled;
   bool pending;
   uint32_t* pending_out;
+  uint32_t pending_n;
+  uint32_t pending_buf;
+  // tracing (optional)
+  unsigned long long* trace;
+  uint32_t trace_cap;
+  uint32_t trace_next;
+  // host-fed staging (optional)
+  uint32_t depth;
+  size_t max_chunk;
+  uint8_t* staging[kMaxStaging];
+  cudaEvent_t copied[kMaxStaging];
+  cudaEvent_t consumed[kMaxStaging];
+  cudaStream_t copy_stream;
+  unsigned long long host_pushes;
 };
 
 namespace {
 
-int launch_chunk(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t* d_out, cudaStream_t s) {
-  static int attr_done[kMaxDevices];
-  int rc = ensure_smem_attr((const void*)chunk_kernel, attr_done);
-  if (rc) return rc;
-  ChunkArgs a;
-  a.st = st->d;
-  a.in = d_chunk;
-  a.n = n;
-  a.prev_out = st->pending_out;
-  a.cur = (uint32_t)(st->launches % 3);
-  a.prev = (uint32_t)((st->launches + 2) % 3);
-  a.has_prev = st->pending ? 1u : 0u;
-  a.budget = st->cfg.budget;
-  a.theta = st->cfg.theta_milli;
-  a.mode = st->cfg.mode;
-
-  cudaLaunchConfig_t lc;
-  memset(&lc, 0, sizeof(lc));
-  lc.gridDim = dim3((unsigned)st->grid);
-  lc.blockDim = dim3(kThreads);
-  lc.dynamicSmemBytes = kSmemBytes;
-  lc.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  lc.attrs = attr;
-  lc.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&lc, chunk_kernel, a);
+int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, const size_t* ns, uint32_t* const* outs,
+                 cudaStream_t s) {
+  BatchArgs* a = (BatchArgs*)calloc(1, sizeof(BatchArgs));
+  if (!a) return HIST_ENOMEM;
+  a->st = st->d;
+  a->count = count;
+  a->has_prev = st->pending ? 1u : 0u;
+  a->prev_out = st->pending_out;
+  a->prev_n = st->pending_n;
+  a->prev_buf = st->pending_buf;
+  a->first_buf = st->decoupled ? (uint32_t)(st->decoupled_launches & 1) : (uint32_t)(st->chunks_launched % 3);
+  a->budget = st->cfg.budget;
+  a->theta = st->cfg.theta_milli;
+  a->mode = st->cfg.mode;
+  a->trace = st->trace;
+  a->trace_cap = st->trace_cap;
+  a->trace_first = st->trace_next;
+  for (uint32_t i = 0; i < count; ++i) {
+    a->c[i].in = ins[i];
+    a->c[i].n = (uint32_t)ns[i];
+    a->c[i].out = outs ? outs[i] : nullptr;
+  }
+  void* params[] = {a};
+  const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)st->grid), dim3(kThreads), params, kSmemBytes, s);
+  free(a);
   if (e != cudaSuccess) return cuda_fail(e);
-  st->launches += 1;
-  st->pending = true;
-  st->pending_out = d_out;
+  if (st->decoupled) {
+    st->decoupled_launches += 1;
+  } else {
+    const uint32_t last = count - 1;
+    st->pending = true;
+    st->pending_out = outs ? outs[last] : nullptr;
+    st->pending_n = (uint32_t)ns[last];
+    st->pending_buf = (uint32_t)((st->chunks_launched + last) % 3);
+  }
+  st->chunks_launched += count;
+  if (st->trace) st->trace_next += count;
+  return HIST_OK;
+}
+
+int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, const size_t* ns, uint32_t* const* outs,
+                cudaStream_t s) {
+  for (uint32_t i = 0; i < count; i += kMaxBatch) {
+    const uint32_t c = count - i < kMaxBatch ? count - i : kMaxBatch;
+    int rc = launch_batch(st, c, ins + i, ns + i, outs ? outs + i : nullptr, s);
+    if (rc) return rc;
+  }
   return HIST_OK;
 }
 
 int do_flush(hist_stream* st, cudaStream_t s) {
   if (!st->pending) return HIST_OK;
-  finish_kernel<<<1, kThreads, 0, s>>>(st->d, (uint32_t)((st->launches + 2) % 3), st->pending_out,
-                                       st->cfg.budget, st->cfg.theta_milli, st->cfg.mode);
+  finish_kernel<<<1, kThreads, 0, s>>>(st->d, st->pending_buf, st->pending_n, st->pending_out, st->cfg.budget,
+                                       st->cfg.theta_milli, st->cfg.mode);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);
   st->pending = false;
@@ -246,6 +594,30 @@ int do_flush(hist_stream* st, cudaStream_t s) {
 bool config_ok(const hist_config* c) {
   return c && c->budget >= HIST_BUDGET_MIN && c->budget <= HIST_BUDGET_MAX && c->theta_milli <= 1000 &&
          c->mode <= HIST_MODE_ADAPTIVE;
+}
+
+int grid_for(const hist_config* cfg, int sms, const void* fn) {
+  // at most the CTAs that can be resident at once: a cooperative launch needs them all
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kSmemBytes) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int cap = per_sm * sms;
+  const int g = cfg->grid ? (int)cfg->grid : sms;
+  return g > cap ? cap : g;
+}
+
+void release_staging(hist_stream* st) {
+  for (uint32_t i = 0; i < kMaxStaging; ++i) {
+    if (st->staging[i]) cudaFree(st->staging[i]);
+    if (st->copied[i]) cudaEventDestroy(st->copied[i]);
+    if (st->consumed[i]) cudaEventDestroy(st->consumed[i]);
+    st->staging[i] = nullptr;
+    st->copied[i] = st->consumed[i] = nullptr;
+  }
+  if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
+  st->copy_stream = nullptr;
+  st->depth = 0;
+  st->max_chunk = 0;
 }
 
 }  // namespace
@@ -268,7 +640,16 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   if (!st) return HIST_ENOMEM;
   st->cfg = *cfg;
   st->sms = sm_count();
-  st->grid = cfg->grid ? (int)cfg->grid : st->sms;
+  // modes whose chunk layouts never depend on the previous chunk's histogram
+  st->decoupled = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
+  const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
+  static int attr_sync[kMaxDevices], attr_dec[kMaxDevices];
+  int rc = ensure_smem_attr(fn, st->decoupled ? attr_dec : attr_sync);
+  if (rc) {
+    free(st);
+    return rc;
+  }
+  st->grid = grid_for(cfg, st->sms, fn);
   cudaError_t e = cudaMalloc((void**)&st->d, sizeof(StreamDev));
   if (e != cudaSuccess) {
     free(st);
@@ -292,6 +673,7 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
 int hist_stream_destroy(hist_stream* st) {
   if (!st) return HIST_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();
+  release_staging(st);
   cudaFree(st->d);
   free(st);
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
@@ -300,7 +682,7 @@ int hist_stream_destroy(hist_stream* st) {
 int hist_stream_push(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t* d_chunk_out,
                      hist_cuda_stream s) {
   if (!st || (!d_chunk && n) || n >= ((size_t)1 << 32)) return HIST_EINVAL;
-  return launch_chunk(st, d_chunk, n, d_chunk_out, (cudaStream_t)s);
+  return push_chunks(st, 1, &d_chunk, &n, d_chunk_out ? &d_chunk_out : nullptr, (cudaStream_t)s);
 }
 
 int hist_stream_push_many(hist_stream* st, uint32_t count, const uint8_t* const* d_chunks, const size_t* sizes,
@@ -308,10 +690,57 @@ int hist_stream_push_many(hist_stream* st, uint32_t count, const uint8_t* const*
   if (!st || (count && (!d_chunks || !sizes))) return HIST_EINVAL;
   for (uint32_t i = 0; i < count; ++i)
     if ((!d_chunks[i] && sizes[i]) || sizes[i] >= ((size_t)1 << 32)) return HIST_EINVAL;
-  for (uint32_t i = 0; i < count; ++i) {
-    int rc = launch_chunk(st, d_chunks[i], sizes[i], d_chunk_outs ? d_chunk_outs[i] : nullptr, (cudaStream_t)s);
-    if (rc) return rc;
+  if (count == 0) return HIST_OK;
+  return push_chunks(st, count, d_chunks, sizes, d_chunk_outs, (cudaStream_t)s);
+}
+
+int hist_stream_attach_staging(hist_stream* st, size_t max_chunk, uint32_t depth) {
+  if (!st || max_chunk == 0 || max_chunk >= ((size_t)1 << 32) || depth < 2 || depth > kMaxStaging)
+    return HIST_EINVAL;
+  if (st->depth) return HIST_ESTATE;
+  cudaError_t e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking);
+  for (uint32_t i = 0; e == cudaSuccess && i < depth; ++i) {
+    e = cudaMalloc((void**)&st->staging[i], max_chunk);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->consumed[i], cudaEventDisableTiming);
   }
+  if (e != cudaSuccess) {
+    release_staging(st);
+    return e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e);
+  }
+  st->depth = depth;
+  st->max_chunk = max_chunk;
+  st->host_pushes = 0;
+  return HIST_OK;
+}
+
+int hist_stream_push_host(hist_stream* st, const uint8_t* h_chunk, size_t n, uint32_t* d_chunk_out,
+                          hist_cuda_stream s) {
+  if (!st || (!h_chunk && n)) return HIST_EINVAL;
+  if (!st->depth) return HIST_ESTATE;
+  if (n > st->max_chunk) return HIST_EINVAL;
+  const uint32_t b = (uint32_t)(st->host_pushes % st->depth);
+  cudaStream_t cs = st->copy_stream;
+  // the buffer's previous chunk kernel must be done before it is overwritten
+  cudaError_t e = cudaStreamWaitEvent(cs, st->consumed[b], 0);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(st->staging[b], h_chunk, n, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(st->copied[b], cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)s, st->copied[b], 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const uint8_t* in = st->staging[b];
+  int rc = push_chunks(st, 1, &in, &n, d_chunk_out ? &d_chunk_out : nullptr, (cudaStream_t)s);
+  if (rc) return rc;
+  e = cudaEventRecord(st->consumed[b], (cudaStream_t)s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  st->host_pushes += 1;
+  return HIST_OK;
+}
+
+int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chunks) {
+  if (!st || (d_trace && capacity_chunks == 0)) return HIST_EINVAL;
+  st->trace = reinterpret_cast<unsigned long long*>(d_trace);
+  st->trace_cap = d_trace ? capacity_chunks : 0;
+  st->trace_next = 0;
   return HIST_OK;
 }
 
@@ -371,7 +800,6 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h, hist_cuda
   tmp->chunks = h->chunks;
   tmp->flag = h->flag;
   tmp->last_kernel = h->last_kernel;
-  tmp->status = 0;
   cudaError_t e = cudaMemcpyAsync(st->d, tmp, sizeof(StreamDev), cudaMemcpyHostToDevice, (cudaStream_t)s);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)s);
   free(tmp);
