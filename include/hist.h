@@ -244,6 +244,37 @@ int hist_stream_get_state(hist_stream* st, hist_stream_state* h_state, hist_cuda
  * HIST_EINVAL if the state's patterns are invalid for this stream's budget. */
 int hist_stream_set_state(hist_stream* st, const hist_stream_state* h_state, hist_cuda_stream s);
 
+/* ------------------------------------------------ stream without allocation -- */
+/* The paper has no counterpart of this call: it serves callers that cannot
+ * allocate device memory where they need histograms -- code running while a
+ * CUDA graph is being captured, real-time loops in which a cudaMalloc would
+ * stall on a device-wide synchronisation, and hosts whose device memory
+ * belongs to another allocator that must see every allocation.
+ *
+ * Runs a fresh stream (first chunk plain with default_pattern(cfg->budget),
+ * then the switch and pattern of every chunk from the previous one, as
+ * hist_stream_push does) over `count` chunks and writes, in order on `s`:
+ *   d_chunk_outs  optional, count x uint32_t[256]: each chunk's histogram;
+ *   d_totals      uint64_t[256]: the sum of the chunk histograms (overwritten);
+ *   d_status      optional uint32_t: 0, or 4 if a bounded device wait ran out.
+ * d_chunks / sizes are host arrays of `count` device pointers and sizes; each
+ * size is below 2^32, and count is 1..HIST_NOALLOC_MAX_CHUNKS (more ->
+ * HIST_EINVAL).  cfg->grid is ignored.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * -- the partial sums of three chunks in flight and their counters, about
+ * 12.5 KiB -- is one fixed device array in the library, held by every GPU
+ * that loads the library until the process exits, and cleared at the start of
+ * every call.  The first call on a device looks up that array's device
+ * address and sets the kernel up; make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (on different streams, or from several threads) race and give wrong
+ * results; run them in order on one stream. */
+#define HIST_NOALLOC_MAX_CHUNKS 128u
+int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes, uint32_t count,
+                            const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals,
+                            uint32_t* d_status, hist_cuda_stream s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,8 @@ ECUDA = -5
 EBUSY = -6
 ESTATE = -7
 
+HIST_NOALLOC_MAX_CHUNKS = 128
+
 
 class HistPattern(ctypes.Structure):
     _fields_ = [
@@ -100,6 +102,7 @@ SIGNATURES = [
     ("hist_stream_totals", _I, [_P, _P, _P]),
     ("hist_stream_get_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_set_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
+    ("hist_stream_run_noalloc", _I, [_P, _P, _U32, ctypes.POINTER(HistConfig), _P, _P, _P, _P]),
 ]
 
 _lib = None
