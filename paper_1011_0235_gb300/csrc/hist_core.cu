@@ -93,14 +93,17 @@ int sm_count() {
   return sms;
 }
 
-int ensure_smem_attr(const void* fn, int* done) {
-  // Kernels using kSmemBytes of dynamic shared memory need the opt-in, once per
-  // (kernel, device); `done` is the caller's per-kernel array of kMaxDevices.
+int ensure_smem_attr(const void* fn, int* done) { return ensure_smem_attr_bytes(fn, done, kSmemBytes); }
+
+int ensure_smem_attr_bytes(const void* fn, int* done, size_t bytes) {
+  // Kernels using more than 48 KiB of dynamic shared memory need the opt-in,
+  // once per (kernel, device); `done` is the caller's per-kernel array of
+  // kMaxDevices.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
   if (dev >= 0 && dev < kMaxDevices && done[dev]) return HIST_OK;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return cuda_fail(e);
   if (dev >= 0 && dev < kMaxDevices) done[dev] = 1;
   return HIST_OK;

@@ -107,21 +107,49 @@ __device__ __forceinline__ void thread_bases(const uint32_t* table, const uint32
   lutb = smem_addr(lut) + (lane << 2);
 }
 
-// Count the 16-byte vectors [begin, end) of p, this CTA's slice: thread t takes
-// vectors begin + t, begin + t + kThreads, ... (coalesced), two loads in flight.
+// Count the 16-byte vectors [begin, end) of p with threads 0..nthr-1 of the
+// CTA: thread tid takes vectors begin + tid, begin + tid + nthr, ...
+// (coalesced), UNROLL loads in flight.
+template <int PATH, int LK, int UNROLL>
+static __device__ void count_range(const uint4* __restrict__ p, size_t begin, size_t end, uint32_t* table,
+                                   const uint32_t* lut, int tid, int nthr) {
+  uint32_t base, lutb, tab;
+  thread_bases<PATH, LK>(table, lut, base, lutb, tab);
+  size_t i = begin + tid;
+  for (; i + (size_t)(UNROLL - 1) * nthr < end; i += (size_t)UNROLL * nthr) {
+    uint4 v[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) v[u] = ldg_stream(p + i + (size_t)u * nthr);
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) count_vec<PATH, LK>(v[u], base, lutb, tab);
+  }
+  for (; i < end; i += nthr) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, tab);
+}
+
+// The whole CTA, two loads in flight.
 template <int PATH, int LK>
 static __device__ void count_slice(const uint4* __restrict__ p, size_t begin, size_t end, uint32_t* table,
                                    const uint32_t* lut) {
-  uint32_t base, lutb, tab;
-  thread_bases<PATH, LK>(table, lut, base, lutb, tab);
-  size_t i = begin + threadIdx.x;
-  for (; i + kThreads < end; i += 2 * kThreads) {
-    const uint4 a = ldg_stream(p + i);
-    const uint4 b = ldg_stream(p + i + kThreads);
-    count_vec<PATH, LK>(a, base, lutb, tab);
-    count_vec<PATH, LK>(b, base, lutb, tab);
+  count_range<PATH, LK, 2>(p, begin, end, table, lut, threadIdx.x, kThreads);
+}
+
+// Layout dispatch for count_range.
+template <int UNROLL>
+__device__ __forceinline__ void count_range_dispatch(int path, int lk, const uint4* p, size_t begin, size_t end,
+                                                     uint32_t* table, const uint32_t* lut, int tid, int nthr) {
+  if (begin >= end) return;
+  if (path == PATH_PLAIN) count_range<PATH_PLAIN, 0, UNROLL>(p, begin, end, table, lut, tid, nthr);
+  else if (path == PATH_LUT) count_range<PATH_LUT, 0, UNROLL>(p, begin, end, table, lut, tid, nthr);
+  else {
+    switch (lk) {
+      case 5: count_range<PATH_SHIFT, 5, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+      case 4: count_range<PATH_SHIFT, 4, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+      case 3: count_range<PATH_SHIFT, 3, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+      case 2: count_range<PATH_SHIFT, 2, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+      case 1: count_range<PATH_SHIFT, 1, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+      default: count_range<PATH_SHIFT, 0, UNROLL>(p, begin, end, table, lut, tid, nthr); break;
+    }
   }
-  if (i < end) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, tab);
 }
 
 __device__ __forceinline__ void count_dispatch(int path, int lk, const uint4* p, size_t begin,
@@ -409,7 +437,7 @@ struct EpiShared {
 // histogram `hist` whose total is known to be `total`, by threads 0..255 (one
 // bin each, warp reductions in hardware); all threads of the CTA call (two
 // barriers).  Writes P; returns the degeneracy to threads 0..255.
-static __device__ hist_degeneracy_result block_epilogue(const uint32_t* hist, unsigned long long total,
+static __device__ __noinline__ hist_degeneracy_result block_epilogue(const uint32_t* hist, unsigned long long total,
                                                         uint32_t budget, uint32_t theta_milli, hist_pattern& P,
                                                         EpiShared& es) {
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;

@@ -16,6 +16,7 @@ int cuda_fail(cudaError_t e);
 int sm_count();
 // Opt a kernel into the library's dynamic shared-memory size on this device.
 int ensure_smem_attr(const void* fn, int* done);
+int ensure_smem_attr_bytes(const void* fn, int* done, size_t bytes);
 // The one-shot histogram (hist_plain / hist_adaptive).
 int oneshot(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t* d_out, cudaStream_t s);
 

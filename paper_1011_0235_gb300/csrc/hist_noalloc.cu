@@ -35,10 +35,13 @@ constexpr uint32_t kNaPollLimit = 1u << 22;  // bounded wait: about a second
 constexpr uint32_t kNaStatusTimeout = 4;
 
 // Partial sums of the three chunks in flight (chunk j uses buffer j mod 3)
-// and the pixel counters that say when a chunk's sums are complete.
+// and their counters: CTAs that published (high 32 bits) and their pixels
+// (low 32 bits).  A chunk is complete when every CTA has published and the
+// pixels equal its size; the arrivals make sure that a CTA with no pixels is
+// also past the steps before its publication.
 struct NoAllocScratch {
   uint32_t rep[3][kNaReplicas][HIST_BINS];
-  uint32_t cnt[3][32];
+  unsigned long long cnt[3][16];
   uint32_t abort;
   uint32_t status;
 };
@@ -67,9 +70,9 @@ __device__ __forceinline__ uint32_t na_kernel_for(uint32_t mode, uint32_t flag) 
   return mode == HIST_MODE_AUTO ? flag : (mode == HIST_MODE_PLAIN ? HIST_FLAG_PLAIN : HIST_FLAG_ADAPTIVE);
 }
 
-__device__ __forceinline__ uint32_t na_ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long na_ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint32_t na_ld_relaxed(const uint32_t* p) {
@@ -108,7 +111,8 @@ __device__ __forceinline__ void na_prefetch(const NaChunk& d) {
   }
 }
 
-// Wait (bounded) until chunk buffer b holds n pixels, then sum its replicas
+// Wait (bounded) until every CTA has published chunk buffer b and it holds n
+// pixels, then sum its replicas
 // into cs.hist.  All threads call.
 __device__ bool na_gather(NoAllocScratch* sc, uint32_t* status_out, uint32_t b, uint32_t n, uint32_t* part,
                           CtaShared& cs) {
@@ -116,7 +120,7 @@ __device__ bool na_gather(NoAllocScratch* sc, uint32_t* status_out, uint32_t b, 
   if (t == 0) {
     uint32_t state = 0;
     for (uint32_t it = 0;; ++it) {
-      if (na_ld_acquire(&sc->cnt[b][0]) == n) {
+      if (na_ld_acquire(&sc->cnt[b][0]) == (((unsigned long long)gridDim.x << 32) | n)) {
         state = 1;
         break;
       }
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) noalloc_stream_kernel(const __gri
       c = (uint32_t)warp_sum(c);
     }
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&sc->cnt[b][0], c);
+    if (threadIdx.x == 0) atomicAdd(&sc->cnt[b][0], (1ull << 32) | c);
   }
   // the last chunk
   const uint32_t last = a.count - 1;

@@ -4,10 +4,12 @@
 // A batch of chunks runs in one cooperative launch with one 1024-thread CTA
 // per SM.  For each chunk every CTA
 //   1. waits until the previous chunk's histogram is complete: each CTA adds
-//      its per-bin sums into 4 global replicas, then (after a fence) its pixel
-//      count into one counter word; the histogram is complete exactly when the
-//      counter equals the previous chunk's size.  One thread per CTA polls the
-//      counter (bounded), then the CTA reads the replicas once;
+//      its per-bin sums into 4 global replicas, then (after a fence) one
+//      arrival and its pixel count into one 64-bit counter; the chunk is
+//      complete when every CTA has arrived and the pixels equal the chunk's
+//      size (the arrivals matter: a CTA with no pixels must also be past its
+//      earlier steps).  One thread per CTA polls the counter (bounded), then
+//      the CTA reads the replicas once;
 //   2. derives this chunk's switch and binning pattern from that histogram in
 //      one warp (every CTA computes the same values); CTA 0 folds the previous
 //      chunk into the stream state (totals, last histogram, output);
@@ -42,9 +44,11 @@ constexpr uint32_t kStatusPattern = 8;     // device status: a layout differed f
 // Device-resident stream state.
 struct StreamDev {
   uint32_t rep[3][kStreamReplicas][HIST_BINS];  // chunk partials, by chunk index mod 3
-  uint32_t cnt[3][32];  // pixels added into rep[i] so far (one 128-byte line each)
+  // CTAs that published into rep[i] (high 32 bits) and their pixels (low 32
+  // bits), one 128-byte line each
+  unsigned long long cnt[3][16];
   uint32_t brep[2][kMaxBatch][kStreamReplicas][HIST_BINS];  // decoupled batches: partials per chunk, two sets
-  uint32_t bcnt[2][kMaxBatch][32];
+  unsigned long long bcnt[2][kMaxBatch][16];                 // decoupled: pixels published per chunk
   unsigned long long totals[HIST_BINS];
   uint32_t last_hist[HIST_BINS];
   hist_pattern pattern;       // pattern for the next chunk
@@ -109,20 +113,24 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// Counter value of a complete chunk: `ctas` arrivals and n pixels.
+__device__ __forceinline__ unsigned long long complete_count(uint32_t ctas, uint32_t n) {
+  return ((unsigned long long)ctas << 32) | n;
+}
 
-// Wait until the pixels added into buffer `buf` reach n, then leave the
-// histogram in cs.hist.  All threads call.  Returns false if the wait ran out
-// or another CTA aborted (the stream status is set).
-__device__ bool poll_gather(StreamDev* st, const uint32_t* rep, const uint32_t* cnt, uint32_t n, uint32_t* part,
-                            CtaShared& cs, uint32_t* table_to_zero) {
+// Wait until counter `cnt` reaches `target`, then sum the replicas `rep` into
+// cs.hist.  All threads call.  Returns false if the wait ran out or another
+// CTA aborted (the stream status is set).
+__device__ bool poll_gather(StreamDev* st, const uint32_t* rep, const unsigned long long* cnt,
+                            unsigned long long target, uint32_t* part, CtaShared& cs, uint32_t* table_to_zero) {
   const int t = threadIdx.x;
   if (table_to_zero && t >= 32) {
     // the other warps clear the counting table while warp 0 waits
@@ -132,7 +140,7 @@ __device__ bool poll_gather(StreamDev* st, const uint32_t* rep, const uint32_t* 
   if (t == 0) {
     uint32_t state = 0;
     for (uint32_t it = 0;; ++it) {
-      if (ld_acquire(cnt) == n) {
+      if (ld_acquire(cnt) == target) {
         state = 1;
         break;
       }
@@ -302,7 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_
     } else {
       const uint32_t pbuf = j == 0 ? a.prev_buf : (a.first_buf + j - 1) % 3;
       const uint32_t pn = j == 0 ? a.prev_n : a.c[j - 1].n;
-      if (!poll_gather(st, &st->rep[pbuf][0][0], &st->cnt[pbuf][0], pn, lut, cs, j == 0 ? nullptr : table)) return;
+      if (!poll_gather(st, &st->rep[pbuf][0][0], &st->cnt[pbuf][0], complete_count(gridDim.x, pn), lut, cs,
+                       j == 0 ? nullptr : table))
+        return;
       mark(j, 1);
       epilogue(pn, a.budget, a.theta, cs, es);
     }
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_
     // 4. per-bin sums into the replicas, then the pixel count
     const uint32_t c = publish_partials(cs, a.c[j], table, lut, &st->rep[buf][blockIdx.x % kStreamReplicas][0], true);
     mark(j, 5);
-    if (threadIdx.x == 0) red_release_add(&st->cnt[buf][0], c);
+    if (threadIdx.x == 0) red_release_add(&st->cnt[buf][0], complete_count(1, c));
     mark(j, 6);
     // fold chunk j-1 into the state, off the path the other CTAs wait on
     if (fold) write_epilogue(st, pout, a.mode, cs.flag, cs, blockIdx.x, gridDim.x);
@@ -364,12 +374,146 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
   return __syncthreads_and(ok);
 }
 
+// Named barriers of the decoupled kernel (0 is __syncthreads).
+constexpr int kBarFull = 1;   // +p: table p holds a counted chunk (counting warps arrive, flush warp waits)
+constexpr int kBarFree = 3;   // +p: table p is clear again (flush warp arrives, counting warps wait)
+constexpr int kBarCount = 5;  // the counting warps among themselves
+constexpr int kCountThreads = kThreads - 32;  // warps 0..30 count, warp 31 flushes
+constexpr size_t kDecSmemBytes = (size_t)(2 * kTableWords + kLutWords) * 4;  // two tables + slot table
+
+__device__ __forceinline__ void nbar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void nbar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// One warp sums table `t` per bin: lane l gets bins l + 32 i in sum[i].  The
+// layout is PLAIN (nwarps per-warp tables), SHIFT (bin b owns the 2^lk slots
+// from b << lk) or a general pattern P.  For SHIFT each lane reads its own
+// rows in 16-byte pieces, rotated by the lane so that the 8 lanes of each
+// shared-memory phase touch 8 different bank quads.
+__device__ __noinline__ void warp_flush(const uint32_t* t, int path, int lk, const hist_pattern& P, int nwarps,
+                                        uint32_t* sum) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < 8; ++i) sum[i] = 0;
+  if (path == PATH_PLAIN) {
+    for (int i = 0; i < 8; ++i) {
+      uint32_t s = 0;
+      for (int w = 0; w < nwarps; ++w) s += t[w * HIST_BINS + lane + 32 * i];
+      sum[i] = s;
+    }
+  } else if (path == PATH_SHIFT) {
+    const int K = 1 << lk;
+    for (int i = 0; i < 8; ++i) {
+      const int b = lane + 32 * i;
+      const uint32_t* row = t + (b << lk);
+      uint32_t s = 0;
+      if (K >= 4) {
+        const int pieces = K >> 2;
+        const uint4* r4 = reinterpret_cast<const uint4*>(row);
+        for (int q = 0; q < pieces; ++q) {
+          const uint4 v = r4[(q + lane) & (pieces - 1)];
+          s += v.x + v.y + v.z + v.w;
+        }
+      } else {
+        for (int j = 0; j < K; ++j) s += row[j];
+      }
+      sum[i] = s;
+    }
+  } else {
+    for (int i = 0; i < 8; ++i) {
+      const int b = lane + 32 * i;
+      const uint32_t l2 = P.log2k[b] > 5 ? 5u : P.log2k[b];
+      const uint32_t o = P.off[b];
+      uint32_t s = 0;
+      for (uint32_t j = 0; j < (1u << l2); ++j) s += t[(o + j) & (kTableWords - 1)];
+      sum[i] = s;
+    }
+  }
+}
+
+// General layout of a decoupled chunk (chunk 0: the stream's current pattern;
+// after an empty chunk: the default pattern), rare.  Every counting thread
+// calls; builds the slot table if the pattern needs one.
+__device__ __noinline__ void dec_layout_general(const BatchArgs& a, uint32_t j, const hist_pattern& used0,
+                                                hist_pattern& pat, int* path_lk, uint32_t* lut, int* lut_owner,
+                                                CtaShared& cs) {
+  const int t = threadIdx.x;
+  nbar_sync(kBarCount, kCountThreads);
+  if (j == 0) {
+    for (int i = t; i < (int)(sizeof(hist_pattern) / 4); i += kCountThreads)
+      reinterpret_cast<uint32_t*>(&pat)[i] = reinterpret_cast<const uint32_t*>(&used0)[i];
+  } else {
+    // default pattern: the rule on an empty histogram
+    for (int i = t; i < HIST_BINS; i += kCountThreads) cs.hist[i] = 0;
+    nbar_sync(kBarCount, kCountThreads);
+    if (t < 32) warp_epilogue(cs.hist, a.budget, a.theta, pat);
+  }
+  nbar_sync(kBarCount, kCountThreads);
+  const int lane = t & 31;
+  const uint32_t lk0 = pat.log2k[0];
+  bool ok = lk0 <= 5;
+  for (int i = 0; i < 8; ++i) {
+    const int b = lane + 32 * i;
+    ok = ok && pat.log2k[b] == lk0 && (uint32_t)pat.off[b] == ((uint32_t)b << lk0);
+  }
+  if (__all_sync(0xffffffffu, ok)) {
+    path_lk[0] = PATH_SHIFT;
+    path_lk[1] = (int)lk0;
+    return;
+  }
+  path_lk[0] = PATH_LUT;
+  path_lk[1] = 0;
+  if (*lut_owner != (int)j) {
+    for (int e = t; e < kLutWords; e += kCountThreads) {
+      const int v = e >> 5, l = e & 31;
+      const uint32_t l2 = pat.log2k[v] > 5 ? 5u : pat.log2k[v];
+      lut[e] = ((uint32_t)pat.off[v] + ((uint32_t)l & ((1u << l2) - 1u))) & (kTableWords - 1);
+    }
+    *lut_owner = (int)j;
+    nbar_sync(kBarCount, kCountThreads);
+  }
+}
+
+// Layout for chunk j of a decoupled batch, computed by every counting thread
+// (warp-uniform): PLAIN, the full table (SHIFT 5), or a general pattern.
+// Writes pat for the flush warp.
+__device__ __forceinline__ void dec_layout(const BatchArgs& a, uint32_t j, bool adaptive, const hist_pattern& used0,
+                                           hist_pattern& pat, int& path, int& lk, uint32_t* lut, int& lut_owner,
+                                           CtaShared& cs) {
+  const int t = threadIdx.x;
+  if (!adaptive) {
+    path = PATH_PLAIN;
+    lk = 0;
+    return;
+  }
+  if (j > 0 && a.c[j - 1].n > 0) {
+    if (t < HIST_BINS) {
+      pat.off[t] = (uint16_t)(t * HIST_KMAX);
+      pat.log2k[t] = 5;
+    }
+    if (t == 0) {
+      pat.budget = a.budget;
+      pat.used = HIST_BINS * HIST_KMAX;
+    }
+    path = PATH_SHIFT;
+    lk = 5;
+    return;
+  }
+  int pl[2];
+  dec_layout_general(a, j, used0, pat, pl, lut, &lut_owner, cs);
+  path = pl[0];
+  lk = pl[1];
+}
+
 // Decoupled batch, for the modes in which chunk j+1's kernel and layout do not
 // depend on chunk j's histogram: the plain mode (the plain kernel uses no
 // pattern) and the adaptive mode at the full budget (the pattern rule then
 // gives the full table for every non-empty chunk, the default pattern after
-// an empty one).  Phase 1: the CTAs count the chunks back to back into
-// per-chunk partial buffers (one set per batch, two sets used alternately).
+// an empty one).
+// Phase 1: warps 0..30 count the chunks back to back into two tables used in
+// turn; warp 31 reduces each counted table, adds its per-bin sums into the
+// chunk's partial buffer (one set per batch, two sets used alternately) and
+// clears the table, so the counting warps never stop for a flush.
 // Phase 2: chunk k is folded by CTA k mod the CTA count, which computes its
 // switch and pattern from its own histogram, checks that the layout used for
 // chunk k+1 is the one the rule gives (stream status otherwise) and, for the
@@ -377,53 +521,116 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 // pending.
 __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;
+  uint32_t* tables = smem;                  // two tables of kTableWords
+  uint32_t* lut = smem + 2 * kTableWords;   // slot table, then scratch of phase 2
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
   __shared__ uint32_t counts[kMaxBatch];
   __shared__ hist_pattern used0;  // the pattern chunk 0 was given
   __shared__ hist_pattern next;   // a pattern computed in phase 2
+  __shared__ hist_pattern pats[2];
+  __shared__ int paths[2], lks[2];
+  __shared__ uint32_t fres[HIST_BINS];  // flush warp: one chunk's per-bin sums
   StreamDev* st = a.st;
   const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
   auto mark = [&](uint32_t j, int phase) {
-    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
+    if (a.trace && tslot >= 0 && a.trace_first + j < a.trace_cap)
       a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
   };
   const bool adaptive = a.mode != HIST_MODE_PLAIN;
   const uint32_t kern = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
   const uint32_t set = a.first_buf & 1;  // partial-buffer set of this batch
+  const bool flusher = threadIdx.x >= kCountThreads;
 
   prefetch_slice(a.c[0]);
-  zero_table(table);
-  copy_pattern(&cs.pat, &st->pattern);
+  for (int i = threadIdx.x; i < 2 * kTableWords / 4; i += kThreads)
+    reinterpret_cast<uint4*>(tables)[i] = make_uint4(0, 0, 0, 0);
   copy_pattern(&used0, &st->pattern);
   __syncthreads();
 
-  // phase 1: count every chunk
-  for (uint32_t j = 0; j < a.count; ++j) {
-    mark(j, 0);
-    if (j > 0 && adaptive) saturated_pattern(a.c[j - 1].n, a.budget, cs, es);
-    set_layout(kern, lut, cs);
-    mark(j, 2);
-    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
-    count_geo(cs.path, cs.lk, chunk_geo(a.c[j]), table, lut);
-    mark(j, 3);
-    __syncthreads();
-    mark(j, 4);
-    const uint32_t c =
-        publish_partials(cs, a.c[j], table, lut, &st->brep[set][j][blockIdx.x % kStreamReplicas][0], false);
-    if (threadIdx.x == 0) counts[j] = c;
-    mark(j, 5);
-    zero_table(table);
-    __syncthreads();
-    mark(j, 7);
+  // phase 1
+  if (!flusher) {
+    int lut_owner = -1;
+    for (uint32_t j = 0; j < a.count; ++j) {
+      const int p = j & 1;
+      if (j >= 2) nbar_sync(kBarFree + p, kThreads);
+      if (threadIdx.x == 0) mark(j, 0);
+      int path, lk;
+      dec_layout(a, j, adaptive, used0, pats[p], path, lk, lut, lut_owner, cs);
+      if (threadIdx.x == 0) {
+        paths[p] = path;
+        lks[p] = lk;
+        mark(j, 2);
+      }
+      if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+      const Geo g = chunk_geo(a.c[j]);
+      count_range_dispatch<4>(path, lk, g.body, g.begin, g.end, tables + p * kTableWords, lut, threadIdx.x,
+                              kCountThreads);
+      if (threadIdx.x == 0) mark(j, 3);
+      nbar_arrive(kBarFull + p, kThreads);
+    }
+  } else {
+    // The tables are not cleared between chunks: they keep counting, and a
+    // chunk's per-bin counts are the difference between this reduction and
+    // the previous one of the same table (exact modulo 2^32).  A table is
+    // cleared only when the next chunk on it changes layout.
+    const int lane = threadIdx.x & 31;
+    uint32_t prev[2][8];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) prev[q][i] = 0;
+    for (uint32_t j = 0; j < a.count; ++j) {
+      const int p = j & 1;
+      nbar_sync(kBarFull + p, kThreads);
+      if (lane == 0) mark(j, 4);
+      uint32_t* tab = tables + p * kTableWords;
+      uint32_t sum[8];
+      warp_flush(tab, paths[p], lks[p], pats[p], kCountThreads / 32, sum);
+      // the layout of chunk j+2 on this table: the full table (adaptive, after
+      // a non-empty chunk) keeps it; anything else clears it
+      const bool keep = !adaptive || (j > 0 && a.c[j - 1].n > 0 && j + 1 < a.count && a.c[j + 1].n > 0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t d = sum[i] - (p ? prev[1][i] : prev[0][i]);
+        fres[lane + 32 * i] = d;
+        if (p) prev[1][i] = keep ? sum[i] : 0u;
+        else prev[0][i] = keep ? sum[i] : 0u;
+      }
+      __syncwarp();
+      if (blockIdx.x == 0) {
+        // the chunk's unaligned edge bytes
+        const ChunkDesc& d = a.c[j];
+        const Split sp = split_bytes(d.in, d.n);
+        if ((size_t)lane < sp.head) atomicAdd(&fres[d.in[lane]], 1u);
+        if (lane >= 16 && (size_t)(lane - 16) < sp.tail) atomicAdd(&fres[d.in[sp.head + sp.nvec * 16 + (lane - 16)]], 1u);
+        __syncwarp();
+      }
+      uint32_t* rep = &st->brep[set][j][blockIdx.x % kStreamReplicas][0];
+      uint32_t c = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t v = fres[lane + 32 * i];
+        c += v;
+        if (v) atomicAdd(rep + lane + 32 * i, v);
+      }
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (lane == 0) counts[j] = c;
+      if (lane == 0) mark(j, 5);
+      if (!keep) {
+        uint4* t4 = reinterpret_cast<uint4*>(tab);
+        for (int i = lane; i < kTableWords / 4; i += 32) t4[i] = make_uint4(0, 0, 0, 0);
+      }
+      __syncwarp();
+      if (j + 2 < a.count) nbar_arrive(kBarFree + p, kThreads);
+      if (lane == 0) mark(j, 7);
+    }
   }
   // publish every chunk count after one fence
   __threadfence();
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < a.count; j += kThreads)
-    if (counts[j]) red_release_add(&st->bcnt[set][j][0], counts[j]);
+    if (counts[j]) red_release_add(&st->bcnt[set][j][0], counts[j]);  // pixels only: no buffer is reused in a batch
 
   // clear the other set (the previous batch's), a slice per CTA
   for (uint32_t b = blockIdx.x; b < kMaxBatch; b += gridDim.x) {
@@ -476,12 +683,12 @@ __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __gr
 }
 
 // Epilogue of the last pushed chunk (one CTA of 1024 threads).
-__global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t* out,
-                                                          uint32_t budget, uint32_t theta, uint32_t mode) {
+__global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t ctas,
+                                                          uint32_t* out, uint32_t budget, uint32_t theta, uint32_t mode) {
   __shared__ uint32_t part[kThreads];
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
-  if (!poll_gather(st, &st->rep[buf][0][0], &st->cnt[buf][0], n, part, cs, nullptr)) return;
+  if (!poll_gather(st, &st->rep[buf][0][0], &st->cnt[buf][0], complete_count(ctas, n), part, cs, nullptr)) return;
   epilogue(n, budget, theta, cs, es);
   write_epilogue(st, out, mode, cs.flag, cs, 0, 1);
 }
@@ -553,7 +760,8 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   }
   void* params[] = {a};
   const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)st->grid), dim3(kThreads), params, kSmemBytes, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)st->grid), dim3(kThreads), params,
+                                              st->decoupled ? kDecSmemBytes : kSmemBytes, s);
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
   if (st->decoupled) {
@@ -582,8 +790,8 @@ int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, cons
 
 int do_flush(hist_stream* st, cudaStream_t s) {
   if (!st->pending) return HIST_OK;
-  finish_kernel<<<1, kThreads, 0, s>>>(st->d, st->pending_buf, st->pending_n, st->pending_out, st->cfg.budget,
-                                       st->cfg.theta_milli, st->cfg.mode);
+  finish_kernel<<<1, kThreads, 0, s>>>(st->d, st->pending_buf, st->pending_n, (uint32_t)st->grid, st->pending_out,
+                                       st->cfg.budget, st->cfg.theta_milli, st->cfg.mode);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);
   st->pending = false;
@@ -596,13 +804,13 @@ bool config_ok(const hist_config* c) {
          c->mode <= HIST_MODE_ADAPTIVE;
 }
 
-int grid_for(const hist_config* cfg, int sms, const void* fn) {
+int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
   // at most the CTAs that can be resident at once: a cooperative launch needs them all
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kSmemBytes) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int cap = per_sm * sms;
-  const int g = cfg->grid ? (int)cfg->grid : sms;
+  const int g = cfg->grid ? (int)cfg->grid : sms;  // one CTA per SM: one table flush per SM per chunk
   return g > cap ? cap : g;
 }
 
@@ -644,12 +852,13 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   st->decoupled = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
   const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
   static int attr_sync[kMaxDevices], attr_dec[kMaxDevices];
-  int rc = ensure_smem_attr(fn, st->decoupled ? attr_dec : attr_sync);
+  const size_t smem = st->decoupled ? kDecSmemBytes : kSmemBytes;
+  int rc = ensure_smem_attr_bytes(fn, st->decoupled ? attr_dec : attr_sync, smem);
   if (rc) {
     free(st);
     return rc;
   }
-  st->grid = grid_for(cfg, st->sms, fn);
+  st->grid = grid_for(cfg, st->sms, fn, smem);
   cudaError_t e = cudaMalloc((void**)&st->d, sizeof(StreamDev));
   if (e != cudaSuccess) {
     free(st);
