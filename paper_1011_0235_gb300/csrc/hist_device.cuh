@@ -293,6 +293,14 @@ __host__ __device__ __forceinline__ Split split_bytes(const uint8_t* a, size_t n
   return s;
 }
 
+// Count head and tail bytes of a split into the shared histogram h (threads
+// 0..31 of the CTA).
+__device__ __forceinline__ void count_edges_into(const uint8_t* a, const Split& sp, uint32_t* h) {
+  const int t = threadIdx.x;
+  if (t < (int)sp.head) atomicAdd(&h[a[t]], 1u);
+  else if (t >= 16 && t < 16 + (int)sp.tail) atomicAdd(&h[a[sp.head + sp.nvec * 16 + (t - 16)]], 1u);
+}
+
 // Count head and tail bytes of a split into cs.res (one warp of the CTA).
 __device__ __forceinline__ void count_edges(const uint8_t* a, const Split& sp, CtaShared& cs) {
   const int t = threadIdx.x;

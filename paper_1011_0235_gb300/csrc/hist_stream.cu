@@ -374,81 +374,84 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
   return __syncthreads_and(ok);
 }
 
-// Named barriers of the decoupled kernel (0 is __syncthreads).
-constexpr int kBarFull = 1;   // +p: table p holds a counted chunk (counting warps arrive, flush warp waits)
-constexpr int kBarFree = 3;   // +p: table p is clear again (flush warp arrives, counting warps wait)
-constexpr int kBarCount = 5;  // the counting warps among themselves
-constexpr int kCountThreads = kThreads - 32;  // warps 0..30 count, warp 31 flushes
 constexpr size_t kDecSmemBytes = (size_t)(2 * kTableWords + kLutWords) * 4;  // two tables + slot table
 
-__device__ __forceinline__ void nbar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void nbar_arrive(int id, int n) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-// One warp sums table `t` per bin: lane l gets bins l + 32 i in sum[i].  The
-// layout is PLAIN (nwarps per-warp tables), SHIFT (bin b owns the 2^lk slots
-// from b << lk) or a general pattern P.  For SHIFT each lane reads its own
-// rows in 16-byte pieces, rotated by the lane so that the 8 lanes of each
-// shared-memory phase touch 8 different bank quads.
-__device__ __noinline__ void warp_flush(const uint32_t* t, int path, int lk, const hist_pattern& P, int nwarps,
-                                        uint32_t* sum) {
-  const int lane = threadIdx.x & 31;
-  for (int i = 0; i < 8; ++i) sum[i] = 0;
+// Lagged reduction of a counted table.  Thread t takes bin t >> 2 and reads 8
+// of its slots (4 threads per bin); the loads are issued right after the
+// chunk's barrier and consumed only after the next chunk has been counted, so
+// no thread waits for them behind the atomics still in the shared-memory
+// pipe.
+__device__ __forceinline__ void lag_load(const uint32_t* tab, int path, int lk, const hist_pattern& P, uint32_t (&v)[8]) {
+  const int t = threadIdx.x, b = t >> 2, q = t & 3;
   if (path == PATH_PLAIN) {
-    for (int i = 0; i < 8; ++i) {
-      uint32_t s = 0;
-      for (int w = 0; w < nwarps; ++w) s += t[w * HIST_BINS + lane + 32 * i];
-      sum[i] = s;
-    }
-  } else if (path == PATH_SHIFT) {
-    const int K = 1 << lk;
-    for (int i = 0; i < 8; ++i) {
-      const int b = lane + 32 * i;
-      const uint32_t* row = t + (b << lk);
-      uint32_t s = 0;
-      if (K >= 4) {
-        const int pieces = K >> 2;
-        const uint4* r4 = reinterpret_cast<const uint4*>(row);
-        for (int q = 0; q < pieces; ++q) {
-          const uint4 v = r4[(q + lane) & (pieces - 1)];
-          s += v.x + v.y + v.z + v.w;
-        }
-      } else {
-        for (int j = 0; j < K; ++j) s += row[j];
-      }
-      sum[i] = s;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = tab[(q + 4 * i) * HIST_BINS + b];
+  } else if (path == PATH_SHIFT && lk == 5) {
+    // two 16-byte pieces of the bin's row: 16-byte groups 2q + s + (b & 1)
+    // (mod 8), s = 0, 1, so the 8 threads of each shared-memory phase (two
+    // bins) touch 8 different bank quads
+    const uint4* r4 = reinterpret_cast<const uint4*>(tab + (b << 5));
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const uint4 w = r4[(2 * q + s + (b & 1)) & 7];
+      v[4 * s] = w.x;
+      v[4 * s + 1] = w.y;
+      v[4 * s + 2] = w.z;
+      v[4 * s + 3] = w.w;
     }
   } else {
+    uint32_t o, k;
+    if (path == PATH_SHIFT) {
+      o = (uint32_t)b << lk;
+      k = 1u << lk;
+    } else {
+      o = P.off[b];
+      k = 1u << (P.log2k[b] > 5 ? 5u : P.log2k[b]);
+    }
+#pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int b = lane + 32 * i;
-      const uint32_t l2 = P.log2k[b] > 5 ? 5u : P.log2k[b];
-      const uint32_t o = P.off[b];
-      uint32_t s = 0;
-      for (uint32_t j = 0; j < (1u << l2); ++j) s += t[(o + j) & (kTableWords - 1)];
-      sum[i] = s;
+      const uint32_t j = (uint32_t)(q + 4 * i);
+      v[i] = j < k ? tab[(o + j) & (kTableWords - 1)] : 0u;
     }
   }
+}
+
+// Finish the lagged reduction of chunk m on table p: the bin's sum, its
+// difference from the previous reduction of the table, added into chunk m's
+// partial buffer; the CTA's pixel count of chunk m into counts[m].
+__device__ __forceinline__ void lag_finish(const uint32_t (&v)[8], uint32_t* prev, uint32_t* rep, uint32_t* count) {
+  const int t = threadIdx.x, b = t >> 2, q = t & 3;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += v[i];
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  uint32_t d = 0;
+  if (q == 0) {
+    d = s - prev[b];
+    prev[b] = s;
+    if (d) atomicAdd(rep + b, d);
+  }
+  const uint32_t c = __reduce_add_sync(0xffffffffu, d);
+  if ((t & 31) == 0 && c) atomicAdd(count, c);
 }
 
 // General layout of a decoupled chunk (chunk 0: the stream's current pattern;
-// after an empty chunk: the default pattern), rare.  Every counting thread
-// calls; builds the slot table if the pattern needs one.
+// after an empty chunk: the default pattern), rare.  All threads call;
+// builds the slot table if the pattern needs one.
 __device__ __noinline__ void dec_layout_general(const BatchArgs& a, uint32_t j, const hist_pattern& used0,
-                                                hist_pattern& pat, int* path_lk, uint32_t* lut, int* lut_owner,
-                                                CtaShared& cs) {
+                                                hist_pattern& pat, int* path_lk, uint32_t* lut, CtaShared& cs) {
   const int t = threadIdx.x;
-  nbar_sync(kBarCount, kCountThreads);
+  __syncthreads();
   if (j == 0) {
-    for (int i = t; i < (int)(sizeof(hist_pattern) / 4); i += kCountThreads)
-      reinterpret_cast<uint32_t*>(&pat)[i] = reinterpret_cast<const uint32_t*>(&used0)[i];
+    copy_pattern(&pat, &used0);
   } else {
     // default pattern: the rule on an empty histogram
-    for (int i = t; i < HIST_BINS; i += kCountThreads) cs.hist[i] = 0;
-    nbar_sync(kBarCount, kCountThreads);
+    if (t < HIST_BINS) cs.hist[t] = 0;
+    __syncthreads();
     if (t < 32) warp_epilogue(cs.hist, a.budget, a.theta, pat);
   }
-  nbar_sync(kBarCount, kCountThreads);
+  __syncthreads();
   const int lane = t & 31;
   const uint32_t lk0 = pat.log2k[0];
   bool ok = lk0 <= 5;
@@ -463,23 +466,19 @@ __device__ __noinline__ void dec_layout_general(const BatchArgs& a, uint32_t j, 
   }
   path_lk[0] = PATH_LUT;
   path_lk[1] = 0;
-  if (*lut_owner != (int)j) {
-    for (int e = t; e < kLutWords; e += kCountThreads) {
-      const int v = e >> 5, l = e & 31;
-      const uint32_t l2 = pat.log2k[v] > 5 ? 5u : pat.log2k[v];
-      lut[e] = ((uint32_t)pat.off[v] + ((uint32_t)l & ((1u << l2) - 1u))) & (kTableWords - 1);
-    }
-    *lut_owner = (int)j;
-    nbar_sync(kBarCount, kCountThreads);
+  for (int e = t; e < kLutWords; e += kThreads) {
+    const int v = e >> 5, l = e & 31;
+    const uint32_t l2 = pat.log2k[v] > 5 ? 5u : pat.log2k[v];
+    lut[e] = ((uint32_t)pat.off[v] + ((uint32_t)l & ((1u << l2) - 1u))) & (kTableWords - 1);
   }
+  __syncthreads();
 }
 
-// Layout for chunk j of a decoupled batch, computed by every counting thread
-// (warp-uniform): PLAIN, the full table (SHIFT 5), or a general pattern.
-// Writes pat for the flush warp.
+// Layout of chunk j of a decoupled batch (uniform over the CTA): PLAIN, the
+// full table (SHIFT 5), or a general pattern; written to `pat` for the
+// reduction of the table.
 __device__ __forceinline__ void dec_layout(const BatchArgs& a, uint32_t j, bool adaptive, const hist_pattern& used0,
-                                           hist_pattern& pat, int& path, int& lk, uint32_t* lut, int& lut_owner,
-                                           CtaShared& cs) {
+                                           hist_pattern& pat, int& path, int& lk, uint32_t* lut, CtaShared& cs) {
   const int t = threadIdx.x;
   if (!adaptive) {
     path = PATH_PLAIN;
@@ -500,9 +499,26 @@ __device__ __forceinline__ void dec_layout(const BatchArgs& a, uint32_t j, bool 
     return;
   }
   int pl[2];
-  dec_layout_general(a, j, used0, pat, pl, lut, &lut_owner, cs);
+  dec_layout_general(a, j, used0, pat, pl, lut, cs);
   path = pl[0];
   lk = pl[1];
+}
+
+// Pixels of chunk d that phase 1 does not count (its unaligned head and tail).
+__device__ __forceinline__ uint32_t edge_bytes(const ChunkDesc& d) {
+  const Split sp = split_bytes(d.in, d.n);
+  return (uint32_t)(sp.head + sp.tail);
+}
+
+// Poll for chunk k's counted pixels, gather its histogram into cs.hist and add
+// its edge bytes.  All threads call.
+__device__ bool dec_gather(StreamDev* st, const ChunkDesc& d, uint32_t set, uint32_t k, uint32_t* part,
+                           CtaShared& cs) {
+  if (!poll_gather(st, &st->brep[set][k][0][0], &st->bcnt[set][k][0], d.n - edge_bytes(d), part, cs, nullptr))
+    return false;
+  count_edges_into(d.in, split_bytes(d.in, d.n), cs.hist);
+  __syncthreads();
+  return true;
 }
 
 // Decoupled batch, for the modes in which chunk j+1's kernel and layout do not
@@ -510,15 +526,19 @@ __device__ __forceinline__ void dec_layout(const BatchArgs& a, uint32_t j, bool 
 // pattern) and the adaptive mode at the full budget (the pattern rule then
 // gives the full table for every non-empty chunk, the default pattern after
 // an empty one).
-// Phase 1: warps 0..30 count the chunks back to back into two tables used in
-// turn; warp 31 reduces each counted table, adds its per-bin sums into the
-// chunk's partial buffer (one set per batch, two sets used alternately) and
-// clears the table, so the counting warps never stop for a flush.
-// Phase 2: chunk k is folded by CTA k mod the CTA count, which computes its
-// switch and pattern from its own histogram, checks that the layout used for
-// chunk k+1 is the one the rule gives (stream status otherwise) and, for the
-// last chunk, writes the stream state.  Such a stream never leaves a chunk
-// pending.
+// Phase 1: the CTAs count the chunks back to back into two tables used in
+// turn, one barrier per chunk.  A table is reduced with loads issued after
+// its chunk's barrier and consumed after the next chunk (see lag_load), and
+// it is not cleared between its chunks: a chunk's counts are the difference
+// from the previous reduction of the same table (exact modulo 2^32); it is
+// cleared only when the next chunk on it changes layout.  The per-bin
+// differences go to the chunk's partial buffer (one set per batch, two sets
+// used alternately).
+// Phase 2: chunk k is folded by CTA k mod the CTA count, which adds the
+// chunk's unaligned edge bytes, computes its switch and pattern from its own
+// histogram, checks that the layout used for chunk k+1 is the one the rule
+// gives (stream status otherwise) and, for the last chunk, writes the stream
+// state.  Such a stream never leaves a chunk pending.
 __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* tables = smem;                  // two tables of kTableWords
@@ -526,105 +546,70 @@ __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __gr
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
   __shared__ uint32_t counts[kMaxBatch];
-  __shared__ hist_pattern used0;  // the pattern chunk 0 was given
-  __shared__ hist_pattern next;   // a pattern computed in phase 2
+  __shared__ uint32_t prev[2][HIST_BINS];  // per table: the bin sums of its last reduction
+  __shared__ hist_pattern used0;           // the pattern chunk 0 was given
+  __shared__ hist_pattern next;            // a pattern computed in phase 2
   __shared__ hist_pattern pats[2];
   __shared__ int paths[2], lks[2];
-  __shared__ uint32_t fres[HIST_BINS];  // flush warp: one chunk's per-bin sums
   StreamDev* st = a.st;
   const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
   auto mark = [&](uint32_t j, int phase) {
-    if (a.trace && tslot >= 0 && a.trace_first + j < a.trace_cap)
+    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
       a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
   };
   const bool adaptive = a.mode != HIST_MODE_PLAIN;
   const uint32_t kern = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
   const uint32_t set = a.first_buf & 1;  // partial-buffer set of this batch
-  const bool flusher = threadIdx.x >= kCountThreads;
 
   prefetch_slice(a.c[0]);
   for (int i = threadIdx.x; i < 2 * kTableWords / 4; i += kThreads)
     reinterpret_cast<uint4*>(tables)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < (int)kMaxBatch; i += kThreads) counts[i] = 0;
+  for (int i = threadIdx.x; i < 2 * HIST_BINS; i += kThreads) (&prev[0][0])[i] = 0;
   copy_pattern(&used0, &st->pattern);
   __syncthreads();
 
   // phase 1
-  if (!flusher) {
-    int lut_owner = -1;
-    for (uint32_t j = 0; j < a.count; ++j) {
-      const int p = j & 1;
-      if (j >= 2) nbar_sync(kBarFree + p, kThreads);
-      if (threadIdx.x == 0) mark(j, 0);
-      int path, lk;
-      dec_layout(a, j, adaptive, used0, pats[p], path, lk, lut, lut_owner, cs);
-      if (threadIdx.x == 0) {
-        paths[p] = path;
-        lks[p] = lk;
-        mark(j, 2);
-      }
-      if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
-      const Geo g = chunk_geo(a.c[j]);
-      count_range_dispatch<4>(path, lk, g.body, g.begin, g.end, tables + p * kTableWords, lut, threadIdx.x,
-                              kCountThreads);
-      if (threadIdx.x == 0) mark(j, 3);
-      nbar_arrive(kBarFull + p, kThreads);
+  uint32_t v[8];
+  for (uint32_t j = 0; j < a.count; ++j) {
+    const int p = j & 1;
+    mark(j, 0);
+    int path, lk;
+    dec_layout(a, j, adaptive, used0, pats[p], path, lk, lut, cs);
+    if (threadIdx.x == 0) {
+      paths[p] = path;
+      lks[p] = lk;
     }
-  } else {
-    // The tables are not cleared between chunks: they keep counting, and a
-    // chunk's per-bin counts are the difference between this reduction and
-    // the previous one of the same table (exact modulo 2^32).  A table is
-    // cleared only when the next chunk on it changes layout.
-    const int lane = threadIdx.x & 31;
-    uint32_t prev[2][8];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int i = 0; i < 8; ++i) prev[q][i] = 0;
-    for (uint32_t j = 0; j < a.count; ++j) {
-      const int p = j & 1;
-      nbar_sync(kBarFull + p, kThreads);
-      if (lane == 0) mark(j, 4);
-      uint32_t* tab = tables + p * kTableWords;
-      uint32_t sum[8];
-      warp_flush(tab, paths[p], lks[p], pats[p], kCountThreads / 32, sum);
-      // the layout of chunk j+2 on this table: the full table (adaptive, after
-      // a non-empty chunk) keeps it; anything else clears it
-      const bool keep = !adaptive || (j > 0 && a.c[j - 1].n > 0 && j + 1 < a.count && a.c[j + 1].n > 0);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t d = sum[i] - (p ? prev[1][i] : prev[0][i]);
-        fres[lane + 32 * i] = d;
-        if (p) prev[1][i] = keep ? sum[i] : 0u;
-        else prev[0][i] = keep ? sum[i] : 0u;
+    mark(j, 2);
+    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+    const Geo g = chunk_geo(a.c[j]);
+    count_range_dispatch<4>(path, lk, g.body, g.begin, g.end, tables + p * kTableWords, lut, threadIdx.x, kThreads);
+    mark(j, 3);
+    __syncthreads();  // chunk j's increments are all issued
+    mark(j, 4);
+    if (j > 0) {
+      // chunk j-1 on the other table: its loads were issued one chunk ago
+      const int q = p ^ 1;
+      lag_finish(v, prev[q], &st->brep[set][j - 1][blockIdx.x % kStreamReplicas][0], &counts[j - 1]);
+      // the next chunk on that table, j+1, keeps the full-table layout of
+      // chunk j-1, or the table is cleared
+      const bool keep = !adaptive || (j > 1 && a.c[j - 2].n > 0 && a.c[j].n > 0);
+      if (!keep && j + 1 < a.count) {
+        __syncthreads();
+        uint4* t4 = reinterpret_cast<uint4*>(tables + q * kTableWords);
+        for (int i = threadIdx.x; i < kTableWords / 4; i += kThreads) t4[i] = make_uint4(0, 0, 0, 0);
+        if (threadIdx.x < HIST_BINS) prev[q][threadIdx.x] = 0;
+        __syncthreads();
       }
-      __syncwarp();
-      if (blockIdx.x == 0) {
-        // the chunk's unaligned edge bytes
-        const ChunkDesc& d = a.c[j];
-        const Split sp = split_bytes(d.in, d.n);
-        if ((size_t)lane < sp.head) atomicAdd(&fres[d.in[lane]], 1u);
-        if (lane >= 16 && (size_t)(lane - 16) < sp.tail) atomicAdd(&fres[d.in[sp.head + sp.nvec * 16 + (lane - 16)]], 1u);
-        __syncwarp();
-      }
-      uint32_t* rep = &st->brep[set][j][blockIdx.x % kStreamReplicas][0];
-      uint32_t c = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t v = fres[lane + 32 * i];
-        c += v;
-        if (v) atomicAdd(rep + lane + 32 * i, v);
-      }
-      c = __reduce_add_sync(0xffffffffu, c);
-      if (lane == 0) counts[j] = c;
-      if (lane == 0) mark(j, 5);
-      if (!keep) {
-        uint4* t4 = reinterpret_cast<uint4*>(tab);
-        for (int i = lane; i < kTableWords / 4; i += 32) t4[i] = make_uint4(0, 0, 0, 0);
-      }
-      __syncwarp();
-      if (j + 2 < a.count) nbar_arrive(kBarFree + p, kThreads);
-      if (lane == 0) mark(j, 7);
     }
+    lag_load(tables + p * kTableWords, path, lk, pats[p], v);
+    mark(j, 5);
+  }
+  __syncthreads();
+  {
+    const uint32_t m = a.count - 1;
+    const int q = m & 1;
+    lag_finish(v, prev[q], &st->brep[set][m][blockIdx.x % kStreamReplicas][0], &counts[m]);
   }
   // publish every chunk count after one fence
   __threadfence();
@@ -642,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __gr
   // phase 2: fold chunk k in CTA k mod the CTA count
   for (uint32_t k = blockIdx.x; k < a.count; k += gridDim.x) {
     const uint32_t n = a.c[k].n;
-    if (!poll_gather(st, &st->brep[set][k][0][0], &st->bcnt[set][k][0], n, lut, cs, nullptr)) return;
+    if (!dec_gather(st, a.c[k], set, k, lut, cs)) return;
     const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
     if (threadIdx.x == 0) cs.flag = r.flag;
     __syncthreads();
@@ -665,8 +650,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __gr
         saturated_pattern(a.c[k - 1].n, a.budget, cs, es);
       } else {
         // plain mode records binning_pattern(chunk k-1) as chunk k's pattern
-        if (!poll_gather(st, &st->brep[set][k - 1][0][0], &st->bcnt[set][k - 1][0], a.c[k - 1].n, lut, cs, nullptr))
-          return;
+        __syncthreads();
+        if (!dec_gather(st, a.c[k - 1], set, k - 1, lut, cs)) return;
         block_epilogue(cs.hist, a.c[k - 1].n, a.budget, a.theta, cs.pat, es);
       }
       __syncthreads();
@@ -810,7 +795,7 @@ int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int cap = per_sm * sms;
-  const int g = cfg->grid ? (int)cfg->grid : sms;  // one CTA per SM: one table flush per SM per chunk
+  const int g = cfg->grid ? (int)cfg->grid : sms;  // one CTA per SM: one table reduction per SM per chunk
   return g > cap ? cap : g;
 }
 
