@@ -351,6 +351,42 @@ def run_native(args):
             extras["degenerate_%s_gbs" % name] = round(world * nbytes * args.steps / e2 / 1e9, 2)
             s2.close()
         del xdg
+        # batch: 4096 images of uneven sizes in one graph-captured launch,
+        # settings from the autotuner
+        import ctypes
+        from paper_1011_0235_gb300 import _abi
+        from synth import workloads
+        images = workloads.batch_images(count=4096)
+        bbytes = sum(im.n for im in images)
+        bbuf = torch.empty(workloads.packed_bytes(images), dtype=torch.uint8, device="cuda")
+        sq = torch.cuda.current_stream().cuda_stream
+        for im in images:
+            synth.device_fill(bbuf.data_ptr() + im.offset, im.n, im.thr, synth.SEED_BASE + 4, im.counter0, sq)
+        bptrs = torch.tensor([bbuf.data_ptr() + im.offset for im in images], dtype=torch.int64, device="cuda")
+        bsizes = torch.tensor([im.n for im in images], dtype=torch.int64, device="cuda")
+        bout = torch.empty((len(images), 256), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        lib = hl.lib()
+        best = _abi.BatchTuning()
+        bms = ctypes.c_float()
+        _abi.check("hist_batch_autotune", lib.hist_batch_autotune(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
+                                                                  bout.data_ptr(), 2, ctypes.byref(best),
+                                                                  ctypes.byref(bms)))
+        gexec = ctypes.c_void_p()
+        _abi.check("hist_batch_capture", lib.hist_batch_capture(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
+                                                                bout.data_ptr(), ctypes.byref(best),
+                                                                ctypes.byref(gexec)))
+        ksb = max(3, min(args.steps, 10))
+        e5 = time_steps(torch, lambda: _abi.check("hist_batch_graph_launch", lib.hist_batch_graph_launch(
+            gexec, torch.cuda.current_stream().cuda_stream)), 2, ksb)
+        lib.hist_batch_graph_destroy(gexec)
+        extras["batch_images"] = len(images)
+        extras["batch_bytes"] = bbytes
+        extras["batch_graph_gbs"] = round(bbytes * ksb / e5 / 1e9, 2)
+        extras["batch_frac_of_hbm"] = round(bbytes * ksb / e5 / 1e9 / hbm, 4)
+        extras["batch_tuning"] = {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll,
+                                  "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}
+        del bbuf, bout
         # one-shot kernels on the whole 1 GiB at once (no stream)
         full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
         o = hl.empty_hist()

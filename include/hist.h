@@ -244,6 +244,49 @@ int hist_stream_get_state(hist_stream* st, hist_stream_state* h_state, hist_cuda
  * HIST_EINVAL if the state's patterns are invalid for this stream's budget. */
 int hist_stream_set_state(hist_stream* st, const hist_stream_state* h_state, hist_cuda_stream s);
 
+/* ---------------------------------------------------------------- batch -- */
+/* Many histograms in one call (Sec. III.B: slices or packets too small for a
+ * launch each are batched into one call that returns many histograms).
+ * d_ptrs / d_sizes are DEVICE arrays of `count` image pointers and sizes
+ * (each image below 2^32 bytes, any alignment); d_out is count x uint32_t[256]
+ * on the device, overwritten: histogram i is d_out[256 i .. 256 i + 255].
+ * Work: a memset of d_out and one kernel per HIST_BATCH_MAX_IMAGES images.
+ * Each CTA takes an equal share of the images' concatenated bytes and counts
+ * it in a lane-private sub-bin table (k = 32 sub-bins per bin), or with
+ * 2^small_log2k sub-bins for images below small_bytes; a CTA adds into an
+ * image's output where its share leaves the image.  No scratch memory. */
+#define HIST_BATCH_MAX_IMAGES 4096u
+
+typedef struct hist_batch_tuning {
+  uint32_t ctas_per_sm; /* 1 or 2 (default 1) */
+  uint32_t unroll;      /* 16-byte loads in flight per thread: 2 or 4 (4 needs ctas_per_sm 1; default 4) */
+  uint32_t small_bytes; /* images below this size use small_log2k (default 0: none) */
+  uint32_t small_log2k; /* 0..5 (default 5) */
+  uint32_t reserved[4];
+} hist_batch_tuning;
+
+void hist_batch_tuning_init(hist_batch_tuning* t);
+/* Enqueue the batch on `s`; tuning null = defaults.  HIST_EINVAL for a bad
+ * tuning or null arrays with count > 0. */
+int hist_batch(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+               const hist_batch_tuning* tuning, hist_cuda_stream s);
+
+/* The same batch as an instantiated CUDA graph (memset + kernels), for
+ * replaying over new contents of the same device arrays and buffers.  The
+ * caller owns the graph (hist_batch_graph_destroy). */
+typedef struct hist_batch_graph hist_batch_graph;
+int hist_batch_capture(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                       const hist_batch_tuning* tuning, hist_batch_graph** graph);
+int hist_batch_graph_launch(hist_batch_graph* graph, hist_cuda_stream s);
+int hist_batch_graph_destroy(hist_batch_graph* graph);
+
+/* Autotuner: times every candidate setting (CTAs per SM, loads in flight,
+ * sub-bins of small images) `repeats` times on this batch, synchronously, and
+ * writes the fastest to *best (and its time in ms to *best_ms if not null).
+ * d_out receives the batch's histograms. */
+int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                        uint32_t repeats, hist_batch_tuning* best, float* best_ms);
+
 /* ------------------------------------------------ stream without allocation -- */
 /* The paper has no counterpart of this call: it serves callers that cannot
  * allocate device memory where they need histograms -- code running while a

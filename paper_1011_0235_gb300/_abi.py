@@ -33,6 +33,7 @@ EBUSY = -6
 ESTATE = -7
 
 HIST_NOALLOC_MAX_CHUNKS = 128
+HIST_BATCH_MAX_IMAGES = 4096
 
 
 class HistPattern(ctypes.Structure):
@@ -59,6 +60,16 @@ class HistConfig(ctypes.Structure):
         ("theta_milli", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
         ("grid", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("unroll", ctypes.c_uint32),
+        ("small_bytes", ctypes.c_uint32),
+        ("small_log2k", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32 * 4),
     ]
 
@@ -103,6 +114,12 @@ SIGNATURES = [
     ("hist_stream_get_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_set_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_run_noalloc", _I, [_P, _P, _U32, ctypes.POINTER(HistConfig), _P, _P, _P, _P]),
+    ("hist_batch_tuning_init", None, [ctypes.POINTER(BatchTuning)]),
+    ("hist_batch", _I, [_P, _P, _U32, _P, ctypes.POINTER(BatchTuning), _P]),
+    ("hist_batch_capture", _I, [_P, _P, _U32, _P, ctypes.POINTER(BatchTuning), ctypes.POINTER(_P)]),
+    ("hist_batch_graph_launch", _I, [_P, _P]),
+    ("hist_batch_graph_destroy", _I, [_P]),
+    ("hist_batch_autotune", _I, [_P, _P, _U32, _P, _U32, ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_float)]),
 ]
 
 _lib = None

@@ -1,0 +1,144 @@
+"""GPU parity of the batched launch (many images of uneven sizes in one call)
+against the oracle, per image, bit-exact."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1011_0235_gb300 as hl
+import synth
+from paper_1011_0235_gb300 import _abi
+from synth import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(cuda_ok):
+    from paper_1011_0235_gb300 import build
+
+    build.build()
+    hl.lib()
+
+
+def _fill(images, total):
+    buf = torch.zeros(total, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for im in images:
+        synth.device_fill(buf.data_ptr() + im.offset, im.n, im.thr, synth.SEED_BASE + 4, im.counter0, s)
+    torch.cuda.synchronize()
+    return buf
+
+
+def _arrays(buf, images):
+    ptrs = torch.tensor([buf.data_ptr() + im.offset for im in images], dtype=torch.int64, device="cuda")
+    sizes = torch.tensor([im.n for im in images], dtype=torch.int64, device="cuda")
+    return ptrs, sizes
+
+
+def _tuning(**kw):
+    t = _abi.BatchTuning()
+    hl.lib().hist_batch_tuning_init(ctypes.byref(t))
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def _run(ptrs, sizes, count, tuning=None):
+    out = torch.full((count, 256), -1, dtype=torch.int32, device="cuda")
+    rc = hl.lib().hist_batch(ptrs.data_ptr(), sizes.data_ptr(), count, out.data_ptr(),
+                             ctypes.byref(tuning) if tuning is not None else None,
+                             torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+def _oracle(im):
+    return oracle.hist_u32(synth.host(im.n, im.thr, synth.SEED_BASE + 4, im.counter0))
+
+
+TUNINGS = [dict(), dict(ctas_per_sm=2, unroll=2), dict(unroll=2), dict(small_bytes=1 << 16, small_log2k=0),
+           dict(small_bytes=1 << 18, small_log2k=3), dict(ctas_per_sm=2, unroll=2, small_bytes=1 << 20, small_log2k=2)]
+
+
+@pytest.mark.parametrize("tune", TUNINGS)
+def test_batch_small_images_all_tunings(tune):
+    images = workloads.batch_images(count=300, side_lo=1, side_hi=400, jitter=True)
+    images[5].n = 0  # an empty image
+    buf = _fill(images, workloads.packed_bytes(images))
+    ptrs, sizes = _arrays(buf, images)
+    got = _run(ptrs, sizes, len(images), _tuning(**tune))
+    for i, im in enumerate(images):
+        assert np.array_equal(got[i], _oracle(im)), (i, im.n)
+
+
+def test_batch_more_than_one_launch():
+    # more images than one kernel takes
+    images = workloads.batch_images(count=4096 + 300, side_lo=1, side_hi=64, jitter=True)
+    buf = _fill(images, workloads.packed_bytes(images))
+    ptrs, sizes = _arrays(buf, images)
+    got = _run(ptrs, sizes, len(images))
+    for i in list(range(0, len(images), 37)) + [4095, 4096, 4097, len(images) - 1]:
+        assert np.array_equal(got[i], _oracle(images[i])), i
+    assert int(got.astype(np.int64).sum()) == sum(im.n for im in images)
+
+
+def test_batch_graph_capture_replays():
+    images = workloads.batch_images(count=200, side_lo=16, side_hi=1024, jitter=True)
+    buf = _fill(images, workloads.packed_bytes(images))
+    ptrs, sizes = _arrays(buf, images)
+    out = torch.full((len(images), 256), -1, dtype=torch.int32, device="cuda")
+    g = ctypes.c_void_p()
+    assert hl.lib().hist_batch_capture(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(), None,
+                                       ctypes.byref(g)) == 0
+    s = torch.cuda.current_stream().cuda_stream
+    ref = [_oracle(im) for im in images]
+    for rep in range(2):
+        out.fill_(-1)
+        assert hl.lib().hist_batch_graph_launch(g, s) == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        for i in range(len(images)):
+            assert np.array_equal(got[i], ref[i]), (rep, i)
+    # new contents in the same buffers: the graph sees them
+    buf.zero_()
+    assert hl.lib().hist_batch_graph_launch(g, s) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    assert all(int(got[i][0]) == images[i].n for i in range(len(images)))
+    assert hl.lib().hist_batch_graph_destroy(g) == 0
+
+
+def test_batch_autotune_returns_a_valid_setting():
+    images = workloads.batch_images(count=256, side_lo=64, side_hi=2048)
+    buf = _fill(images, workloads.packed_bytes(images))
+    ptrs, sizes = _arrays(buf, images)
+    out = torch.empty((len(images), 256), dtype=torch.int32, device="cuda")
+    best = _abi.BatchTuning()
+    ms = ctypes.c_float()
+    assert hl.lib().hist_batch_autotune(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(), 1,
+                                        ctypes.byref(best), ctypes.byref(ms)) == 0
+    assert best.unroll in (2, 4) and best.ctas_per_sm in (1, 2) and ms.value > 0
+    got = _run(ptrs, sizes, len(images), best)
+    for i in range(0, len(images), 17):
+        assert np.array_equal(got[i], _oracle(images[i])), i
+
+
+def test_batch_full_size_4096_images_sampled():
+    # 4096 images, sides log-uniform in [64, 4096], aspect 1:1..4:3, laws as in
+    # the benchmark (about 9.6 GB): every image checked by its pixel total, a
+    # sample of images bin by bin
+    images = workloads.batch_images(count=4096)
+    total = workloads.packed_bytes(images)
+    buf = _fill(images, total)
+    ptrs, sizes = _arrays(buf, images)
+    got = _run(ptrs, sizes, len(images))
+    assert all(int(got[i].astype(np.int64).sum()) == im.n for i, im in enumerate(images))
+    rng = np.random.default_rng(1)
+    pick = set(rng.integers(0, 4096, 48).tolist())
+    pick |= {int(np.argmax([im.n for im in images])), int(np.argmin([im.n for im in images])), 0, 4095}
+    for i in sorted(pick):
+        assert np.array_equal(got[i], _oracle(images[i])), i
