@@ -318,6 +318,110 @@ int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes,
                             const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals,
                             uint32_t* d_status, hist_cuda_stream s);
 
+/* --------------------------------------------------------------- server -- */
+/* A serving loop (Sec. III.B's stream, for many independent streams whose
+ * chunks arrive as requests).  Each of `streams` streams keeps its adaptive
+ * state on the device -- totals, last histogram, the switch flag, the next
+ * binning pattern and its layout -- so request j of stream s runs the kernel
+ * and pattern chosen from request j-1 of s, exactly as hist_stream_push would
+ * on a stream of its own (first request: plain kernel, default pattern).
+ *
+ * Continuous batching on the host (no device-side waits):
+ *   submit  queues a request (FIFO); nothing is enqueued on the GPU.
+ *   poll    retires batches whose completion event has fired, writing one
+ *           hist_completion per finished request, then admits the next batch
+ *           if one of max_inflight batch slots is free: in FIFO order, every
+ *           queued request whose stream has no request on the GPU and whose
+ *           bytes fit the HBM budget (bytes of all requests on the GPU <=
+ *           hbm_budget), up to max_batch requests.  The batch is one kernel
+ *           on the slot's own CUDA stream, so batches overlap on the device.
+ *   drain   polls until nothing is queued or in flight (bounded by
+ *           timeout_ms; HIST_ETIMEDOUT when it runs out).
+ * A request's bytes (d_in, n < 2^32, any alignment) must stay valid and
+ * unchanged, and d_out (uint32_t[256], or null) untouched, until its
+ * completion has been returned by poll.  The server owns its device state;
+ * one host thread at a time may call it.  Results are exact: a request's
+ * histogram and the stream's state do not depend on what else shares its
+ * batch.  Any CUDA error is returned by the poll or drain that sees it. */
+#define HIST_SERVER_MAX_STREAMS 4096u
+#define HIST_SERVER_MAX_BATCH 1024u
+#define HIST_SERVER_MAX_INFLIGHT 8u
+
+typedef struct hist_server_config {
+  uint32_t streams;        /* independent streams, 1..HIST_SERVER_MAX_STREAMS (default 256) */
+  uint32_t max_batch;      /* requests per batch, 1..HIST_SERVER_MAX_BATCH (default 256) */
+  uint32_t max_inflight;   /* batches on the GPU at once, 1..HIST_SERVER_MAX_INFLIGHT (default 4) */
+  uint32_t theta_milli;    /* degeneracy threshold (default 450) */
+  uint32_t pattern_budget; /* sub-bin table slots of every stream's patterns (default 8192) */
+  uint32_t mode;           /* HIST_MODE_* for every stream (default AUTO) */
+  uint64_t hbm_budget;     /* admission budget: request bytes on the GPU (default 32 GiB) */
+  uint32_t reserved[4];
+} hist_server_config;
+
+typedef struct hist_server_stats {
+  uint64_t submitted;      /* requests submitted */
+  uint64_t completed;      /* requests returned by poll */
+  uint64_t bytes;          /* bytes of the completed requests */
+  uint64_t batches;        /* batches launched */
+  uint64_t queued;         /* requests waiting now */
+  uint64_t inflight_bytes; /* request bytes on the GPU now */
+  uint64_t deferred;       /* admissions that skipped a request for the byte budget */
+  uint64_t reserved[5];
+} hist_server_stats;
+
+/* One finished request.  Times are CLOCK_MONOTONIC nanoseconds (in
+ * hist_server_replay: from the start of the replay). */
+typedef struct hist_completion {
+  uint64_t tag;       /* the caller's tag */
+  uint32_t stream;
+  uint32_t status;    /* 0 */
+  uint64_t bytes;
+  uint64_t submit_ns; /* submitted (replay: scheduled arrival) */
+  uint64_t admit_ns;  /* its batch was launched */
+  uint64_t done_ns;   /* poll saw its batch complete */
+} hist_completion;
+
+typedef struct hist_server hist_server;
+
+void hist_server_config_init(hist_server_config* c);
+/* Allocates the per-stream state, max_inflight batch slots (about 1.1 MiB of
+ * device memory each) and their CUDA streams; synchronizes the device.
+ * HIST_EINVAL for a bad config. */
+int hist_server_create(const hist_server_config* cfg, hist_server** out);
+/* Waits for the GPU, then frees everything. */
+int hist_server_destroy(hist_server* srv);
+/* Queue a request: the next chunk of stream `stream`.  HIST_EBUDGET if n
+ * alone exceeds the HBM budget (it could never be admitted). */
+int hist_server_submit(hist_server* srv, uint32_t stream, const uint8_t* d_in, size_t n, uint32_t* d_out,
+                       uint64_t tag);
+/* Retire finished batches (at most `cap` completions are written; the rest
+ * stay for the next poll) and admit one batch.  *n_done = completions written. */
+int hist_server_poll(hist_server* srv, hist_completion* h_done, uint32_t cap, uint32_t* n_done);
+/* Poll until idle; timeout_ms 0 = no limit.  Completions are discarded. */
+int hist_server_drain(hist_server* srv, uint32_t timeout_ms);
+/* Drain, then copy stream `stream`'s state to the host (status is 0). */
+int hist_server_stream_state(hist_server* srv, uint32_t stream, hist_stream_state* h_state);
+int hist_server_get_stats(hist_server* srv, hist_server_stats* h_stats);
+
+/* Replay a schedule in real time on the calling thread: request i is
+ * submitted once arrival_ns (ns after the start of the call, non-decreasing)
+ * has passed, and the loop polls until every request has completed;
+ * h_done[i] receives request i's completion (tag = the request's tag).
+ * Latency of request i = h_done[i].done_ns - h_done[i].submit_ns.
+ * timeout_ms bounds the whole replay (0 = no limit). */
+typedef struct hist_request {
+  uint64_t arrival_ns;
+  uint32_t stream;
+  uint32_t reserved;
+  const uint8_t* d_in;
+  uint64_t n;
+  uint32_t* d_out;
+  uint64_t tag;
+} hist_request;
+
+int hist_server_replay(hist_server* srv, const hist_request* h_reqs, uint32_t count, hist_completion* h_done,
+                       uint32_t timeout_ms);
+
 #ifdef __cplusplus
 }
 #endif

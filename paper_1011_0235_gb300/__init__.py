@@ -221,3 +221,71 @@ class Stream:
 
     def set_state(self, s: StreamState, stream=None) -> None:
         _abi.check("hist_stream_set_state", lib().hist_stream_set_state(self._h, ctypes.byref(s), _stream_ptr(stream)))
+
+
+class Server:
+    """Serving loop over many streams, continuously batched (``hist_server_*``).
+
+    Each of `streams` streams keeps its adaptive state on the device; a request
+    is the next chunk of one stream.  ``submit`` queues, ``poll`` retires
+    finished batches and admits the next one, ``drain`` runs until idle.  The
+    bytes of a request must already be on the device when it is submitted
+    (synchronize the stream that wrote them), and stay unchanged, like its
+    output buffer, until its completion has been returned.
+    """
+
+    def __init__(self, streams: int = 256, max_batch: int = 256, max_inflight: int = 4,
+                 hbm_budget: int = 32 << 30, theta_milli: int = THETA_MILLI_DEFAULT,
+                 pattern_budget: int = BUDGET_MAX, mode: int = MODE_AUTO):
+        cfg = _abi.ServerConfig()
+        lib().hist_server_config_init(ctypes.byref(cfg))
+        cfg.streams, cfg.max_batch, cfg.max_inflight = streams, max_batch, max_inflight
+        cfg.hbm_budget, cfg.theta_milli, cfg.pattern_budget, cfg.mode = hbm_budget, theta_milli, pattern_budget, mode
+        h = ctypes.c_void_p()
+        _abi.check("hist_server_create", lib().hist_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.config = cfg
+        self._done = (_abi.Completion * (max_batch * max_inflight))()
+
+    def close(self) -> None:
+        if self._h:
+            _abi.check("hist_server_destroy", lib().hist_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, stream_id: int, x: torch.Tensor, out: Optional[torch.Tensor] = None, tag: int = 0) -> None:
+        x = _dev_u8(x)
+        self.submit_ptr(stream_id, x.data_ptr(), x.numel(), _ptr(out), tag)
+
+    def submit_ptr(self, stream_id: int, ptr: int, n: int, out_ptr: Optional[int] = None, tag: int = 0) -> None:
+        _abi.check("hist_server_submit", lib().hist_server_submit(self._h, stream_id, ptr, n, out_ptr, tag))
+
+    def poll(self) -> list:
+        n = ctypes.c_uint32()
+        _abi.check("hist_server_poll", lib().hist_server_poll(self._h, self._done, len(self._done), ctypes.byref(n)))
+        return [_abi.Completion.from_buffer_copy(self._done[i]) for i in range(n.value)]
+
+    def drain(self, timeout_ms: int = 0) -> None:
+        _abi.check("hist_server_drain", lib().hist_server_drain(self._h, timeout_ms))
+
+    def stream_state(self, stream_id: int) -> StreamState:
+        s = StreamState()
+        _abi.check("hist_server_stream_state", lib().hist_server_stream_state(self._h, stream_id, ctypes.byref(s)))
+        return s
+
+    def stats(self):
+        s = _abi.ServerStats()
+        _abi.check("hist_server_get_stats", lib().hist_server_get_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def replay(self, reqs, timeout_ms: int = 0):
+        """Replay a schedule (a ctypes array of ``_abi.Request``) in real time;
+        returns the completions, one per request, in request order."""
+        done = (_abi.Completion * len(reqs))()
+        _abi.check("hist_server_replay", lib().hist_server_replay(self._h, reqs, len(reqs), done, timeout_ms))
+        return done

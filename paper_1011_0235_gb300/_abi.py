@@ -34,6 +34,9 @@ ESTATE = -7
 
 HIST_NOALLOC_MAX_CHUNKS = 128
 HIST_BATCH_MAX_IMAGES = 4096
+HIST_SERVER_MAX_STREAMS = 4096
+HIST_SERVER_MAX_BATCH = 1024
+HIST_SERVER_MAX_INFLIGHT = 8
 
 
 class HistPattern(ctypes.Structure):
@@ -88,6 +91,56 @@ class StreamState(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("streams", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint32),
+        ("max_inflight", ctypes.c_uint32),
+        ("theta_milli", ctypes.c_uint32),
+        ("pattern_budget", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
+        ("hbm_budget", ctypes.c_uint64),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("bytes", ctypes.c_uint64),
+        ("batches", ctypes.c_uint64),
+        ("queued", ctypes.c_uint64),
+        ("inflight_bytes", ctypes.c_uint64),
+        ("deferred", ctypes.c_uint64),
+        ("reserved", ctypes.c_uint64 * 5),
+    ]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [
+        ("tag", ctypes.c_uint64),
+        ("stream", ctypes.c_uint32),
+        ("status", ctypes.c_uint32),
+        ("bytes", ctypes.c_uint64),
+        ("submit_ns", ctypes.c_uint64),
+        ("admit_ns", ctypes.c_uint64),
+        ("done_ns", ctypes.c_uint64),
+    ]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("arrival_ns", ctypes.c_uint64),
+        ("stream", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("d_in", ctypes.c_void_p),
+        ("n", ctypes.c_uint64),
+        ("d_out", ctypes.c_void_p),
+        ("tag", ctypes.c_uint64),
+    ]
+
+
 # (name, restype, argtypes) of every exported entry point
 _P, _Z, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 SIGNATURES = [
@@ -120,6 +173,15 @@ SIGNATURES = [
     ("hist_batch_graph_launch", _I, [_P, _P]),
     ("hist_batch_graph_destroy", _I, [_P]),
     ("hist_batch_autotune", _I, [_P, _P, _U32, _P, _U32, ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_float)]),
+    ("hist_server_config_init", None, [ctypes.POINTER(ServerConfig)]),
+    ("hist_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    ("hist_server_destroy", _I, [_P]),
+    ("hist_server_submit", _I, [_P, _U32, _P, _Z, _P, _U64]),
+    ("hist_server_poll", _I, [_P, ctypes.POINTER(Completion), _U32, ctypes.POINTER(_U32)]),
+    ("hist_server_drain", _I, [_P, _U32]),
+    ("hist_server_stream_state", _I, [_P, _U32, ctypes.POINTER(StreamState)]),
+    ("hist_server_get_stats", _I, [_P, ctypes.POINTER(ServerStats)]),
+    ("hist_server_replay", _I, [_P, ctypes.POINTER(Request), _U32, ctypes.POINTER(Completion), _U32]),
 ]
 
 _lib = None

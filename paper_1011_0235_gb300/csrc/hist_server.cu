@@ -1,0 +1,614 @@
+// hist_server.cu -- a serving loop for histogram requests on many streams.
+//
+// Each request is the next chunk of one of `streams` independent streams; a
+// stream's adaptive state (the switch flag, the binning pattern and the
+// layout derived from it, the totals and the last histogram) stays on the
+// device, so a request runs the kernel and pattern chosen from its stream's
+// previous request (Sec. III.B / III.C), exactly as hist_stream_push would.
+//
+// Continuous batching on the host: submitted requests wait in a FIFO queue;
+// whenever a batch slot is free, the queued requests that fit the HBM byte
+// budget and whose stream has no request on the GPU form a batch, launched
+// on the slot's own CUDA stream, so batches overlap on the device.  A batch
+// is one kernel with no device-side waits: the CTAs split the requests by a
+// cost model (bytes plus a fixed cost per request), count each piece with
+// its stream's layout and add it into the request's accumulator; the CTA
+// that completes a request (a done-bytes counter) computes its degeneracy
+// and next pattern and updates the stream's state.  A request counted whole
+// by one CTA skips the accumulator.  Completion is seen by polling the
+// slot's event.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <list>
+#include <new>
+#include <vector>
+
+#include "hist.h"
+#include "hist_device.cuh"
+#include "hist_internal.h"
+
+using namespace histdev;
+using namespace histlib;
+
+namespace {
+
+constexpr uint32_t kSrvMaxBatch = HIST_SERVER_MAX_BATCH;  // <= kThreads (one prefix lane each)
+constexpr uint32_t kSrvMaxSlots = HIST_SERVER_MAX_INFLIGHT;
+// cost of a request beyond its bytes, in bytes: about what one CTA counts
+// while it reduces its table and runs a request's epilogue
+constexpr unsigned long long kReqCost = 64ull << 10;
+// cost units per CTA of a batch (the grid is at most one CTA per SM)
+constexpr unsigned long long kCtaCost = 256ull << 10;
+// dynamic shared memory: table, slot table, request cost prefix (u64 per request + 1)
+constexpr size_t kSrvSmem = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kSrvMaxBatch + 1) * 8;
+
+static_assert(kSrvMaxBatch <= (uint32_t)kThreads, "one prefix lane per request");
+
+// Per-stream state on the device.
+struct SrvStream {
+  unsigned long long totals[HIST_BINS];
+  uint32_t last_hist[HIST_BINS];
+  hist_pattern pattern;       // pattern for the stream's next request
+  hist_pattern last_pattern;  // pattern its last request was given
+  unsigned long long chunks;
+  uint32_t flag;              // switch from the last request
+  uint32_t last_kernel;       // kernel the last request ran
+  uint32_t shift;             // 1 if `pattern` has one k = 2^lk for all bins at off = b k
+  uint32_t lk;
+};
+
+struct SrvReq {
+  const uint8_t* in;
+  uint32_t* out;
+  uint32_t n;
+  uint32_t stream;
+};
+
+// Per batch slot, on the device.  acc and done return to zero when a
+// request's epilogue has read them, so a slot needs clearing only once.
+struct SrvSlot {
+  SrvReq req[kSrvMaxBatch];
+  uint32_t acc[kSrvMaxBatch][HIST_BINS];  // partial sums of split requests
+  unsigned long long done[kSrvMaxBatch];  // bytes of each split request counted
+};
+
+struct SrvArgs {
+  SrvStream* streams;
+  SrvSlot* slot;
+  uint32_t count;
+  uint32_t budget;
+  uint32_t theta;
+  uint32_t mode;
+};
+
+__device__ __forceinline__ uint32_t srv_kernel_for(uint32_t mode, uint32_t flag) {
+  return mode == HIST_MODE_AUTO ? flag : (mode == HIST_MODE_PLAIN ? HIST_FLAG_PLAIN : HIST_FLAG_ADAPTIVE);
+}
+
+// Whether P gives every bin the same k = 2^lk at off = b k (all threads call).
+__device__ bool srv_is_shift(const hist_pattern& P) {
+  const bool act = threadIdx.x < HIST_BINS;
+  const uint32_t lk0 = P.log2k[0];
+  const int ok = !act || (P.log2k[threadIdx.x] == lk0 && lk0 <= 5 &&
+                          (uint32_t)P.off[threadIdx.x] == ((uint32_t)threadIdx.x << lk0));
+  return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ void srv_copy_words(void* dst, const void* src, int words) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+}
+
+// pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total.
+__device__ void srv_cost_prefix(const SrvSlot* slot, uint32_t count, unsigned long long* pre) {
+  __shared__ unsigned long long wsum[kWarps];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned long long c = t < (int)count ? (unsigned long long)slot->req[t].n + kReqCost : 0ull;
+  unsigned long long x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  unsigned long long before = 0;
+  for (int i = 0; i < w; ++i) before += wsum[i];
+  if (t < (int)count) pre[t] = before + x - c;
+  if (t == (int)count - 1) pre[count] = before + x;
+  __syncthreads();
+}
+
+// Request q is complete and cs.hist holds its histogram: write its output
+// and advance its stream's state.  All threads of the CTA call.
+__device__ void srv_epilogue(const SrvArgs& a, const SrvReq& q, CtaShared& cs, EpiShared& es) {
+  SrvStream* st = a.streams + q.stream;
+  const uint32_t kernel = srv_kernel_for(a.mode, st->flag);
+  __syncthreads();  // cs.hist is written; every thread has read the old flag
+  const hist_degeneracy_result d = block_epilogue(cs.hist, q.n, a.budget, a.theta, cs.pat, es);
+  __syncthreads();
+  if (threadIdx.x < HIST_BINS) {
+    const uint32_t h = cs.hist[threadIdx.x];
+    if (q.out) q.out[threadIdx.x] = h;
+    st->totals[threadIdx.x] += h;
+    st->last_hist[threadIdx.x] = h;
+  }
+  srv_copy_words(&st->last_pattern, &st->pattern, (int)(sizeof(hist_pattern) / 4));
+  __syncthreads();
+  srv_copy_words(&st->pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
+  const bool shift = srv_is_shift(cs.pat);
+  if (threadIdx.x == 0) {
+    st->shift = shift ? 1u : 0u;
+    st->lk = shift ? cs.pat.log2k[0] : 0u;
+    st->last_kernel = kernel;
+    st->flag = d.flag;
+    st->chunks += 1;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(SrvArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;
+  unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
+  __shared__ CtaShared cs;
+  __shared__ EpiShared es;
+  __shared__ uint32_t part[kThreads];
+  __shared__ int last;
+
+  zero_table(table);
+  srv_cost_prefix(a.slot, a.count, pre);
+  const unsigned long long W = pre[a.count];
+  const unsigned long long lo = W * blockIdx.x / gridDim.x;
+  const unsigned long long hi = W * (blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  // the request holding cost position lo
+  uint32_t r = 0, rh = a.count;
+  while (r + 1 < rh) {
+    const uint32_t mid = (r + rh) >> 1;
+    if (pre[mid] <= lo) r = mid;
+    else rh = mid;
+  }
+  for (; r < a.count && pre[r] < hi; ++r) {
+    const SrvReq q = a.slot->req[r];
+    const unsigned long long p0 = pre[r];
+    if (q.n == 0) {
+      // no bytes: the CTA holding the request's first cost position folds it
+      if (p0 >= lo) {
+        if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
+        srv_epilogue(a, q, cs, es);
+      }
+      continue;
+    }
+    // this CTA's bytes of the request: its cost range cut to [0, n)
+    const unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
+    const unsigned long long e0 = hi - p0 < (unsigned long long)q.n ? hi - p0 : (unsigned long long)q.n;
+    if (b0 >= e0) continue;
+    const SrvStream* st = a.streams + q.stream;
+    int path = PATH_PLAIN, lk = 0;
+    if (srv_kernel_for(a.mode, st->flag) == HIST_FLAG_ADAPTIVE) {
+      if (st->shift) {
+        path = PATH_SHIFT;
+        lk = (int)st->lk;
+      } else {
+        srv_copy_words(&cs.pat, &st->pattern, (int)(sizeof(hist_pattern) / 4));
+        __syncthreads();
+        classify_pattern(cs.pat, lut, cs);  // writes the slot table
+        path = cs.path;
+        lk = cs.lk;
+      }
+    }
+    const uint8_t* base = q.in + b0;
+    const size_t len = (size_t)(e0 - b0);
+    const Split sp = split_bytes(base, len);
+    count_range_dispatch<4>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
+                            threadIdx.x, blockDim.x);
+    flush_table(path, lk, table, cs.pat, part, cs);
+    count_edges(base, sp, cs);
+    zero_table(table);
+    __syncthreads();
+    if (b0 == 0 && e0 == q.n) {
+      // the whole request
+      if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = cs.res[threadIdx.x];
+      srv_epilogue(a, q, cs, es);
+      continue;
+    }
+    if (threadIdx.x < HIST_BINS) {
+      if (cs.res[threadIdx.x]) atomicAdd(&a.slot->acc[r][threadIdx.x], cs.res[threadIdx.x]);
+      __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned long long before = atomicAdd(&a.slot->done[r], (unsigned long long)len);
+      last = before + len == (unsigned long long)q.n;
+    }
+    __syncthreads();
+    if (last) {
+      // every other piece of r was added (and fenced) before its done count
+      __threadfence();
+      if (threadIdx.x < HIST_BINS) {
+        cs.hist[threadIdx.x] = __ldcg(&a.slot->acc[r][threadIdx.x]);
+        a.slot->acc[r][threadIdx.x] = 0;
+      }
+      if (threadIdx.x == 0) a.slot->done[r] = 0;
+      srv_epilogue(a, q, cs, es);
+    }
+  }
+}
+
+// Every stream starts with no chunks, the plain kernel and the default
+// pattern (one CTA).
+__global__ void server_init_kernel(SrvStream* s, uint32_t streams, uint32_t budget) {
+  __shared__ CtaShared cs;
+  __shared__ EpiShared es;
+  if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
+  __syncthreads();
+  block_epilogue(cs.hist, 0, budget, HIST_THETA_MILLI_DEFAULT, cs.pat, es);
+  __syncthreads();
+  const bool shift = srv_is_shift(cs.pat);
+  for (uint32_t i = 0; i < streams; ++i) {
+    SrvStream* st = s + i;
+    srv_copy_words(&st->pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
+    srv_copy_words(&st->last_pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
+    if (threadIdx.x == 0) {
+      st->shift = shift ? 1u : 0u;
+      st->lk = shift ? cs.pat.log2k[0] : 0u;
+      st->flag = HIST_FLAG_PLAIN;
+      st->last_kernel = HIST_FLAG_PLAIN;
+    }
+  }
+}
+
+uint64_t now_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+struct PendingReq {
+  uint32_t stream;
+  const uint8_t* in;
+  size_t n;
+  uint32_t* out;
+  uint64_t tag;
+  uint64_t submit_ns;
+};
+
+struct BatchSlot {
+  bool busy = false;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done = nullptr;
+  SrvSlot* d_slot = nullptr;
+  SrvReq* h_req = nullptr;  // pinned staging of the request table
+  std::vector<PendingReq> reqs;
+  uint64_t admit_ns = 0;
+  uint64_t bytes = 0;
+};
+
+}  // namespace
+
+struct hist_server {
+  hist_server_config cfg;
+  SrvStream* d_streams = nullptr;
+  std::vector<uint8_t> stream_busy;  // a request of the stream is on the GPU
+  std::vector<uint64_t> scan_mark;   // the stream was passed over in admission scan #mark
+  uint64_t scan = 0;
+  std::list<PendingReq> queue;  // FIFO; admission erases from the middle
+  BatchSlot slot[kSrvMaxSlots];
+  uint64_t inflight_bytes = 0;
+  int sms = 0;
+  hist_server_stats stats;
+};
+
+namespace {
+
+bool server_config_ok(const hist_server_config* c) {
+  return c && c->streams >= 1 && c->streams <= HIST_SERVER_MAX_STREAMS && c->max_batch >= 1 &&
+         c->max_batch <= kSrvMaxBatch && c->max_inflight >= 1 && c->max_inflight <= kSrvMaxSlots &&
+         c->hbm_budget > 0 && c->theta_milli <= 1000 && c->pattern_budget >= HIST_BUDGET_MIN &&
+         c->pattern_budget <= HIST_BUDGET_MAX && c->mode <= HIST_MODE_ADAPTIVE;
+}
+
+// Retire finished batches, writing at most `cap` completions to `out` (out
+// null: discard them); returns how many were written or discarded.
+uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
+  uint32_t n = 0;
+  for (uint32_t k = 0; k < s->cfg.max_inflight; ++k) {
+    BatchSlot& f = s->slot[k];
+    if (!f.busy) continue;
+    if (out && n + f.reqs.size() > cap) continue;  // no room for this batch's records yet
+    const cudaError_t q = cudaEventQuery(f.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) {
+      *err = cuda_fail(q);
+      return n;
+    }
+    const uint64_t t = now_ns();
+    for (const PendingReq& r : f.reqs) {
+      s->stream_busy[r.stream] = 0;
+      if (out) {
+        hist_completion& c = out[n];
+        c.tag = r.tag;
+        c.stream = r.stream;
+        c.status = 0;
+        c.bytes = r.n;
+        c.submit_ns = r.submit_ns;
+        c.admit_ns = f.admit_ns;
+        c.done_ns = t;
+      }
+      ++n;
+      s->stats.completed += 1;
+      s->stats.bytes += r.n;
+    }
+    s->inflight_bytes -= f.bytes;
+    f.reqs.clear();
+    f.busy = false;
+  }
+  return n;
+}
+
+// Launch one batch if a slot is free and the queue holds admissible requests.
+// FIFO order; a request whose stream has a request on the GPU (or an earlier
+// one still queued) is passed over, and the scan stops at the first request
+// that does not fit the byte budget, so no request waits forever behind
+// smaller later ones.
+int admit(hist_server* s) {
+  BatchSlot* f = nullptr;
+  for (uint32_t k = 0; k < s->cfg.max_inflight; ++k)
+    if (!s->slot[k].busy) {
+      f = &s->slot[k];
+      break;
+    }
+  if (!f || s->queue.empty()) return HIST_OK;
+  f->reqs.clear();
+  f->bytes = 0;
+  const uint64_t mark = ++s->scan;
+  for (auto it = s->queue.begin(); it != s->queue.end() && f->reqs.size() < s->cfg.max_batch;) {
+    const PendingReq& r = *it;
+    if (s->stream_busy[r.stream] || s->scan_mark[r.stream] == mark) {
+      s->scan_mark[r.stream] = mark;  // keep the stream's order
+      ++it;
+      continue;
+    }
+    if (s->inflight_bytes + f->bytes + r.n > s->cfg.hbm_budget) {
+      s->stats.deferred += 1;
+      break;
+    }
+    s->stream_busy[r.stream] = 1;
+    f->bytes += r.n;
+    f->reqs.push_back(r);
+    it = s->queue.erase(it);
+  }
+  if (f->reqs.empty()) return HIST_OK;
+  const uint32_t count = (uint32_t)f->reqs.size();
+  for (uint32_t i = 0; i < count; ++i) {
+    f->h_req[i].in = f->reqs[i].in;
+    f->h_req[i].out = f->reqs[i].out;
+    f->h_req[i].n = (uint32_t)f->reqs[i].n;
+    f->h_req[i].stream = f->reqs[i].stream;
+  }
+  auto undo = [&]() {
+    for (const PendingReq& r : f->reqs) s->stream_busy[r.stream] = 0;
+    s->queue.insert(s->queue.begin(), f->reqs.begin(), f->reqs.end());
+    f->reqs.clear();
+  };
+  cudaError_t e = cudaMemcpyAsync(f->d_slot->req, f->h_req, count * sizeof(SrvReq), cudaMemcpyHostToDevice, f->cs);
+  if (e != cudaSuccess) {
+    undo();
+    return cuda_fail(e);
+  }
+  unsigned long long cost = 0;
+  for (const PendingReq& r : f->reqs) cost += r.n + kReqCost;
+  unsigned long long grid = (cost + kCtaCost - 1) / kCtaCost;
+  if (grid > (unsigned long long)s->sms) grid = (unsigned long long)s->sms;
+  if (grid < 1) grid = 1;
+  SrvArgs a;
+  a.streams = s->d_streams;
+  a.slot = f->d_slot;
+  a.count = count;
+  a.budget = s->cfg.pattern_budget;
+  a.theta = s->cfg.theta_milli;
+  a.mode = s->cfg.mode;
+  server_batch_kernel<<<(unsigned)grid, kThreads, kSrvSmem, f->cs>>>(a);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventRecord(f->done, f->cs);
+  if (e != cudaSuccess) {
+    undo();
+    return cuda_fail(e);
+  }
+  f->busy = true;
+  f->admit_ns = now_ns();
+  s->inflight_bytes += f->bytes;
+  s->stats.batches += 1;
+  return HIST_OK;
+}
+
+bool server_idle(const hist_server* s) {
+  if (!s->queue.empty()) return false;
+  for (uint32_t k = 0; k < s->cfg.max_inflight; ++k)
+    if (s->slot[k].busy) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hist_server_config_init(hist_server_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->streams = 256;
+  c->max_batch = 256;
+  c->max_inflight = 4;
+  c->theta_milli = HIST_THETA_MILLI_DEFAULT;
+  c->pattern_budget = HIST_BUDGET_MAX;
+  c->mode = HIST_MODE_AUTO;
+  c->hbm_budget = 32ull << 30;
+}
+
+int hist_server_create(const hist_server_config* cfg, hist_server** out) {
+  if (!out || !server_config_ok(cfg)) return HIST_EINVAL;
+  *out = nullptr;
+  hist_server* s = new (std::nothrow) hist_server();
+  if (!s) return HIST_ENOMEM;
+  s->cfg = *cfg;
+  s->stream_busy.assign(cfg->streams, 0);
+  s->scan_mark.assign(cfg->streams, 0);
+  s->sms = sm_count();
+  memset(&s->stats, 0, sizeof(s->stats));
+  static int attr_done[kMaxDevices];
+  int rc = s->sms > 0 ? ensure_smem_attr_bytes((const void*)server_batch_kernel, attr_done, kSrvSmem) : HIST_ECUDA;
+  if (rc == HIST_OK) {
+    cudaError_t e = cudaMalloc((void**)&s->d_streams, sizeof(SrvStream) * cfg->streams);
+    if (e == cudaSuccess) e = cudaMemset(s->d_streams, 0, sizeof(SrvStream) * cfg->streams);
+    for (uint32_t k = 0; e == cudaSuccess && k < cfg->max_inflight; ++k) {
+      BatchSlot& f = s->slot[k];
+      e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&f.d_slot, sizeof(SrvSlot));
+      if (e == cudaSuccess) e = cudaMemset(f.d_slot, 0, sizeof(SrvSlot));
+      if (e == cudaSuccess) e = cudaHostAlloc((void**)&f.h_req, sizeof(SrvReq) * kSrvMaxBatch, cudaHostAllocDefault);
+    }
+    if (e == cudaSuccess) {
+      server_init_kernel<<<1, 256>>>(s->d_streams, cfg->streams, cfg->pattern_budget);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e);
+  }
+  if (rc) {
+    hist_server_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return HIST_OK;
+}
+
+int hist_server_destroy(hist_server* s) {
+  if (!s) return HIST_EINVAL;
+  cudaError_t e = cudaSuccess;
+  for (uint32_t k = 0; k < kSrvMaxSlots; ++k) {
+    BatchSlot& f = s->slot[k];
+    if (f.cs) {
+      const cudaError_t w = cudaStreamSynchronize(f.cs);
+      if (e == cudaSuccess) e = w;
+    }
+  }
+  for (uint32_t k = 0; k < kSrvMaxSlots; ++k) {
+    BatchSlot& f = s->slot[k];
+    if (f.d_slot) cudaFree(f.d_slot);
+    if (f.h_req) cudaFreeHost(f.h_req);
+    if (f.done) cudaEventDestroy(f.done);
+    if (f.cs) cudaStreamDestroy(f.cs);
+  }
+  if (s->d_streams) cudaFree(s->d_streams);
+  delete s;
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
+int hist_server_submit(hist_server* s, uint32_t stream, const uint8_t* d_in, size_t n, uint32_t* d_out,
+                       uint64_t tag) {
+  if (!s || stream >= s->cfg.streams || (!d_in && n) || n >= ((size_t)1 << 32)) return HIST_EINVAL;
+  if (n > s->cfg.hbm_budget) return HIST_EBUDGET;
+  s->queue.push_back(PendingReq{stream, d_in, n, d_out, tag, now_ns()});
+  s->stats.submitted += 1;
+  return HIST_OK;
+}
+
+int hist_server_poll(hist_server* s, hist_completion* out, uint32_t cap, uint32_t* n_out) {
+  if (n_out) *n_out = 0;
+  if (!s || (cap && !out)) return HIST_EINVAL;
+  int err = HIST_OK;
+  const uint32_t n = retire(s, cap ? out : nullptr, cap, &err);
+  if (n_out && cap) *n_out = n;
+  if (err) return err;
+  return admit(s);
+}
+
+int hist_server_drain(hist_server* s, uint32_t timeout_ms) {
+  if (!s) return HIST_EINVAL;
+  const uint64_t t0 = now_ns();
+  while (!server_idle(s)) {
+    int err = HIST_OK;
+    retire(s, nullptr, 0, &err);
+    if (err) return err;
+    const int rc = admit(s);
+    if (rc) return rc;
+    if (timeout_ms && now_ns() - t0 > (uint64_t)timeout_ms * 1000000ull) return HIST_ETIMEDOUT;
+  }
+  return HIST_OK;
+}
+
+int hist_server_stream_state(hist_server* s, uint32_t stream, hist_stream_state* h) {
+  if (!s || !h || stream >= s->cfg.streams) return HIST_EINVAL;
+  const int rc = hist_server_drain(s, 0);
+  if (rc) return rc;
+  SrvStream tmp;
+  const cudaError_t e = cudaMemcpy(&tmp, s->d_streams + stream, sizeof(SrvStream), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  memset(h, 0, sizeof(*h));
+  memcpy(h->totals, tmp.totals, sizeof(h->totals));
+  memcpy(h->last_hist, tmp.last_hist, sizeof(h->last_hist));
+  h->pattern = tmp.pattern;
+  h->last_pattern = tmp.last_pattern;
+  h->chunks = tmp.chunks;
+  h->flag = tmp.flag;
+  h->last_kernel = tmp.last_kernel;
+  return HIST_OK;
+}
+
+int hist_server_get_stats(hist_server* s, hist_server_stats* out) {
+  if (!s || !out) return HIST_EINVAL;
+  *out = s->stats;
+  out->queued = s->queue.size();
+  out->inflight_bytes = s->inflight_bytes;
+  return HIST_OK;
+}
+
+int hist_server_replay(hist_server* s, const hist_request* reqs, uint32_t count, hist_completion* out,
+                       uint32_t timeout_ms) {
+  if (!s || (count && (!reqs || !out))) return HIST_EINVAL;
+  for (uint32_t i = 0; i < count; ++i) {
+    const hist_request& r = reqs[i];
+    if (r.stream >= s->cfg.streams || (!r.d_in && r.n) || r.n >= (1ull << 32) ||
+        (i && r.arrival_ns < reqs[i - 1].arrival_ns))
+      return HIST_EINVAL;
+    if (r.n > s->cfg.hbm_budget) return HIST_EBUDGET;
+  }
+  if (!server_idle(s)) return HIST_ESTATE;
+  std::vector<hist_completion> buf((size_t)s->cfg.max_batch * s->cfg.max_inflight);
+  uint32_t done = 0, next = 0;
+  const uint64_t t0 = now_ns();
+  while (done < count) {
+    const uint64_t now = now_ns() - t0;
+    if (timeout_ms && now > (uint64_t)timeout_ms * 1000000ull) return HIST_ETIMEDOUT;
+    while (next < count && reqs[next].arrival_ns <= now) {
+      const hist_request& r = reqs[next];
+      s->queue.push_back(PendingReq{r.stream, r.d_in, (size_t)r.n, r.d_out, next, t0 + r.arrival_ns});
+      s->stats.submitted += 1;
+      ++next;
+    }
+    uint32_t n = 0;
+    const int rc = hist_server_poll(s, buf.data(), (uint32_t)buf.size(), &n);
+    if (rc) return rc;
+    for (uint32_t i = 0; i < n; ++i) {
+      hist_completion c = buf[i];
+      const uint64_t idx = c.tag;
+      c.tag = reqs[idx].tag;
+      c.submit_ns -= t0;
+      c.admit_ns -= t0;
+      c.done_ns -= t0;
+      out[idx] = c;
+    }
+    done += n;
+  }
+  return HIST_OK;
+}
+
+}  // extern "C"

@@ -105,3 +105,67 @@ def test_argument_errors_without_gpu(lib):
     assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == _abi.EINVAL
     cfg.theta_milli, cfg.mode = 450, 3
     assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == _abi.EINVAL
+
+
+def test_server_argument_errors_without_gpu(lib):
+    cfg = _abi.ServerConfig()
+    lib.hist_server_config_init(ctypes.byref(cfg))
+    assert (cfg.streams, cfg.max_batch, cfg.max_inflight, cfg.theta_milli, cfg.pattern_budget, cfg.mode,
+            cfg.hbm_budget) == (256, 256, 4, 450, 8192, 0, 32 << 30)
+    h = ctypes.c_void_p()
+    for field, bad in (("streams", 0), ("streams", _abi.HIST_SERVER_MAX_STREAMS + 1), ("max_batch", 0),
+                       ("max_batch", _abi.HIST_SERVER_MAX_BATCH + 1), ("max_inflight", 0),
+                       ("max_inflight", _abi.HIST_SERVER_MAX_INFLIGHT + 1), ("hbm_budget", 0),
+                       ("theta_milli", 1001), ("pattern_budget", 255), ("pattern_budget", 8193), ("mode", 3)):
+        c = _abi.ServerConfig.from_buffer_copy(bytes(cfg))
+        setattr(c, field, bad)
+        assert lib.hist_server_create(ctypes.byref(c), ctypes.byref(h)) == _abi.EINVAL, field
+    assert lib.hist_server_create(None, ctypes.byref(h)) == _abi.EINVAL
+    assert lib.hist_server_submit(None, 0, None, 0, None, 0) == _abi.EINVAL
+    assert lib.hist_server_poll(None, None, 0, None) == _abi.EINVAL
+    assert lib.hist_server_drain(None, 0) == _abi.EINVAL
+    assert lib.hist_server_destroy(None) == _abi.EINVAL
+    assert lib.hist_server_replay(None, None, 0, None, 0) == _abi.EINVAL
+
+
+# struct name in hist.h -> ctypes class of the binding
+_STRUCTS = {
+    "hist_pattern": "HistPattern",
+    "hist_degeneracy_result": "DegeneracyResult",
+    "hist_config": "HistConfig",
+    "hist_batch_tuning": "BatchTuning",
+    "hist_stream_state": "StreamState",
+    "hist_server_config": "ServerConfig",
+    "hist_server_stats": "ServerStats",
+    "hist_completion": "Completion",
+    "hist_request": "Request",
+}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof and every field offset of the header's structs, as gcc lays
+    them out, equal the ctypes binding's."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hist.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(_abi, pyname)
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for row in out:
+        if row:
+            c, f, v = row.split()
+            got[(c, f)] = int(v)
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(_abi, pyname)
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f in cls._fields_:
+            assert got[(cname, f[0])] == getattr(cls, f[0]).offset, (cname, f[0])
