@@ -380,7 +380,7 @@ def run_native(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
     value = world * nbytes * args.steps / el / 1e9
-    # the adaptive stream at the full table runs decoupled: one launch per
+    # the adaptive stream at the full table runs batch_flat_kernel: one launch per
     # push_many of up to STREAM_MAX_BATCH chunks, nothing left for flush
     launches_per_step = -(-chunks // STREAM_MAX_BATCH)
 
@@ -390,14 +390,14 @@ def run_native(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
 
-    # dominant (only) kernel of the step: batch_decoupled_kernel, all chunks
+    # dominant (only) kernel of the step: batch_flat_kernel, all chunks
     # of a push_many in one launch; algorithmic bytes = the pixels it reads
     avg_launch_s = el / (args.steps * launches_per_step)
     bytes_per_launch = nbytes // launches_per_step
     achieved = bytes_per_launch / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": recorded_traffic("batch_decoupled_kernel"),
-                "kernel": "batch_decoupled_kernel", "peak_source": peak_src,
+                "frac": round(achieved / hbm, 4), "traffic": recorded_traffic("batch_flat_kernel"),
+                "kernel": "batch_flat_kernel", "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launch_ms": round(avg_launch_s * 1e3, 4)}
 

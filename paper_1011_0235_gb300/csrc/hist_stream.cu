@@ -1,8 +1,10 @@
 // hist_stream.cu -- the chunked stream of Sec. III.B with the kernel switch of
 // Sec. III.C, all on the device.
 //
-// A batch of chunks runs in one cooperative launch with one 1024-thread CTA
-// per SM.  For each chunk every CTA
+// A stream whose chunk kernels and layouts depend on the previous chunk's
+// histogram (the AUTO mode, and the adaptive mode below the full budget)
+// runs each batch of chunks in one cooperative launch of batch_synced_kernel
+// with one 1024-thread CTA per SM.  For each chunk every CTA
 //   1. waits until the previous chunk's histogram is complete: each CTA adds
 //      its per-bin sums into 4 global replicas, then (after a fence) one
 //      arrival and its pixel count into one 64-bit counter; the chunk is
@@ -10,15 +12,17 @@
 //      size (the arrivals matter: a CTA with no pixels must also be past its
 //      earlier steps).  One thread per CTA polls the counter (bounded), then
 //      the CTA reads the replicas once;
-//   2. derives this chunk's switch and binning pattern from that histogram in
-//      one warp (every CTA computes the same values); CTA 0 folds the previous
-//      chunk into the stream state (totals, last histogram, output);
-//   3. counts its slice of the chunk with the chosen kernel from registers
-//      that were loaded while the previous chunk was still being counted, and
-//      loads the next chunk's slice as it goes;
+//   2. derives this chunk's switch and binning pattern from that histogram
+//      (every CTA computes the same values); every CTA folds a slice of the
+//      previous chunk into the stream state (totals, last histogram, output);
+//   3. counts its slice of the chunk with the chosen kernel, the next
+//      chunk's slice streaming into L2 meanwhile;
 //   4. adds its per-bin sums into the chunk's replicas.
 // The last chunk of a batch stays pending: its epilogue runs at the head of
 // the next batch or in the finish kernel (hist_stream_flush).
+//
+// The other streams (plain mode; adaptive mode at the full budget) run
+// batch_flat_kernel, which needs no waits (see the comment above it).
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -47,8 +51,14 @@ struct StreamDev {
   // CTAs that published into rep[i] (high 32 bits) and their pixels (low 32
   // bits), one 128-byte line each
   unsigned long long cnt[3][16];
-  uint32_t brep[2][kMaxBatch][kStreamReplicas][HIST_BINS];  // decoupled batches: partials per chunk, two sets
-  unsigned long long bcnt[2][kMaxBatch][16];                 // decoupled: pixels published per chunk
+  // flat batches: per-chunk sums and counted bytes (back to zero once the
+  // chunk's epilogue has read them), chunks of the running launch completed,
+  // the binning patterns of its last two chunks and its last switch
+  uint32_t facc[kMaxBatch][HIST_BINS];
+  unsigned long long fdone[kMaxBatch];
+  unsigned long long fchunks;
+  hist_pattern fpat[2];
+  uint32_t fflag;
   unsigned long long totals[HIST_BINS];
   uint32_t last_hist[HIST_BINS];
   hist_pattern pattern;       // pattern for the next chunk
@@ -374,183 +384,137 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
   return __syncthreads_and(ok);
 }
 
-constexpr size_t kDecSmemBytes = (size_t)(2 * kTableWords + kLutWords) * 4;  // two tables + slot table
+// ------------------------------------------------------------ flat batches --
+//
+// For the modes in which a chunk's kernel and layout do not depend on the
+// previous chunk's histogram -- the plain mode (the plain kernel uses no
+// pattern) and the adaptive mode at the full budget (the pattern rule then
+// gives the full table after every non-empty chunk and the default pattern
+// after an empty one) -- the chunks of a batch need not be counted one after
+// the other.  batch_flat_kernel splits the batch's chunks, placed end to end,
+// into one contiguous range per CTA by a cost model (a chunk costs its bytes
+// plus kFlatChunkCost), so a CTA counts one or two pieces of chunks and
+// reduces its table only where its range crosses a chunk boundary.  A CTA
+// adds a piece's per-bin sums into the chunk's accumulator and its bytes
+// into the chunk's counter; the CTA whose bytes complete a chunk runs the
+// chunk's epilogue (switch, pattern, output, totals, and the check that the
+// layout the next chunk was counted with is the one the rule gives), and
+// the CTA that completes the batch's last epilogue writes the stream state.
+// No CTA waits for another, so the launch is not cooperative, and a chunk's
+// accumulator returns to zero in its epilogue.
 
-// Lagged reduction of a counted table.  Thread t takes bin t >> 2 and reads 8
-// of its slots (4 threads per bin); the loads are issued right after the
-// chunk's barrier and consumed only after the next chunk has been counted, so
-// no thread waits for them behind the atomics still in the shared-memory
-// pipe.
-__device__ __forceinline__ void lag_load(const uint32_t* tab, int path, int lk, const hist_pattern& P, uint32_t (&v)[8]) {
-  const int t = threadIdx.x, b = t >> 2, q = t & 3;
-  if (path == PATH_PLAIN) {
+constexpr unsigned long long kFlatChunkCost = 64ull << 10;  // cost of a chunk beyond its bytes
+// dynamic shared memory: table, slot table, chunk cost prefix (u64 per chunk + 1)
+constexpr size_t kFlatSmemBytes = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kMaxBatch + 1) * 8;
+static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
+
+// pre[j] = sum over chunks before j of (n + kFlatChunkCost); pre[count] = total.
+__device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre) {
+  __shared__ unsigned long long wsum[kWarps];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned long long c = t < (int)a.count ? (unsigned long long)a.c[t].n + kFlatChunkCost : 0ull;
+  unsigned long long x = c;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = tab[(q + 4 * i) * HIST_BINS + b];
-  } else if (path == PATH_SHIFT && lk == 5) {
-    // two 16-byte pieces of the bin's row: 16-byte groups 2q + s + (b & 1)
-    // (mod 8), s = 0, 1, so the 8 threads of each shared-memory phase (two
-    // bins) touch 8 different bank quads
-    const uint4* r4 = reinterpret_cast<const uint4*>(tab + (b << 5));
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const uint4 w = r4[(2 * q + s + (b & 1)) & 7];
-      v[4 * s] = w.x;
-      v[4 * s + 1] = w.y;
-      v[4 * s + 2] = w.z;
-      v[4 * s + 3] = w.w;
-    }
-  } else {
-    uint32_t o, k;
-    if (path == PATH_SHIFT) {
-      o = (uint32_t)b << lk;
-      k = 1u << lk;
-    } else {
-      o = P.off[b];
-      k = 1u << (P.log2k[b] > 5 ? 5u : P.log2k[b]);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint32_t j = (uint32_t)(q + 4 * i);
-      v[i] = j < k ? tab[(o + j) & (kTableWords - 1)] : 0u;
-    }
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-}
-
-// Finish the lagged reduction of chunk m on table p: the bin's sum, its
-// difference from the previous reduction of the table, added into chunk m's
-// partial buffer; the CTA's pixel count of chunk m into counts[m].
-__device__ __forceinline__ void lag_finish(const uint32_t (&v)[8], uint32_t* prev, uint32_t* rep, uint32_t* count) {
-  const int t = threadIdx.x, b = t >> 2, q = t & 3;
-  uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) s += v[i];
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  uint32_t d = 0;
-  if (q == 0) {
-    d = s - prev[b];
-    prev[b] = s;
-    if (d) atomicAdd(rep + b, d);
-  }
-  const uint32_t c = __reduce_add_sync(0xffffffffu, d);
-  if ((t & 31) == 0 && c) atomicAdd(count, c);
-}
-
-// General layout of a decoupled chunk (chunk 0: the stream's current pattern;
-// after an empty chunk: the default pattern), rare.  All threads call;
-// builds the slot table if the pattern needs one.
-__device__ __noinline__ void dec_layout_general(const BatchArgs& a, uint32_t j, const hist_pattern& used0,
-                                                hist_pattern& pat, int* path_lk, uint32_t* lut, CtaShared& cs) {
-  const int t = threadIdx.x;
+  if (lane == 31) wsum[w] = x;
   __syncthreads();
-  if (j == 0) {
-    copy_pattern(&pat, &used0);
-  } else {
-    // default pattern: the rule on an empty histogram
-    if (t < HIST_BINS) cs.hist[t] = 0;
-    __syncthreads();
-    if (t < 32) warp_epilogue(cs.hist, a.budget, a.theta, pat);
-  }
-  __syncthreads();
-  const int lane = t & 31;
-  const uint32_t lk0 = pat.log2k[0];
-  bool ok = lk0 <= 5;
-  for (int i = 0; i < 8; ++i) {
-    const int b = lane + 32 * i;
-    ok = ok && pat.log2k[b] == lk0 && (uint32_t)pat.off[b] == ((uint32_t)b << lk0);
-  }
-  if (__all_sync(0xffffffffu, ok)) {
-    path_lk[0] = PATH_SHIFT;
-    path_lk[1] = (int)lk0;
-    return;
-  }
-  path_lk[0] = PATH_LUT;
-  path_lk[1] = 0;
-  for (int e = t; e < kLutWords; e += kThreads) {
-    const int v = e >> 5, l = e & 31;
-    const uint32_t l2 = pat.log2k[v] > 5 ? 5u : pat.log2k[v];
-    lut[e] = ((uint32_t)pat.off[v] + ((uint32_t)l & ((1u << l2) - 1u))) & (kTableWords - 1);
-  }
+  unsigned long long before = 0;
+  for (int i = 0; i < w; ++i) before += wsum[i];
+  if (t < (int)a.count) pre[t] = before + x - c;
+  if (t == (int)a.count - 1) pre[a.count] = before + x;
   __syncthreads();
 }
 
-// Layout of chunk j of a decoupled batch (uniform over the CTA): PLAIN, the
-// full table (SHIFT 5), or a general pattern; written to `pat` for the
-// reduction of the table.
-__device__ __forceinline__ void dec_layout(const BatchArgs& a, uint32_t j, bool adaptive, const hist_pattern& used0,
-                                           hist_pattern& pat, int& path, int& lk, uint32_t* lut, CtaShared& cs) {
-  const int t = threadIdx.x;
+// Layout of chunk j (uniform over the CTA): the plain tables, the full table,
+// or -- for chunk 0 (the stream's current pattern) and after an empty chunk
+// (the default pattern) -- the pattern in cs.pat with its slot table.
+__device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j, uint32_t* lut, CtaShared& cs,
+                                                 EpiShared& es) {
+  __syncthreads();
+  if (j == 0) copy_pattern(&cs.pat, &a.st->pattern);
+  else saturated_pattern(0, a.budget, cs, es);
+  __syncthreads();
+  classify_pattern(cs.pat, lut, cs);
+}
+
+__device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool adaptive, uint32_t* lut,
+                                            CtaShared& cs, EpiShared& es, int& path, int& lk) {
   if (!adaptive) {
     path = PATH_PLAIN;
     lk = 0;
     return;
   }
   if (j > 0 && a.c[j - 1].n > 0) {
-    if (t < HIST_BINS) {
-      pat.off[t] = (uint16_t)(t * HIST_KMAX);
-      pat.log2k[t] = 5;
-    }
-    if (t == 0) {
-      pat.budget = a.budget;
-      pat.used = HIST_BINS * HIST_KMAX;
-    }
     path = PATH_SHIFT;
     lk = 5;
     return;
   }
-  int pl[2];
-  dec_layout_general(a, j, used0, pat, pl, lut, cs);
-  path = pl[0];
-  lk = pl[1];
+  flat_layout_general(a, j, lut, cs, es);
+  path = cs.path;
+  lk = cs.lk;
 }
 
-// Pixels of chunk d that phase 1 does not count (its unaligned head and tail).
-__device__ __forceinline__ uint32_t edge_bytes(const ChunkDesc& d) {
-  const Split sp = split_bytes(d.in, d.n);
-  return (uint32_t)(sp.head + sp.tail);
+__device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pattern* src) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
 }
 
-// Poll for chunk k's counted pixels, gather its histogram into cs.hist and add
-// its edge bytes.  All threads call.
-__device__ bool dec_gather(StreamDev* st, const ChunkDesc& d, uint32_t set, uint32_t k, uint32_t* part,
-                           CtaShared& cs) {
-  if (!poll_gather(st, &st->brep[set][k][0][0], &st->bcnt[set][k][0], d.n - edge_bytes(d), part, cs, nullptr))
-    return false;
-  count_edges_into(d.in, split_bytes(d.in, d.n), cs.hist);
+// Chunk j is complete and cs.hist holds its histogram.  All threads call.
+__device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, bool adaptive, hist_pattern& next,
+                                           CtaShared& cs, EpiShared& es) {
+  StreamDev* st = a.st;
+  const int t = threadIdx.x;
+  const uint32_t n = a.c[j].n;
   __syncthreads();
-  return true;
+  const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
+  __syncthreads();
+  if (t < HIST_BINS) {
+    const uint32_t h = cs.hist[t];
+    if (a.c[j].out) a.c[j].out[t] = h;
+    if (h) atomicAdd(&st->totals[t], (unsigned long long)h);
+    if (j + 1 == a.count) st->last_hist[t] = h;
+  }
+  if (adaptive && j + 1 < a.count) {
+    // chunk j+1 was counted with the layout the rule gives after n pixels
+    saturated_pattern(n, a.budget, cs, es);
+    if (!same_pattern(next, cs.pat) && t == 0) atomicExch(&st->status, kStatusPattern);
+  }
+  if (j + 2 >= a.count) copy_pattern(&st->fpat[j + 1 == a.count ? 1 : 0], &next);
+  if (j + 1 == a.count && t == 0) st->fflag = r.flag;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) cs.kernel = atomicAdd(&st->fchunks, 1ull) + 1 == a.count ? 1u : 0u;
+  __syncthreads();
+  if (cs.kernel) {
+    // every chunk's epilogue is done: the stream state after the batch
+    __threadfence();
+    if (a.count == 1) copy_pattern(&st->last_pattern, &st->pattern);
+    else copy_pattern_cg(&st->last_pattern, &st->fpat[0]);
+    __syncthreads();
+    copy_pattern_cg(&st->pattern, &st->fpat[1]);
+    if (t == 0) {
+      st->flag = __ldcg(&st->fflag);
+      st->last_kernel = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+      st->chunks += a.count;
+      st->fchunks = 0;
+    }
+  }
+  __syncthreads();
 }
 
-// Decoupled batch, for the modes in which chunk j+1's kernel and layout do not
-// depend on chunk j's histogram: the plain mode (the plain kernel uses no
-// pattern) and the adaptive mode at the full budget (the pattern rule then
-// gives the full table for every non-empty chunk, the default pattern after
-// an empty one).
-// Phase 1: the CTAs count the chunks back to back into two tables used in
-// turn, one barrier per chunk.  A table is reduced with loads issued after
-// its chunk's barrier and consumed after the next chunk (see lag_load), and
-// it is not cleared between its chunks: a chunk's counts are the difference
-// from the previous reduction of the same table (exact modulo 2^32); it is
-// cleared only when the next chunk on it changes layout.  The per-bin
-// differences go to the chunk's partial buffer (one set per batch, two sets
-// used alternately).
-// Phase 2: chunk k is folded by CTA k mod the CTA count, which adds the
-// chunk's unaligned edge bytes, computes its switch and pattern from its own
-// histogram, checks that the layout used for chunk k+1 is the one the rule
-// gives (stream status otherwise) and, for the last chunk, writes the stream
-// state.  Such a stream never leaves a chunk pending.
-__global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* tables = smem;                  // two tables of kTableWords
-  uint32_t* lut = smem + 2 * kTableWords;   // slot table, then scratch of phase 2
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
+  unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
-  __shared__ uint32_t counts[kMaxBatch];
-  __shared__ uint32_t prev[2][HIST_BINS];  // per table: the bin sums of its last reduction
-  __shared__ hist_pattern used0;           // the pattern chunk 0 was given
-  __shared__ hist_pattern next;            // a pattern computed in phase 2
-  __shared__ hist_pattern pats[2];
-  __shared__ int paths[2], lks[2];
+  __shared__ hist_pattern next;
+  __shared__ int last;
   StreamDev* st = a.st;
   const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
   auto mark = [&](uint32_t j, int phase) {
@@ -558,112 +522,78 @@ __global__ void __launch_bounds__(kThreads, 1) batch_decoupled_kernel(const __gr
       a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
   };
   const bool adaptive = a.mode != HIST_MODE_PLAIN;
-  const uint32_t kern = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-  const uint32_t set = a.first_buf & 1;  // partial-buffer set of this batch
 
-  prefetch_slice(a.c[0]);
-  for (int i = threadIdx.x; i < 2 * kTableWords / 4; i += kThreads)
-    reinterpret_cast<uint4*>(tables)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = threadIdx.x; i < (int)kMaxBatch; i += kThreads) counts[i] = 0;
-  for (int i = threadIdx.x; i < 2 * HIST_BINS; i += kThreads) (&prev[0][0])[i] = 0;
-  copy_pattern(&used0, &st->pattern);
-  __syncthreads();
-
-  // phase 1
-  uint32_t v[8];
-  for (uint32_t j = 0; j < a.count; ++j) {
-    const int p = j & 1;
+  zero_table(table);
+  flat_prefix(a, pre);
+  const unsigned long long W = pre[a.count];
+  const unsigned long long lo = W * blockIdx.x / gridDim.x;
+  const unsigned long long hi = W * (blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  // the chunk holding cost position lo
+  uint32_t j = 0, jh = a.count;
+  while (j + 1 < jh) {
+    const uint32_t mid = (j + jh) >> 1;
+    if (pre[mid] <= lo) j = mid;
+    else jh = mid;
+  }
+  for (; j < a.count && pre[j] < hi; ++j) {
+    const ChunkDesc d = a.c[j];
+    const unsigned long long p0 = pre[j];
+    if (d.n == 0) {
+      // no bytes: the CTA holding the chunk's first cost position folds it
+      if (p0 >= lo) {
+        mark(j, 0);
+        if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
+        flat_epilogue(a, j, adaptive, next, cs, es);
+        mark(j, 7);
+      }
+      continue;
+    }
+    // this CTA's bytes of the chunk: its cost range cut to [0, n)
+    const unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
+    const unsigned long long e0 = hi - p0 < (unsigned long long)d.n ? hi - p0 : (unsigned long long)d.n;
+    if (b0 >= e0) continue;
     mark(j, 0);
     int path, lk;
-    dec_layout(a, j, adaptive, used0, pats[p], path, lk, lut, cs);
-    if (threadIdx.x == 0) {
-      paths[p] = path;
-      lks[p] = lk;
-    }
+    flat_layout(a, j, adaptive, lut, cs, es, path, lk);
     mark(j, 2);
-    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
-    const Geo g = chunk_geo(a.c[j]);
-    count_range_dispatch<4>(path, lk, g.body, g.begin, g.end, tables + p * kTableWords, lut, threadIdx.x, kThreads);
-    mark(j, 3);
-    __syncthreads();  // chunk j's increments are all issued
+    const uint8_t* base = d.in + b0;
+    const uint32_t len = (uint32_t)(e0 - b0);
+    const Split sp = split_bytes(base, len);
+    count_range_dispatch<2>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
+                            threadIdx.x, kThreads);
     mark(j, 4);
-    if (j > 0) {
-      // chunk j-1 on the other table: its loads were issued one chunk ago
-      const int q = p ^ 1;
-      lag_finish(v, prev[q], &st->brep[set][j - 1][blockIdx.x % kStreamReplicas][0], &counts[j - 1]);
-      // the next chunk on that table, j+1, keeps the full-table layout of
-      // chunk j-1, or the table is cleared
-      const bool keep = !adaptive || (j > 1 && a.c[j - 2].n > 0 && a.c[j].n > 0);
-      if (!keep && j + 1 < a.count) {
-        __syncthreads();
-        uint4* t4 = reinterpret_cast<uint4*>(tables + q * kTableWords);
-        for (int i = threadIdx.x; i < kTableWords / 4; i += kThreads) t4[i] = make_uint4(0, 0, 0, 0);
-        if (threadIdx.x < HIST_BINS) prev[q][threadIdx.x] = 0;
-        __syncthreads();
-      }
-    }
-    lag_load(tables + p * kTableWords, path, lk, pats[p], v);
+    flush_table(path, lk, table, cs.pat, lut, cs);
+    count_edges(base, sp, cs);
+    zero_table(table);
+    __syncthreads();
     mark(j, 5);
-  }
-  __syncthreads();
-  {
-    const uint32_t m = a.count - 1;
-    const int q = m & 1;
-    lag_finish(v, prev[q], &st->brep[set][m][blockIdx.x % kStreamReplicas][0], &counts[m]);
-  }
-  // publish every chunk count after one fence
-  __threadfence();
-  __syncthreads();
-  for (uint32_t j = threadIdx.x; j < a.count; j += kThreads)
-    if (counts[j]) red_release_add(&st->bcnt[set][j][0], counts[j]);  // pixels only: no buffer is reused in a batch
-
-  // clear the other set (the previous batch's), a slice per CTA
-  for (uint32_t b = blockIdx.x; b < kMaxBatch; b += gridDim.x) {
-    uint32_t* r = &st->brep[set ^ 1][b][0][0];
-    for (int w = threadIdx.x; w < kStreamReplicas * HIST_BINS; w += kThreads) r[w] = 0;
-    if (threadIdx.x == 0) st->bcnt[set ^ 1][b][0] = 0;
-  }
-
-  // phase 2: fold chunk k in CTA k mod the CTA count
-  for (uint32_t k = blockIdx.x; k < a.count; k += gridDim.x) {
-    const uint32_t n = a.c[k].n;
-    if (!dec_gather(st, a.c[k], set, k, lut, cs)) return;
-    const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
-    if (threadIdx.x == 0) cs.flag = r.flag;
-    __syncthreads();
+    if (b0 == 0 && e0 == d.n) {
+      // the whole chunk
+      if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = cs.res[threadIdx.x];
+      flat_epilogue(a, j, adaptive, next, cs, es);
+      mark(j, 7);
+      continue;
+    }
     if (threadIdx.x < HIST_BINS) {
-      const uint32_t h = cs.hist[threadIdx.x];
-      if (a.c[k].out) a.c[k].out[threadIdx.x] = h;
-      if (h) atomicAdd(&st->totals[threadIdx.x], (unsigned long long)h);
-      if (k + 1 == a.count) st->last_hist[threadIdx.x] = h;
-    }
-    if (adaptive && k + 1 < a.count) {
-      // the layout chunk k+1 counted with must be binning_pattern(chunk k)
-      saturated_pattern(n, a.budget, cs, es);
-      if (!same_pattern(next, cs.pat) && threadIdx.x == 0) atomicExch(&st->status, kStatusPattern);
-    }
-    if (k + 1 == a.count) {
-      // last chunk: the pattern it was given, then the state
-      if (k == 0) {
-        copy_pattern(&cs.pat, &used0);
-      } else if (adaptive) {
-        saturated_pattern(a.c[k - 1].n, a.budget, cs, es);
-      } else {
-        // plain mode records binning_pattern(chunk k-1) as chunk k's pattern
-        __syncthreads();
-        if (!dec_gather(st, a.c[k - 1], set, k - 1, lut, cs)) return;
-        block_epilogue(cs.hist, a.c[k - 1].n, a.budget, a.theta, cs.pat, es);
-      }
-      __syncthreads();
-      copy_pattern(&st->last_pattern, &cs.pat);
-      copy_pattern(&st->pattern, &next);
-      if (threadIdx.x == 0) {
-        st->last_kernel = kern;
-        st->flag = r.flag;
-        st->chunks += a.count;
-      }
+      if (cs.res[threadIdx.x]) atomicAdd(&st->facc[j][threadIdx.x], cs.res[threadIdx.x]);
+      __threadfence();
     }
     __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->fdone[j], (unsigned long long)len) + len == d.n;
+    __syncthreads();
+    mark(j, 6);
+    if (last) {
+      // every other piece of chunk j was added (and fenced) before its count
+      __threadfence();
+      if (threadIdx.x < HIST_BINS) {
+        cs.hist[threadIdx.x] = __ldcg(&st->facc[j][threadIdx.x]);
+        st->facc[j][threadIdx.x] = 0;
+      }
+      if (threadIdx.x == 0) st->fdone[j] = 0;
+      flat_epilogue(a, j, adaptive, next, cs, es);
+    }
+    mark(j, 7);
   }
 }
 
@@ -699,8 +629,7 @@ struct hist_stream {
   int sms;
   int grid;
   unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
-  unsigned long long decoupled_launches;  // decoupled batches -> partial-buffer set (parity)
-  bool decoupled;
+  bool flat;  // batches run batch_flat_kernel
   bool pending;
   uint32_t* pending_out;
   uint32_t pending_n;
@@ -731,7 +660,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   a->prev_out = st->pending_out;
   a->prev_n = st->pending_n;
   a->prev_buf = st->pending_buf;
-  a->first_buf = st->decoupled ? (uint32_t)(st->decoupled_launches & 1) : (uint32_t)(st->chunks_launched % 3);
+  a->first_buf = (uint32_t)(st->chunks_launched % 3);
   a->budget = st->cfg.budget;
   a->theta = st->cfg.theta_milli;
   a->mode = st->cfg.mode;
@@ -744,14 +673,14 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     a->c[i].out = outs ? outs[i] : nullptr;
   }
   void* params[] = {a};
-  const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)st->grid), dim3(kThreads), params,
-                                              st->decoupled ? kDecSmemBytes : kSmemBytes, s);
+  // the synced kernel's CTAs wait on one another: all must be resident
+  cudaError_t e = st->flat ? cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads),
+                                              params, kFlatSmemBytes, s)
+                           : cudaLaunchCooperativeKernel((const void*)batch_synced_kernel, dim3((unsigned)st->grid),
+                                                         dim3(kThreads), params, kSmemBytes, s);
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (st->decoupled) {
-    st->decoupled_launches += 1;
-  } else {
+  if (!st->flat) {
     const uint32_t last = count - 1;
     st->pending = true;
     st->pending_out = outs ? outs[last] : nullptr;
@@ -789,13 +718,15 @@ bool config_ok(const hist_config* c) {
          c->mode <= HIST_MODE_ADAPTIVE;
 }
 
-int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
-  // at most the CTAs that can be resident at once: a cooperative launch needs them all
+int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem, bool flat) {
+  // at most the CTAs that can be resident at once: a cooperative launch needs
+  // them all; the synced kernel defaults to one CTA per SM (one table
+  // reduction per SM per chunk), the flat one to every resident CTA
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int cap = per_sm * sms;
-  const int g = cfg->grid ? (int)cfg->grid : sms;  // one CTA per SM: one table reduction per SM per chunk
+  const int g = cfg->grid ? (int)cfg->grid : (flat ? cap : sms);
   return g > cap ? cap : g;
 }
 
@@ -834,16 +765,16 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   st->cfg = *cfg;
   st->sms = sm_count();
   // modes whose chunk layouts never depend on the previous chunk's histogram
-  st->decoupled = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
-  const void* fn = st->decoupled ? (const void*)batch_decoupled_kernel : (const void*)batch_synced_kernel;
-  static int attr_sync[kMaxDevices], attr_dec[kMaxDevices];
-  const size_t smem = st->decoupled ? kDecSmemBytes : kSmemBytes;
-  int rc = ensure_smem_attr_bytes(fn, st->decoupled ? attr_dec : attr_sync, smem);
+  st->flat = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
+  const void* fn = st->flat ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
+  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices];
+  const size_t smem = st->flat ? kFlatSmemBytes : kSmemBytes;
+  int rc = ensure_smem_attr_bytes(fn, st->flat ? attr_flat : attr_sync, smem);
   if (rc) {
     free(st);
     return rc;
   }
-  st->grid = grid_for(cfg, st->sms, fn, smem);
+  st->grid = grid_for(cfg, st->sms, fn, smem, st->flat);
   cudaError_t e = cudaMalloc((void**)&st->d, sizeof(StreamDev));
   if (e != cudaSuccess) {
     free(st);
