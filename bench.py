@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
+    ap.add_argument("--profile-part", default=None, choices=["serving", "batch"],
+                    help="run only one other workload once, for ncu: the serving capacity replay "
+                         "(4000 requests) or the 4096-image batch")
     return ap.parse_args()
 
 
@@ -214,7 +217,44 @@ def cpu_oracle_rate(host_chunks, seconds):
             return done / el / 1e9, done, el
 
 
-def serving_extras(torch, np, hl, synth, hbm):
+def batch_extras(torch, hl, synth, hbm, steps, autotune=True):
+    """4096 images of uneven sizes in one graph-captured launch, with the
+    autotuner's setting (or the default setting)."""
+    import ctypes
+    from paper_1011_0235_gb300 import _abi
+    from synth import workloads
+    images = workloads.batch_images(count=4096)
+    bbytes = sum(im.n for im in images)
+    bbuf = torch.empty(workloads.packed_bytes(images), dtype=torch.uint8, device="cuda")
+    sq = torch.cuda.current_stream().cuda_stream
+    for im in images:
+        synth.device_fill(bbuf.data_ptr() + im.offset, im.n, im.thr, synth.SEED_BASE + 4, im.counter0, sq)
+    bptrs = torch.tensor([bbuf.data_ptr() + im.offset for im in images], dtype=torch.int64, device="cuda")
+    bsizes = torch.tensor([im.n for im in images], dtype=torch.int64, device="cuda")
+    bout = torch.empty((len(images), 256), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    lib = hl.lib()
+    best = _abi.BatchTuning()
+    lib.hist_batch_tuning_init(ctypes.byref(best))
+    if autotune:
+        bms = ctypes.c_float()
+        _abi.check("hist_batch_autotune", lib.hist_batch_autotune(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
+                                                                  bout.data_ptr(), 2, ctypes.byref(best),
+                                                                  ctypes.byref(bms)))
+    gexec = ctypes.c_void_p()
+    _abi.check("hist_batch_capture", lib.hist_batch_capture(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
+                                                            bout.data_ptr(), ctypes.byref(best), ctypes.byref(gexec)))
+    e5 = time_steps(torch, lambda: _abi.check("hist_batch_graph_launch", lib.hist_batch_graph_launch(
+        gexec, torch.cuda.current_stream().cuda_stream)), 2 if autotune else 0, steps)
+    lib.hist_batch_graph_destroy(gexec)
+    return {"batch_images": len(images), "batch_bytes": bbytes,
+            "batch_graph_gbs": round(bbytes * steps / e5 / 1e9, 2),
+            "batch_frac_of_hbm": round(bbytes * steps / e5 / 1e9 / hbm, 4),
+            "batch_tuning": {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll,
+                             "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}}
+
+
+def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     """The serving workload: Poisson arrivals over 256 streams with 64 MiB
     payload regions each (16 GiB resident), sizes log-uniform in 4 KiB ..
     64 MiB, 20% of the streams degenerate, a 32 GiB admission budget; the
@@ -254,6 +294,8 @@ def serving_extras(torch, np, hl, synth, hbm):
         srv.close()
         c = np.frombuffer(done, dtype=np.uint64).reshape(count, 6)
         lat = (c[:, 5] - c[:, 3]).astype(np.float64) / 1e3  # us
+        queued = (c[:, 4] - c[:, 3]).astype(np.float64) / 1e3  # arrival -> batch launched
+        on_gpu = (c[:, 5] - c[:, 4]).astype(np.float64) / 1e3  # launched -> completion seen
         nb = float(sum(r.n for r in reqs))
         span = (float(c[:, 5].max()) - (0.0 if at_zero else float(reqs[0].arrival_ns))) / 1e9
         ok = bool(np.array_equal(outs.sum(dim=1, dtype=torch.int64).cpu().numpy(),
@@ -261,10 +303,12 @@ def serving_extras(torch, np, hl, synth, hbm):
         return {"requests": count, "bytes": int(nb), "served_gbs": round(nb / span / 1e9, 2),
                 "p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
                 "p999_us": round(float(np.percentile(lat, 99.9)), 1), "max_us": round(float(lat.max()), 1),
+                "p50_queued_us": round(float(np.percentile(queued, 50)), 1),
+                "p50_launched_to_done_us": round(float(np.percentile(on_gpu, 50)), 1),
                 "batches": int(st.batches), "mean_batch": round(count / max(1, st.batches), 2),
                 "sums_equal_sizes": ok}
 
-    for lam in SERVE_RATES:
+    for lam in rates:
         reqs = workloads.serving_schedule(lam, int(lam * SERVE_SECONDS), streams=streams, region=region,
                                           seed=synth.SEED_BASE + 6 + lam)
         r = run(reqs)
@@ -326,6 +370,26 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------- native ----
+
+def run_part(args):
+    """One workload other than the headline stream, once, for profiling."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1011_0235_gb300 as hl
+    from paper_1011_0235_gb300 import build as hbuild
+
+    hbuild.build()
+    synth.build()
+    hl.lib()
+    if args.profile_part == "serving":
+        out = serving_extras(torch, np, hl, synth, 6800.0, rates=())
+    else:
+        out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=False)
+    print(json.dumps({"profile_part": args.profile_part, "result": out}))
+    return 0
+
 
 def run_native(args):
     import numpy as np
@@ -423,42 +487,7 @@ def run_native(args):
             extras["degenerate_%s_gbs" % name] = round(world * nbytes * args.steps / e2 / 1e9, 2)
             s2.close()
         del xdg
-        # batch: 4096 images of uneven sizes in one graph-captured launch,
-        # settings from the autotuner
-        import ctypes
-        from paper_1011_0235_gb300 import _abi
-        from synth import workloads
-        images = workloads.batch_images(count=4096)
-        bbytes = sum(im.n for im in images)
-        bbuf = torch.empty(workloads.packed_bytes(images), dtype=torch.uint8, device="cuda")
-        sq = torch.cuda.current_stream().cuda_stream
-        for im in images:
-            synth.device_fill(bbuf.data_ptr() + im.offset, im.n, im.thr, synth.SEED_BASE + 4, im.counter0, sq)
-        bptrs = torch.tensor([bbuf.data_ptr() + im.offset for im in images], dtype=torch.int64, device="cuda")
-        bsizes = torch.tensor([im.n for im in images], dtype=torch.int64, device="cuda")
-        bout = torch.empty((len(images), 256), dtype=torch.int32, device="cuda")
-        torch.cuda.synchronize()
-        lib = hl.lib()
-        best = _abi.BatchTuning()
-        bms = ctypes.c_float()
-        _abi.check("hist_batch_autotune", lib.hist_batch_autotune(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
-                                                                  bout.data_ptr(), 2, ctypes.byref(best),
-                                                                  ctypes.byref(bms)))
-        gexec = ctypes.c_void_p()
-        _abi.check("hist_batch_capture", lib.hist_batch_capture(bptrs.data_ptr(), bsizes.data_ptr(), len(images),
-                                                                bout.data_ptr(), ctypes.byref(best),
-                                                                ctypes.byref(gexec)))
-        ksb = max(3, min(args.steps, 10))
-        e5 = time_steps(torch, lambda: _abi.check("hist_batch_graph_launch", lib.hist_batch_graph_launch(
-            gexec, torch.cuda.current_stream().cuda_stream)), 2, ksb)
-        lib.hist_batch_graph_destroy(gexec)
-        extras["batch_images"] = len(images)
-        extras["batch_bytes"] = bbytes
-        extras["batch_graph_gbs"] = round(bbytes * ksb / e5 / 1e9, 2)
-        extras["batch_frac_of_hbm"] = round(bbytes * ksb / e5 / 1e9 / hbm, 4)
-        extras["batch_tuning"] = {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll,
-                                  "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}
-        del bbuf, bout
+        extras.update(batch_extras(torch, hl, synth, hbm, steps=max(3, min(args.steps, 10))))
         extras["serving"] = serving_extras(torch, np, hl, synth, hbm)
         # one-shot kernels on the whole 1 GiB at once (no stream)
         full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
@@ -534,6 +563,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_part:
+        return run_part(args)
     return run_native(args)
 
 
