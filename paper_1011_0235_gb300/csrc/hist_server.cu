@@ -18,6 +18,7 @@
 // by one CTA skips the accumulator.  Completion is seen by polling the
 // slot's event.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -41,10 +42,13 @@ constexpr uint32_t kSrvMaxSlots = HIST_SERVER_MAX_INFLIGHT;
 // cost of a request beyond its bytes, in bytes: about what one CTA counts
 // while it reduces its table and runs a request's epilogue
 constexpr unsigned long long kReqCost = 64ull << 10;
-// cost units per CTA of a batch (the grid is at most one CTA per SM)
-constexpr unsigned long long kCtaCost = 256ull << 10;
+// cost units per CTA of a batch (the grid is at most every resident CTA)
+constexpr unsigned long long kCtaCost = 64ull << 10;
 // dynamic shared memory: table, slot table, request cost prefix (u64 per request + 1)
 constexpr size_t kSrvSmem = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kSrvMaxBatch + 1) * 8;
+// request-table capacities of the two kernel variants (the table travels in
+// the launch's parameters: 24 bytes per request)
+constexpr uint32_t kSmallCap = 32;
 
 static_assert(kSrvMaxBatch <= (uint32_t)kThreads, "one prefix lane per request");
 
@@ -71,18 +75,23 @@ struct SrvReq {
 // Per batch slot, on the device.  acc and done return to zero when a
 // request's epilogue has read them, so a slot needs clearing only once.
 struct SrvSlot {
-  SrvReq req[kSrvMaxBatch];
   uint32_t acc[kSrvMaxBatch][HIST_BINS];  // partial sums of split requests
   unsigned long long done[kSrvMaxBatch];  // bytes of each split request counted
 };
 
-struct SrvArgs {
+struct SrvCommon {
   SrvStream* streams;
   SrvSlot* slot;
   uint32_t count;
   uint32_t budget;
   uint32_t theta;
   uint32_t mode;
+};
+
+template <uint32_t CAP>
+struct SrvArgs {
+  SrvCommon c;
+  SrvReq req[CAP];
 };
 
 __device__ __forceinline__ uint32_t srv_kernel_for(uint32_t mode, uint32_t flag) {
@@ -105,10 +114,10 @@ __device__ __forceinline__ void srv_copy_words(void* dst, const void* src, int w
 }
 
 // pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total.
-__device__ void srv_cost_prefix(const SrvSlot* slot, uint32_t count, unsigned long long* pre) {
+__device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, unsigned long long* pre) {
   __shared__ unsigned long long wsum[kWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const unsigned long long c = t < (int)count ? (unsigned long long)slot->req[t].n + kReqCost : 0ull;
+  const unsigned long long c = t < (int)count ? (unsigned long long)req[t].n + kReqCost : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -126,7 +135,7 @@ __device__ void srv_cost_prefix(const SrvSlot* slot, uint32_t count, unsigned lo
 
 // Request q is complete and cs.hist holds its histogram: write its output
 // and advance its stream's state.  All threads of the CTA call.
-__device__ void srv_epilogue(const SrvArgs& a, const SrvReq& q, CtaShared& cs, EpiShared& es) {
+__device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, CtaShared& cs, EpiShared& es) {
   SrvStream* st = a.streams + q.stream;
   const uint32_t kernel = srv_kernel_for(a.mode, st->flag);
   __syncthreads();  // cs.hist is written; every thread has read the old flag
@@ -152,18 +161,28 @@ __device__ void srv_epilogue(const SrvArgs& a, const SrvReq& q, CtaShared& cs, E
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(SrvArgs a) {
+// The slot table of a stream's pattern that is not a uniform shift (all
+// threads call).
+__device__ __noinline__ void srv_layout_general(const SrvStream* st, uint32_t* lut, CtaShared& cs) {
+  __syncthreads();
+  srv_copy_words(&cs.pat, &st->pattern, (int)(sizeof(hist_pattern) / 4));
+  __syncthreads();
+  classify_pattern(cs.pat, lut, cs);
+}
+
+template <uint32_t CAP>
+__global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_constant__ SrvArgs<CAP> args) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;
+  uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
   unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
-  __shared__ uint32_t part[kThreads];
   __shared__ int last;
+  const SrvCommon& a = args.c;
 
   zero_table(table);
-  srv_cost_prefix(a.slot, a.count, pre);
+  srv_cost_prefix(args.req, a.count, pre);
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x;
   const unsigned long long hi = W * (blockIdx.x + 1) / gridDim.x;
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(SrvArgs a) {
     else rh = mid;
   }
   for (; r < a.count && pre[r] < hi; ++r) {
-    const SrvReq q = a.slot->req[r];
+    const SrvReq q = args.req[r];
     const unsigned long long p0 = pre[r];
     if (q.n == 0) {
       // no bytes: the CTA holding the request's first cost position folds it
@@ -197,19 +216,17 @@ __global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(SrvArgs a) {
         path = PATH_SHIFT;
         lk = (int)st->lk;
       } else {
-        srv_copy_words(&cs.pat, &st->pattern, (int)(sizeof(hist_pattern) / 4));
-        __syncthreads();
-        classify_pattern(cs.pat, lut, cs);  // writes the slot table
+        srv_layout_general(st, lut, cs);
         path = cs.path;
         lk = cs.lk;
       }
     }
     const uint8_t* base = q.in + b0;
-    const size_t len = (size_t)(e0 - b0);
+    const uint32_t len = (uint32_t)(e0 - b0);
     const Split sp = split_bytes(base, len);
-    count_range_dispatch<4>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
-                            threadIdx.x, blockDim.x);
-    flush_table(path, lk, table, cs.pat, part, cs);
+    count_range_dispatch<2>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
+                            threadIdx.x, kThreads);
+    flush_table(path, lk, table, cs.pat, lut, cs);
     count_edges(base, sp, cs);
     zero_table(table);
     __syncthreads();
@@ -224,10 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(SrvArgs a) {
       __threadfence();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned long long before = atomicAdd(&a.slot->done[r], (unsigned long long)len);
-      last = before + len == (unsigned long long)q.n;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&a.slot->done[r], (unsigned long long)len) + len == q.n;
     __syncthreads();
     if (last) {
       // every other piece of r was added (and fenced) before its done count
@@ -282,10 +296,10 @@ struct PendingReq {
 
 struct BatchSlot {
   bool busy = false;
+  bool waited = false;  // completed by a host wait (its event could not be recorded)
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;
   SrvSlot* d_slot = nullptr;
-  SrvReq* h_req = nullptr;  // pinned staging of the request table
   std::vector<PendingReq> reqs;
   uint64_t admit_ns = 0;
   uint64_t bytes = 0;
@@ -303,6 +317,8 @@ struct hist_server {
   BatchSlot slot[kSrvMaxSlots];
   uint64_t inflight_bytes = 0;
   int sms = 0;
+  int max_grid = 0;                          // resident CTAs of the batch kernel
+  SrvArgs<kSrvMaxBatch>* args = nullptr;     // parameter block of the next launch
   hist_server_stats stats;
 };
 
@@ -323,7 +339,7 @@ uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
     BatchSlot& f = s->slot[k];
     if (!f.busy) continue;
     if (out && n + f.reqs.size() > cap) continue;  // no room for this batch's records yet
-    const cudaError_t q = cudaEventQuery(f.done);
+    const cudaError_t q = f.waited ? cudaSuccess : cudaEventQuery(f.done);
     if (q == cudaErrorNotReady) continue;
     if (q != cudaSuccess) {
       *err = cuda_fail(q);
@@ -387,42 +403,50 @@ int admit(hist_server* s) {
   }
   if (f->reqs.empty()) return HIST_OK;
   const uint32_t count = (uint32_t)f->reqs.size();
+  // the launch's parameters: common fields, then the request table
+  SrvArgs<kSrvMaxBatch>* a = s->args;
+  a->c.streams = s->d_streams;
+  a->c.slot = f->d_slot;
+  a->c.count = count;
+  a->c.budget = s->cfg.pattern_budget;
+  a->c.theta = s->cfg.theta_milli;
+  a->c.mode = s->cfg.mode;
+  unsigned long long cost = 0;
   for (uint32_t i = 0; i < count; ++i) {
-    f->h_req[i].in = f->reqs[i].in;
-    f->h_req[i].out = f->reqs[i].out;
-    f->h_req[i].n = (uint32_t)f->reqs[i].n;
-    f->h_req[i].stream = f->reqs[i].stream;
+    const PendingReq& r = f->reqs[i];
+    a->req[i].in = r.in;
+    a->req[i].out = r.out;
+    a->req[i].n = (uint32_t)r.n;
+    a->req[i].stream = r.stream;
+    cost += r.n + kReqCost;
   }
-  auto undo = [&]() {
+  unsigned long long grid = (cost + kCtaCost - 1) / kCtaCost;
+  if (grid > (unsigned long long)s->max_grid) grid = (unsigned long long)s->max_grid;
+  if (grid < 1) grid = 1;
+  // the small variant's parameters are a prefix of the large one's
+  static_assert(offsetof(SrvArgs<kSmallCap>, req) == offsetof(SrvArgs<kSrvMaxBatch>, req), "parameter layout");
+  void* params[] = {a};
+  const void* fn = count <= kSmallCap ? (const void*)server_batch_kernel<kSmallCap>
+                                      : (const void*)server_batch_kernel<kSrvMaxBatch>;
+  cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kThreads), params, kSrvSmem, f->cs);
+  if (e != cudaSuccess) {
+    // nothing was enqueued: the requests go back to the head of the queue
     for (const PendingReq& r : f->reqs) s->stream_busy[r.stream] = 0;
     s->queue.insert(s->queue.begin(), f->reqs.begin(), f->reqs.end());
     f->reqs.clear();
-  };
-  cudaError_t e = cudaMemcpyAsync(f->d_slot->req, f->h_req, count * sizeof(SrvReq), cudaMemcpyHostToDevice, f->cs);
-  if (e != cudaSuccess) {
-    undo();
-    return cuda_fail(e);
-  }
-  unsigned long long cost = 0;
-  for (const PendingReq& r : f->reqs) cost += r.n + kReqCost;
-  unsigned long long grid = (cost + kCtaCost - 1) / kCtaCost;
-  if (grid > (unsigned long long)s->sms) grid = (unsigned long long)s->sms;
-  if (grid < 1) grid = 1;
-  SrvArgs a;
-  a.streams = s->d_streams;
-  a.slot = f->d_slot;
-  a.count = count;
-  a.budget = s->cfg.pattern_budget;
-  a.theta = s->cfg.theta_milli;
-  a.mode = s->cfg.mode;
-  server_batch_kernel<<<(unsigned)grid, kThreads, kSrvSmem, f->cs>>>(a);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaEventRecord(f->done, f->cs);
-  if (e != cudaSuccess) {
-    undo();
     return cuda_fail(e);
   }
   f->busy = true;
+  e = cudaEventRecord(f->done, f->cs);
+  f->waited = e != cudaSuccess;
+  if (f->waited) {
+    // no completion event: wait for the batch here so that it still retires
+    cudaStreamSynchronize(f->cs);
+    f->admit_ns = now_ns();
+    s->inflight_bytes += f->bytes;
+    s->stats.batches += 1;
+    return cuda_fail(e);
+  }
   f->admit_ns = now_ns();
   s->inflight_bytes += f->bytes;
   s->stats.batches += 1;
@@ -462,8 +486,19 @@ int hist_server_create(const hist_server_config* cfg, hist_server** out) {
   s->scan_mark.assign(cfg->streams, 0);
   s->sms = sm_count();
   memset(&s->stats, 0, sizeof(s->stats));
-  static int attr_done[kMaxDevices];
-  int rc = s->sms > 0 ? ensure_smem_attr_bytes((const void*)server_batch_kernel, attr_done, kSrvSmem) : HIST_ECUDA;
+  static int attr_small[kMaxDevices], attr_large[kMaxDevices];
+  int rc = s->sms > 0 ? HIST_OK : HIST_ECUDA;
+  if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)server_batch_kernel<kSmallCap>, attr_small, kSrvSmem);
+  if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)server_batch_kernel<kSrvMaxBatch>, attr_large, kSrvSmem);
+  if (rc == HIST_OK) {
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, (const void*)server_batch_kernel<kSrvMaxBatch>, kThreads, kSrvSmem);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    s->max_grid = s->sms * (per_sm > 0 ? per_sm : 1);
+  }
+  s->args = new (std::nothrow) SrvArgs<kSrvMaxBatch>();
+  if (!s->args && rc == HIST_OK) rc = HIST_ENOMEM;
   if (rc == HIST_OK) {
     cudaError_t e = cudaMalloc((void**)&s->d_streams, sizeof(SrvStream) * cfg->streams);
     if (e == cudaSuccess) e = cudaMemset(s->d_streams, 0, sizeof(SrvStream) * cfg->streams);
@@ -473,7 +508,6 @@ int hist_server_create(const hist_server_config* cfg, hist_server** out) {
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaMalloc((void**)&f.d_slot, sizeof(SrvSlot));
       if (e == cudaSuccess) e = cudaMemset(f.d_slot, 0, sizeof(SrvSlot));
-      if (e == cudaSuccess) e = cudaHostAlloc((void**)&f.h_req, sizeof(SrvReq) * kSrvMaxBatch, cudaHostAllocDefault);
     }
     if (e == cudaSuccess) {
       server_init_kernel<<<1, 256>>>(s->d_streams, cfg->streams, cfg->pattern_budget);
@@ -503,11 +537,11 @@ int hist_server_destroy(hist_server* s) {
   for (uint32_t k = 0; k < kSrvMaxSlots; ++k) {
     BatchSlot& f = s->slot[k];
     if (f.d_slot) cudaFree(f.d_slot);
-    if (f.h_req) cudaFreeHost(f.h_req);
     if (f.done) cudaEventDestroy(f.done);
     if (f.cs) cudaStreamDestroy(f.cs);
   }
   if (s->d_streams) cudaFree(s->d_streams);
+  delete s->args;
   delete s;
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }

@@ -38,9 +38,10 @@ using namespace histlib;
 
 namespace {
 
-constexpr int kWin = 8;              // 16-byte vectors per thread per round (held in registers)
 constexpr int kStreamReplicas = 4;   // global partial histograms per chunk
 constexpr uint32_t kMaxBatch = 128;  // chunks per launch
+constexpr uint32_t kChunkRing = 4 * kMaxBatch;  // flat scratch: chunk accumulators
+constexpr uint32_t kLaunchRing = 8;             // flat scratch: per-launch records
 constexpr uint32_t kPollLimit = 1u << 22;  // bounded wait: about a second
 constexpr uint32_t kStatusTimeout = 4;     // device status: a wait ran out
 constexpr uint32_t kStatusPattern = 8;     // device status: a layout differed from the rule's pattern
@@ -51,14 +52,17 @@ struct StreamDev {
   // CTAs that published into rep[i] (high 32 bits) and their pixels (low 32
   // bits), one 128-byte line each
   unsigned long long cnt[3][16];
-  // flat batches: per-chunk sums and counted bytes (back to zero once the
-  // chunk's epilogue has read them), chunks of the running launch completed,
-  // the binning patterns of its last two chunks and its last switch
-  uint32_t facc[kMaxBatch][HIST_BINS];
-  unsigned long long fdone[kMaxBatch];
-  unsigned long long fchunks;
-  hist_pattern fpat[2];
-  uint32_t fflag;
+  // flat batches.  Launches of one stream overlap, so their scratch is in
+  // rings: flat chunk g (counted from the stream's first flat chunk) sums
+  // into slot g mod kChunkRing, which returns to zero in the chunk's
+  // epilogue; flat launch L (from 1) keeps the switch and patterns of its
+  // last chunks and its completed-chunk count in slot L mod kLaunchRing.
+  uint32_t racc[kChunkRing][HIST_BINS];        // by flat chunk number mod kChunkRing
+  unsigned long long rdone[kChunkRing];
+  unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
+  hist_pattern lpat[kLaunchRing][2];
+  uint32_t lflag[kLaunchRing];
+  unsigned long long launches_done;            // flat launches whose stream state is written
   unsigned long long totals[HIST_BINS];
   uint32_t last_hist[HIST_BINS];
   hist_pattern pattern;       // pattern for the next chunk
@@ -84,14 +88,16 @@ struct BatchArgs {
   uint32_t* prev_out;
   uint32_t prev_n;
   uint32_t prev_buf;
-  uint32_t first_buf;  // replica buffer of this batch's first chunk
+  uint32_t first_buf;  // synced: replica buffer of this batch's first chunk; flat: scratch set
   uint32_t budget;
   uint32_t theta;
   uint32_t mode;
   uint32_t trace_first;             // index of this batch's first chunk in the trace
   unsigned long long* trace;        // optional phase timestamps (see hist_stream_trace)
   uint32_t trace_cap;               // chunks the trace holds
-  uint32_t pad2;
+  uint32_t chunk0_full;             // flat: the stream's pattern is known to be the full table
+  unsigned long long first_chunk;   // flat: number of this batch's first chunk among the stream's flat chunks
+  unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
   ChunkDesc c[kMaxBatch];
 };
 
@@ -434,8 +440,12 @@ __device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre) {
 __device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j, uint32_t* lut, CtaShared& cs,
                                                  EpiShared& es) {
   __syncthreads();
-  if (j == 0) copy_pattern(&cs.pat, &a.st->pattern);
-  else saturated_pattern(0, a.budget, cs, es);
+  if (j == 0) {
+    pdl_wait();  // the previous launch writes the stream's pattern
+    copy_pattern(&cs.pat, &a.st->pattern);
+  } else {
+    saturated_pattern(0, a.budget, cs, es);
+  }
   __syncthreads();
   classify_pattern(cs.pat, lut, cs);
 }
@@ -447,7 +457,7 @@ __device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool
     lk = 0;
     return;
   }
-  if (j > 0 && a.c[j - 1].n > 0) {
+  if (j > 0 ? a.c[j - 1].n > 0 : a.chunk0_full != 0) {
     path = PATH_SHIFT;
     lk = 5;
     return;
@@ -483,27 +493,193 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, bool 
     saturated_pattern(n, a.budget, cs, es);
     if (!same_pattern(next, cs.pat) && t == 0) atomicExch(&st->status, kStatusPattern);
   }
-  if (j + 2 >= a.count) copy_pattern(&st->fpat[j + 1 == a.count ? 1 : 0], &next);
-  if (j + 1 == a.count && t == 0) st->fflag = r.flag;
+  const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+  if (j + 2 >= a.count) copy_pattern(&st->lpat[ls][j + 1 == a.count ? 1 : 0], &next);
+  if (j + 1 == a.count && t == 0) st->lflag[ls] = r.flag;
   __threadfence();
   __syncthreads();
-  if (t == 0) cs.kernel = atomicAdd(&st->fchunks, 1ull) + 1 == a.count ? 1u : 0u;
+  if (t == 0) cs.kernel = atomicAdd(&st->lchunks[ls], 1ull) + 1 == a.count ? 1u : 0u;
   __syncthreads();
   if (cs.kernel) {
     // every chunk's epilogue is done: the stream state after the batch
     __threadfence();
     if (a.count == 1) copy_pattern(&st->last_pattern, &st->pattern);
-    else copy_pattern_cg(&st->last_pattern, &st->fpat[0]);
+    else copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
     __syncthreads();
-    copy_pattern_cg(&st->pattern, &st->fpat[1]);
+    copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
     if (t == 0) {
-      st->flag = __ldcg(&st->fflag);
+      st->flag = __ldcg(&st->lflag[ls]);
       st->last_kernel = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
       st->chunks += a.count;
-      st->fchunks = 0;
+      st->lchunks[ls] = 0;
+      __threadfence();
+      st->launches_done = a.launch;
     }
   }
   __syncthreads();
+}
+
+// CTA-wide state of batch_flat_kernel (shared memory).
+struct FlatShared {
+  CtaShared cs;
+  EpiShared es;
+  hist_pattern next;
+  uint32_t eh[HIST_BINS];  // unaligned edge bytes of the pieces in the table
+  int cur;                 // chunk whose pieces the table holds, -1 if none
+  int path, lk;            // its layout
+  uint32_t bytes;          // its bytes in the table
+  int last;
+  int released;  // this CTA has waited for the previous launch
+  int ring_ok;   // the chunk ring slots of this launch are free
+};
+
+__device__ __forceinline__ void flat_mark(const BatchArgs& a, uint32_t j, int phase) {
+  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
+  if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
+    a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
+}
+
+// Launches of one stream overlap (programmatic dependent launch): every
+// CTA lets the next launch start as soon as it starts, so the next launch's
+// CTAs take the SM slots that this launch's CTAs free as they finish.  A
+// CTA waits for the previous launch to complete before its first epilogue,
+// which reads and writes the stream state (flat_release), and before it
+// first adds into a chunk ring slot, the last user of the slot -- a launch
+// at least kChunkRing / kMaxBatch - 1 launches back -- must have written
+// its state (flat_ring_ready, a bounded wait).  All threads call both.
+__device__ __forceinline__ void flat_release(FlatShared& fs) {
+  if (!fs.released) pdl_wait();
+  __syncthreads();
+  if (threadIdx.x == 0) fs.released = 1;
+}
+
+__device__ __noinline__ void flat_ring_ready(const BatchArgs& a, FlatShared& fs) {
+  // fs.ring_ok is read between the first two barriers and written after the
+  // second, so every thread takes the same branch
+  __syncthreads();
+  if (fs.ring_ok) return;
+  constexpr unsigned long long back = kChunkRing / kMaxBatch - 1;
+  if (threadIdx.x == 0) {
+    uint32_t it = 0;
+    while (a.launch > back && ld_acquire(&a.st->launches_done) < a.launch - back) {
+      if (++it >= kPollLimit) {
+        atomicOr(&a.st->status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(256);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) fs.ring_ok = 1;
+}
+
+// Reduce the table (the pieces of chunk fs.cur) and publish them: into the
+// chunk's accumulator and byte counter, or, when the table holds the whole
+// chunk, straight into the chunk's epilogue.  The CTA whose bytes complete
+// the chunk runs the epilogue.  All threads call.
+__device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint32_t* table, uint32_t* lut,
+                                        FlatShared& fs) {
+  __syncthreads();
+  const int j = fs.cur;
+  if (j < 0) return;
+  StreamDev* st = a.st;
+  const uint32_t slot = (uint32_t)((a.first_chunk + (unsigned)j) % kChunkRing);
+  const int t = threadIdx.x;
+  flush_table(fs.path, fs.lk, table, fs.cs.pat, lut, fs.cs);
+  if (t < HIST_BINS) {
+    fs.cs.res[t] += fs.eh[t];
+    fs.eh[t] = 0;
+  }
+  zero_table(table);
+  const uint32_t n = a.c[j].n, len = fs.bytes;
+  __syncthreads();
+  flat_mark(a, j, 5);
+  if (t == 0) fs.cur = -1;
+  if (len == n) {
+    // the whole chunk
+    if (t < HIST_BINS) fs.cs.hist[t] = fs.cs.res[t];
+    flat_release(fs);
+    flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+    flat_mark(a, j, 7);
+    return;
+  }
+  flat_ring_ready(a, fs);
+  if (t < HIST_BINS) {
+    if (fs.cs.res[t]) atomicAdd(&st->racc[slot][t], fs.cs.res[t]);
+    __threadfence();
+  }
+  __syncthreads();
+  if (t == 0) fs.last = atomicAdd(&st->rdone[slot], (unsigned long long)len) + len == n;
+  __syncthreads();
+  if (fs.last) {
+    // every other piece of chunk j was added (and fenced) before its count
+    __threadfence();
+    if (t < HIST_BINS) {
+      fs.cs.hist[t] = __ldcg(&st->racc[slot][t]);
+      st->racc[slot][t] = 0;
+    }
+    if (t == 0) st->rdone[slot] = 0;
+    flat_release(fs);
+    flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+  }
+  flat_mark(a, j, 7);
+  __syncthreads();
+}
+
+// Count bytes [b0, e0) of chunk j (not empty) into the table, reducing the
+// table first if it holds another chunk.  All threads call.
+__device__ __forceinline__ void flat_piece(const BatchArgs& a, bool adaptive, uint32_t j, uint32_t b0, uint32_t e0,
+                                           uint32_t* table, uint32_t* lut, FlatShared& fs) {
+  if (fs.cur != (int)j) {
+    flat_flush(a, adaptive, table, lut, fs);
+    flat_mark(a, j, 0);
+    int path, lk;
+    flat_layout(a, j, adaptive, lut, fs.cs, fs.es, path, lk);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fs.cur = (int)j;
+      fs.path = path;
+      fs.lk = lk;
+      fs.bytes = 0;
+    }
+    __syncthreads();
+  }
+  const uint8_t* base = a.c[j].in + b0;
+  const Split sp = split_bytes(base, e0 - b0);
+  count_range_dispatch<2>(fs.path, fs.lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
+                          threadIdx.x, kThreads);
+  count_edges_into(base, sp, fs.eh);
+  if (threadIdx.x == 0) fs.bytes += e0 - b0;
+}
+
+// Count the cost range [x0, x1) of the batch.  All threads call.
+__device__ void flat_range(const BatchArgs& a, bool adaptive, const unsigned long long* pre, unsigned long long x0,
+                           unsigned long long x1, uint32_t* table, uint32_t* lut, FlatShared& fs) {
+  uint32_t j = 0, jh = a.count;
+  while (j + 1 < jh) {
+    const uint32_t mid = (j + jh) >> 1;
+    if (pre[mid] <= x0) j = mid;
+    else jh = mid;
+  }
+  for (; j < a.count && pre[j] < x1; ++j) {
+    const unsigned long long p0 = pre[j];
+    const uint32_t n = a.c[j].n;
+    if (n == 0) {
+      // no bytes: the range holding the chunk's first cost position folds it
+      if (p0 >= x0) {
+        flat_flush(a, adaptive, table, lut, fs);
+        flat_mark(a, j, 0);
+        if (threadIdx.x < HIST_BINS) fs.cs.hist[threadIdx.x] = 0;
+        flat_release(fs);
+        flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+        flat_mark(a, j, 7);
+      }
+      continue;
+    }
+    const unsigned long long b0 = x0 > p0 ? x0 - p0 : 0ull;
+    const unsigned long long e0 = x1 - p0 < (unsigned long long)n ? x1 - p0 : (unsigned long long)n;
+    if (b0 < e0) flat_piece(a, adaptive, j, (uint32_t)b0, (uint32_t)e0, table, lut, fs);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_constant__ BatchArgs a) {
@@ -511,90 +687,23 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
   unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
-  __shared__ CtaShared cs;
-  __shared__ EpiShared es;
-  __shared__ hist_pattern next;
-  __shared__ int last;
-  StreamDev* st = a.st;
-  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
-  auto mark = [&](uint32_t j, int phase) {
-    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
-      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
-  };
+  __shared__ FlatShared fs;
   const bool adaptive = a.mode != HIST_MODE_PLAIN;
+  const int t = threadIdx.x;
 
+  pdl_launch_dependents();
+  if (t < HIST_BINS) fs.eh[t] = 0;
+  if (t == 0) {
+    fs.cur = -1;
+    fs.released = 0;
+    fs.ring_ok = 0;
+  }
   zero_table(table);
   flat_prefix(a, pre);
   const unsigned long long W = pre[a.count];
-  const unsigned long long lo = W * blockIdx.x / gridDim.x;
-  const unsigned long long hi = W * (blockIdx.x + 1) / gridDim.x;
-  if (lo >= hi) return;
-  // the chunk holding cost position lo
-  uint32_t j = 0, jh = a.count;
-  while (j + 1 < jh) {
-    const uint32_t mid = (j + jh) >> 1;
-    if (pre[mid] <= lo) j = mid;
-    else jh = mid;
-  }
-  for (; j < a.count && pre[j] < hi; ++j) {
-    const ChunkDesc d = a.c[j];
-    const unsigned long long p0 = pre[j];
-    if (d.n == 0) {
-      // no bytes: the CTA holding the chunk's first cost position folds it
-      if (p0 >= lo) {
-        mark(j, 0);
-        if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
-        flat_epilogue(a, j, adaptive, next, cs, es);
-        mark(j, 7);
-      }
-      continue;
-    }
-    // this CTA's bytes of the chunk: its cost range cut to [0, n)
-    const unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
-    const unsigned long long e0 = hi - p0 < (unsigned long long)d.n ? hi - p0 : (unsigned long long)d.n;
-    if (b0 >= e0) continue;
-    mark(j, 0);
-    int path, lk;
-    flat_layout(a, j, adaptive, lut, cs, es, path, lk);
-    mark(j, 2);
-    const uint8_t* base = d.in + b0;
-    const uint32_t len = (uint32_t)(e0 - b0);
-    const Split sp = split_bytes(base, len);
-    count_range_dispatch<2>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
-                            threadIdx.x, kThreads);
-    mark(j, 4);
-    flush_table(path, lk, table, cs.pat, lut, cs);
-    count_edges(base, sp, cs);
-    zero_table(table);
-    __syncthreads();
-    mark(j, 5);
-    if (b0 == 0 && e0 == d.n) {
-      // the whole chunk
-      if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = cs.res[threadIdx.x];
-      flat_epilogue(a, j, adaptive, next, cs, es);
-      mark(j, 7);
-      continue;
-    }
-    if (threadIdx.x < HIST_BINS) {
-      if (cs.res[threadIdx.x]) atomicAdd(&st->facc[j][threadIdx.x], cs.res[threadIdx.x]);
-      __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&st->fdone[j], (unsigned long long)len) + len == d.n;
-    __syncthreads();
-    mark(j, 6);
-    if (last) {
-      // every other piece of chunk j was added (and fenced) before its count
-      __threadfence();
-      if (threadIdx.x < HIST_BINS) {
-        cs.hist[threadIdx.x] = __ldcg(&st->facc[j][threadIdx.x]);
-        st->facc[j][threadIdx.x] = 0;
-      }
-      if (threadIdx.x == 0) st->fdone[j] = 0;
-      flat_epilogue(a, j, adaptive, next, cs, es);
-    }
-    mark(j, 7);
-  }
+  const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
+  if (lo < hi) flat_range(a, adaptive, pre, lo, hi, table, lut, fs);
+  flat_flush(a, adaptive, table, lut, fs);
 }
 
 // Epilogue of the last pushed chunk (one CTA of 1024 threads).
@@ -630,6 +739,9 @@ struct hist_stream {
   int grid;
   unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
   bool flat;  // batches run batch_flat_kernel
+  bool flat_full;  // the stream's pattern is the full table (known on the host)
+  unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
+  unsigned long long flat_chunks;    // chunks of those launches
   bool pending;
   uint32_t* pending_out;
   uint32_t pending_n;
@@ -661,6 +773,9 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   a->prev_n = st->pending_n;
   a->prev_buf = st->pending_buf;
   a->first_buf = (uint32_t)(st->chunks_launched % 3);
+  a->chunk0_full = st->flat_full ? 1u : 0u;
+  a->first_chunk = st->flat_chunks;
+  a->launch = st->flat_launches + 1;
   a->budget = st->cfg.budget;
   a->theta = st->cfg.theta_milli;
   a->mode = st->cfg.mode;
@@ -673,14 +788,33 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     a->c[i].out = outs ? outs[i] : nullptr;
   }
   void* params[] = {a};
-  // the synced kernel's CTAs wait on one another: all must be resident
-  cudaError_t e = st->flat ? cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads),
-                                              params, kFlatSmemBytes, s)
-                           : cudaLaunchCooperativeKernel((const void*)batch_synced_kernel, dim3((unsigned)st->grid),
-                                                         dim3(kThreads), params, kSmemBytes, s);
+  cudaError_t e;
+  if (st->flat) {
+    // may start while the previous launch on `s` finishes (see batch_flat_kernel)
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)st->grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = kFlatSmemBytes;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel, params);
+  } else {
+    // the synced kernel's CTAs wait on one another: all must be resident
+    e = cudaLaunchCooperativeKernel((const void*)batch_synced_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                                    kSmemBytes, s);
+  }
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (!st->flat) {
+  if (st->flat) {
+    st->flat_launches += 1;
+    st->flat_chunks += count;
+    // in the adaptive mode the pattern after a non-empty chunk is the full table
+    st->flat_full = st->cfg.mode == HIST_MODE_ADAPTIVE && ns[count - 1] > 0;
+  } else {
     const uint32_t last = count - 1;
     st->pending = true;
     st->pending_out = outs ? outs[last] : nullptr;
@@ -928,6 +1062,9 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h, hist_cuda
   cudaError_t e = cudaMemcpyAsync(st->d, tmp, sizeof(StreamDev), cudaMemcpyHostToDevice, (cudaStream_t)s);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)s);
   free(tmp);
+  st->flat_full = false;  // the next flat launch reads the restored pattern
+  st->flat_launches = 0;   // the rings restart with the zeroed scratch
+  st->flat_chunks = 0;
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 

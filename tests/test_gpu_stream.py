@@ -96,6 +96,49 @@ def test_stream_batched_matches_step_by_step_and_outputs():
     st.close()
 
 
+@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
+def test_back_to_back_batches(mode):
+    """Many small push_many calls in a row on one stream, with empty and
+    ragged chunks and a checkpoint in the middle: launches of the flat path
+    overlap their predecessors, so every chunk's output, the totals and the
+    state after every few calls must still match the oracle."""
+    rng = np.random.default_rng(11 + mode)
+    sizes = [int(x) for x in rng.choice([0, 1, 15, 4096, 65_536, 300_001, 1 << 20], size=160)]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 5, SEED + 20 + mode)
+    ref = oracle.StreamOracle(8192, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    offs, pos = [], 0
+    for c, ch in enumerate(chunks):
+        pos += c % 16
+        offs.append(pos)
+        pos += ch.size
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=mode)
+    i = 0
+    calls = 0
+    while i < len(chunks):
+        k = int(rng.integers(1, 6))
+        idx = list(range(i, min(i + k, len(chunks))))
+        st.push_many([bd.data_ptr() + offs[j] for j in idx], [chunks[j].size for j in idx],
+                     [outs[j].data_ptr() for j in idx])
+        i += len(idx)
+        calls += 1
+        if calls % 17 == 0:
+            ref_i = oracle.StreamOracle(8192, mode=mode)
+            for ch in chunks[:i]:
+                rec_i = ref_i.push(ch)
+            _check_state(st.state(), ref_i, rec_i)
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
+
+
 def test_stream_checkpoint_resume():
     chunks = _phase_chunks(10, lambda c: 200_000 + c, 3, SEED + 6)
     ref = oracle.StreamOracle(960)
