@@ -59,6 +59,7 @@ struct StreamDev {
   // last chunks and its completed-chunk count in slot L mod kLaunchRing.
   uint32_t racc[kChunkRing][HIST_BINS];        // by flat chunk number mod kChunkRing
   unsigned long long rdone[kChunkRing];
+  unsigned long long rcnt[kChunkRing];         // auto batches: CTA arrivals, never reset
   unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
   hist_pattern lpat[kLaunchRing][2];
   uint32_t lflag[kLaunchRing];
@@ -473,29 +474,37 @@ __device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pa
   for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
 }
 
-// Chunk j is complete and cs.hist holds its histogram.  All threads call.
-__device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, bool adaptive, hist_pattern& next,
-                                           CtaShared& cs, EpiShared& es) {
+// Chunk j is complete and cs.hist holds its histogram: its switch, pattern,
+// output and totals; `check` says when chunk j+1 was counted with the full
+// table that the rule must then give (0: never, 1: always, 2: when chunk j's
+// switch chose the adaptive kernel); the CTA that completes the batch's last
+// epilogue writes the stream state, `last_kernel` being the kernel the last
+// chunk ran.  All threads call.
+constexpr uint32_t kCheckNever = 0, kCheckAlways = 1, kCheckIfAdaptive = 2;
+__device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint32_t check, uint32_t last_kernel,
+                                           hist_pattern& next, CtaShared& cs, EpiShared& es) {
   StreamDev* st = a.st;
   const int t = threadIdx.x;
   const uint32_t n = a.c[j].n;
   __syncthreads();
   const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
+  if (t == 0) cs.flag = r.flag;  // r is valid in threads 0..255 only
   __syncthreads();
+  const uint32_t flag = cs.flag;
   if (t < HIST_BINS) {
     const uint32_t h = cs.hist[t];
     if (a.c[j].out) a.c[j].out[t] = h;
     if (h) atomicAdd(&st->totals[t], (unsigned long long)h);
     if (j + 1 == a.count) st->last_hist[t] = h;
   }
-  if (adaptive && j + 1 < a.count) {
+  if (j + 1 < a.count && (check == kCheckAlways || (check == kCheckIfAdaptive && flag == HIST_FLAG_ADAPTIVE))) {
     // chunk j+1 was counted with the layout the rule gives after n pixels
     saturated_pattern(n, a.budget, cs, es);
     if (!same_pattern(next, cs.pat) && t == 0) atomicExch(&st->status, kStatusPattern);
   }
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
   if (j + 2 >= a.count) copy_pattern(&st->lpat[ls][j + 1 == a.count ? 1 : 0], &next);
-  if (j + 1 == a.count && t == 0) st->lflag[ls] = r.flag;
+  if (j + 1 == a.count && t == 0) st->lflag[ls] = flag;
   __threadfence();
   __syncthreads();
   if (t == 0) cs.kernel = atomicAdd(&st->lchunks[ls], 1ull) + 1 == a.count ? 1u : 0u;
@@ -509,7 +518,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, bool 
     copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
     if (t == 0) {
       st->flag = __ldcg(&st->lflag[ls]);
-      st->last_kernel = adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+      st->last_kernel = last_kernel;
       st->chunks += a.count;
       st->lchunks[ls] = 0;
       __threadfence();
@@ -599,7 +608,7 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint3
     // the whole chunk
     if (t < HIST_BINS) fs.cs.hist[t] = fs.cs.res[t];
     flat_release(fs);
-    flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
     flat_mark(a, j, 7);
     return;
   }
@@ -620,7 +629,7 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint3
     }
     if (t == 0) st->rdone[slot] = 0;
     flat_release(fs);
-    flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
   }
   flat_mark(a, j, 7);
   __syncthreads();
@@ -671,7 +680,7 @@ __device__ void flat_range(const BatchArgs& a, bool adaptive, const unsigned lon
         flat_mark(a, j, 0);
         if (threadIdx.x < HIST_BINS) fs.cs.hist[threadIdx.x] = 0;
         flat_release(fs);
-        flat_epilogue(a, j, adaptive, fs.next, fs.cs, fs.es);
+        flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
         flat_mark(a, j, 7);
       }
       continue;
@@ -706,6 +715,185 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   flat_flush(a, adaptive, table, lut, fs);
 }
 
+// AUTO mode at the full budget.  Chunk j's kernel is chunk j-1's switch,
+// and the layout that kernel then uses is fixed -- the full table after a
+// non-empty chunk (R3 saturates at the full budget), while an empty chunk
+// always switches to the plain kernel -- so the one value a chunk depends on
+// is one bit.  One cooperative launch per batch, every CTA resident.  For
+// each chunk j every CTA
+//   1. streams its slice of chunk j+1 into L2 (bulk prefetch);
+//   2. counts its slice of chunk j with a guess of the kernel: the latest
+//      switch it knows (chunk j-2's);
+//   3. waits (bounded) until every CTA has published chunk j-1, reads that
+//      histogram and takes its largest bin against the threshold: chunk j's
+//      switch.  If the guess was wrong it clears the table and counts its
+//      slice again, from L2, with the kernel the switch chose, so chunk j's
+//      counts always come from that kernel;
+//   4. adds its per-bin sums into chunk j's ring accumulator and, after a
+//      fence, one arrival into the chunk's ring counter (never reset: use u
+//      of a slot is complete at (u + 1) x the CTA count).
+// The wait of step 3 overlaps the counting of step 2.  The chunk epilogues
+// (pattern, output, totals, and the stream state at the end) run after the
+// last chunk, chunk j in CTA j mod the CTA count.
+
+// Wait until ring counter `slot` has every CTA's arrival for use `use`, then
+// take chunk n's switch from the ring accumulator.  All threads call;
+// returns false if the wait ran out or another CTA aborted.
+__device__ __noinline__ bool auto_switch(StreamDev* st, uint32_t slot, unsigned long long target, uint32_t n,
+                                         uint32_t theta, uint32_t* wmax, FlatShared& fs) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    uint32_t ok = 0;
+    for (uint32_t it = 0;; ++it) {
+      if (ld_acquire(&st->rcnt[slot]) >= target) {
+        ok = 1;
+        break;
+      }
+      if (it >= kPollLimit) {
+        atomicExch(&st->abort, 1u);
+        atomicExch(&st->status, kStatusTimeout);
+        break;
+      }
+      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
+      __nanosleep(32);
+    }
+    fs.last = (int)ok;
+  }
+  __syncthreads();
+  if (!fs.last) return false;
+  __threadfence();
+  if (t < HIST_BINS) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, __ldcg(&st->racc[slot][t]));
+    if ((t & 31) == 0) wmax[t >> 5] = m;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t mx = 0;
+#pragma unroll
+    for (int i = 0; i < HIST_BINS / 32; ++i) mx = wmax[i] > mx ? wmax[i] : mx;
+    fs.cs.flag = reaches_theta(mx, n, theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void auto_layout(uint32_t kern, uint32_t j, StreamDev* st, uint32_t* lut, FlatShared& fs,
+                                            int& path, int& lk) {
+  path = PATH_PLAIN;
+  lk = 0;
+  if (kern != HIST_FLAG_ADAPTIVE) return;
+  if (j > 0) {
+    path = PATH_SHIFT;  // after a non-empty chunk: the full table
+    lk = 5;
+    return;
+  }
+  __syncthreads();
+  copy_pattern(&fs.cs.pat, &st->pattern);  // chunk 0: the stream's pattern
+  __syncthreads();
+  classify_pattern(fs.cs.pat, lut, fs.cs);
+  path = fs.cs.path;
+  lk = fs.cs.lk;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batch_auto_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;  // slot table of chunk 0, then scratch of the reduction
+  __shared__ FlatShared fs;
+  __shared__ uint32_t wmax[HIST_BINS / 32];
+  StreamDev* st = a.st;
+  const int t = threadIdx.x;
+  const unsigned long long G = gridDim.x;
+  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
+  auto mark = [&](uint32_t j, int phase) {
+    if (a.trace && tslot >= 0 && t == 0 && a.trace_first + j < a.trace_cap)
+      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
+  };
+  auto target = [&](uint32_t j) { return ((a.first_chunk + j) / kChunkRing + 1) * G; };
+  auto slot_of = [&](uint32_t j) { return (uint32_t)((a.first_chunk + j) % kChunkRing); };
+
+  uint32_t known = st->flag;  // the latest switch known: chunk 0's kernel
+  prefetch_slice(a.c[0]);
+  zero_table(table);
+  __syncthreads();
+  uint32_t kern = known;  // kernel of the current chunk (uniform)
+  for (uint32_t j = 0; j < a.count; ++j) {
+    const ChunkDesc d = a.c[j];
+    mark(j, 0);
+    int path, lk;
+    auto_layout(known, j, st, lut, fs, path, lk);
+    mark(j, 2);
+    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+    const Geo g = chunk_geo(d);
+    count_geo(path, lk, g, table, lut);
+    mark(j, 3);
+    kern = known;
+    if (j > 0) {
+      // chunk j's kernel: chunk j-1's switch
+      if (!auto_switch(st, slot_of(j - 1), target(j - 1), a.c[j - 1].n, a.theta, wmax, fs)) return;
+      kern = fs.cs.flag;
+      mark(j, 1);
+      if (kern != known) {
+        // wrong guess: count again with the chosen kernel
+        zero_table(table);
+        auto_layout(kern, j, st, lut, fs, path, lk);
+        __syncthreads();
+        count_geo(path, lk, g, table, lut);
+        known = kern;
+      }
+    }
+    // per-bin sums (CTA 0 adds the chunk's unaligned head and tail)
+    flush_table(path, lk, table, fs.cs.pat, lut, fs.cs);
+    mark(j, 4);
+    if (blockIdx.x == 0) {
+      count_edges(d.in, split_bytes(d.in, d.n), fs.cs);
+      __syncthreads();
+    }
+    const uint32_t slot = slot_of(j);
+    if (t < HIST_BINS) {
+      if (fs.cs.res[t]) atomicAdd(&st->racc[slot][t], fs.cs.res[t]);
+      __threadfence();
+    }
+    __syncthreads();
+    mark(j, 5);
+    if (t == 0) red_release_add(&st->rcnt[slot], 1ull);
+    mark(j, 6);
+    zero_table(table);
+    __syncthreads();
+    mark(j, 7);
+  }
+  // every CTA's sums of the last chunk; then every CTA has also read every
+  // histogram it needed, so the accumulators are free for the epilogues
+  if (t == 0) {
+    uint32_t ok = 0;
+    for (uint32_t it = 0;; ++it) {
+      if (ld_acquire(&st->rcnt[slot_of(a.count - 1)]) >= target(a.count - 1)) {
+        ok = 1;
+        break;
+      }
+      if (it >= kPollLimit) {
+        atomicExch(&st->abort, 1u);
+        atomicExch(&st->status, kStatusTimeout);
+        break;
+      }
+      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
+      __nanosleep(32);
+    }
+    fs.last = (int)ok;
+  }
+  __syncthreads();
+  if (!fs.last) return;
+  __threadfence();
+  for (uint32_t j = blockIdx.x; j < a.count; j += (uint32_t)G) {
+    const uint32_t slot = slot_of(j);
+    if (t < HIST_BINS) {
+      fs.cs.hist[t] = __ldcg(&st->racc[slot][t]);
+      st->racc[slot][t] = 0;
+    }
+    flat_epilogue(a, j, kCheckIfAdaptive, kern, fs.next, fs.cs, fs.es);
+  }
+}
+
 // Epilogue of the last pushed chunk (one CTA of 1024 threads).
 __global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t ctas,
                                                           uint32_t* out, uint32_t budget, uint32_t theta, uint32_t mode) {
@@ -738,7 +926,8 @@ struct hist_stream {
   int sms;
   int grid;
   unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
-  bool flat;  // batches run batch_flat_kernel
+  bool flat;   // batches run batch_flat_kernel
+  bool autok;  // batches run batch_auto_kernel
   bool flat_full;  // the stream's pattern is the full table (known on the host)
   unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
   unsigned long long flat_chunks;    // chunks of those launches
@@ -789,7 +978,11 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   }
   void* params[] = {a};
   cudaError_t e;
-  if (st->flat) {
+  if (st->autok) {
+    // CTAs wait on one another for every chunk: all must be resident
+    e = cudaLaunchCooperativeKernel((const void*)batch_auto_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                                    kSmemBytes, s);
+  } else if (st->flat) {
     // may start while the previous launch on `s` finishes (see batch_flat_kernel)
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)st->grid);
@@ -809,7 +1002,10 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   }
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (st->flat) {
+  if (st->autok) {
+    st->flat_launches += 1;
+    st->flat_chunks += count;
+  } else if (st->flat) {
     st->flat_launches += 1;
     st->flat_chunks += count;
     // in the adaptive mode the pattern after a non-empty chunk is the full table
@@ -900,15 +1096,17 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   st->sms = sm_count();
   // modes whose chunk layouts never depend on the previous chunk's histogram
   st->flat = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
-  const void* fn = st->flat ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
-  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices];
+  st->autok = cfg->mode == HIST_MODE_AUTO && cfg->budget == HIST_BUDGET_MAX;
+  const void* fn = st->flat ? (const void*)batch_flat_kernel
+                            : (st->autok ? (const void*)batch_auto_kernel : (const void*)batch_synced_kernel);
+  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_auto[kMaxDevices];
   const size_t smem = st->flat ? kFlatSmemBytes : kSmemBytes;
-  int rc = ensure_smem_attr_bytes(fn, st->flat ? attr_flat : attr_sync, smem);
+  int rc = ensure_smem_attr_bytes(fn, st->flat ? attr_flat : (st->autok ? attr_auto : attr_sync), smem);
   if (rc) {
     free(st);
     return rc;
   }
-  st->grid = grid_for(cfg, st->sms, fn, smem, st->flat);
+  st->grid = grid_for(cfg, st->sms, fn, smem, st->flat || st->autok);
   cudaError_t e = cudaMalloc((void**)&st->d, sizeof(StreamDev));
   if (e != cudaSuccess) {
     free(st);
