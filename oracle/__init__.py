@@ -196,17 +196,27 @@ class StreamOracle:
     """Chunked stream of Sec. III.B with the switch of Sec. III.C.
 
     The first chunk runs the plain kernel with the default pattern.  After each
-    chunk: totals += its histogram; the next chunk's kernel is the switch of
-    that histogram (a moving window of one chunk); the next pattern is the
-    binning pattern of that histogram.  In MODE_PLAIN / MODE_ADAPTIVE the kernel
-    is forced and the pattern is still refreshed.
+    chunk: totals += its histogram (the accumulated histogram of Sec. III.B);
+    the moving-window histogram is the sum of the histograms of the last
+    `window` chunks (fewer at the start of the stream); the next chunk's
+    kernel is the switch of the moving-window histogram (Sec. III.C: the last
+    computed moving-window histogram decides); the next pattern is the
+    binning pattern of the last chunk's histogram.  In MODE_PLAIN /
+    MODE_ADAPTIVE the kernel is forced; the switch and the pattern are still
+    computed.
     """
 
-    def __init__(self, budget: int, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO):
+    def __init__(self, budget: int, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO,
+                 window: int = 1):
+        if window < 1:
+            raise ValueError("window must be at least one chunk")
         self.budget = budget
         self.theta_milli = theta_milli
         self.mode = mode
+        self.window = window
         self.totals = np.zeros(BINS, np.uint64)
+        self.recent = []  # histograms of the last `window` chunks, oldest first
+        self.mw = np.zeros(BINS, np.uint64)
         self.pattern = default_pattern(budget)
         self.flag = FLAG_PLAIN
         self.chunks = 0
@@ -220,7 +230,9 @@ class StreamOracle:
             kernel = FLAG_ADAPTIVE
         rec = ChunkRecord(hist=hist_u32(x), kernel=kernel, pattern=self.pattern)
         self.totals = self.totals + rec.hist.astype(np.uint64)
-        self.flag = switch(rec.hist.astype(np.uint64), self.theta_milli)
+        self.recent = (self.recent + [rec.hist.astype(np.uint64)])[-self.window:]
+        self.mw = np.sum(self.recent, axis=0, dtype=np.uint64)
+        self.flag = switch(self.mw, self.theta_milli)
         self.pattern = binning_pattern(rec.hist, self.budget)
         self.chunks += 1
         return rec

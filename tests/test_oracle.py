@@ -418,3 +418,73 @@ def test_stream_oracle_forced_modes_refresh_pattern():
     assert r0.kernel == r1.kernel == oracle.FLAG_ADAPTIVE
     assert r1.pattern == oracle.binning_pattern(oracle.hist_u32(x0), 960)
     assert int(r1.pattern.k[7]) == 32
+
+
+# ------------------------------------------------------- moving window ----
+
+def test_moving_window_is_the_histogram_of_the_last_w_chunks():
+    # Sec. III.B: the moving-window histogram covers the last W chunks; it
+    # must equal the histogram of those chunks' bytes placed end to end
+    rng = np.random.default_rng(21)
+    for window in (1, 2, 3, 7):
+        st = oracle.StreamOracle(budget=960, window=window)
+        chunks = []
+        for c in range(12):
+            n = int(rng.integers(0, 9000))
+            law = synth.uniform() if c % 3 else synth.degenerate(int(rng.integers(0, 256)), 0.7)
+            x = synth.host(n, law, SEED + 30 + window, counter0=c << 14)
+            chunks.append(x)
+            st.push(x)
+            last = chunks[-window:]
+            expect = np.bincount(np.concatenate(last).astype(np.int64), minlength=256).astype(np.uint64)
+            assert np.array_equal(st.mw, expect), (window, c)
+        assert np.array_equal(st.totals, oracle.hist(np.concatenate(chunks)))
+
+
+def _constructed_chunk(kind):
+    # 25600 pixels: D puts 24320 on value 90 and 5 on every value; U puts 100
+    # on every value.  Counts are exact, so the switch has a closed form.
+    if kind == "D":
+        x = np.concatenate([np.full(24320, 90, np.uint8), np.repeat(np.arange(256, dtype=np.uint8), 5)])
+    else:
+        x = np.repeat(np.arange(256, dtype=np.uint8), 100)
+    return np.random.default_rng(len(kind)).permutation(x)
+
+
+@pytest.mark.parametrize("window", [1, 2, 4, 8])
+def test_moving_window_switch_follows_the_closed_form(window):
+    # With m chunks of type D among the w chunks in the window, bin 90 holds
+    # 24325 m + 100 (w - m) of 25600 w pixels, so the switch (theta 450/1000)
+    # says ADAPTIVE iff 1000 (24325 m + 100 (w - m)) >= 450 * 25600 w.
+    kinds = ["U"] * 6 + ["D"] * 9 + ["U"] * 10 + ["D"] * 3
+    st = oracle.StreamOracle(budget=8192, window=window)
+    got, expect = [], []
+    for k, kind in enumerate(kinds):
+        got.append(st.push(_constructed_chunk(kind)).kernel)
+        if k == 0:
+            expect.append(oracle.FLAG_PLAIN)
+        else:
+            win = kinds[max(0, k - window):k]
+            w, m = len(win), win.count("D")
+            expect.append(int(1000 * (24325 * m + 100 * (w - m)) >= 450 * 25600 * w))
+    assert got == expect
+    # the switch lags a phase change by the chunks the window needs
+    need = next(m for m in range(1, window + 1) if 1000 * (24325 * m + 100 * (window - m)) >= 450 * 25600 * window)
+    assert got[6 + need] == oracle.FLAG_ADAPTIVE and got[6 + need - 1] == oracle.FLAG_PLAIN
+
+
+def test_moving_window_of_one_is_the_previous_chunk():
+    st = oracle.StreamOracle(budget=2048, window=1)
+    prev = None
+    for c in range(10):
+        law = synth.degenerate(3, 0.6) if c % 4 < 2 else synth.normal(100, 3)
+        x = synth.host(4000 + c, law, SEED + 40, counter0=c << 13)
+        rec = st.push(x)
+        if prev is not None:
+            assert rec.kernel == oracle.switch(oracle.hist(prev))
+        prev = x
+
+
+def test_moving_window_rejects_zero():
+    with pytest.raises(ValueError):
+        oracle.StreamOracle(budget=960, window=0)
