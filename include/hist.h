@@ -164,12 +164,22 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
 #define HIST_MODE_PLAIN 1u    /* always the plain kernel (pattern still refreshed) */
 #define HIST_MODE_ADAPTIVE 2u /* always the adaptive kernel */
 
+/* Moving window (Sec. III.B: the accumulated histogram -- the stream
+ * totals -- and the moving-window histogram; Sec. III.C: the switch follows
+ * the last computed moving-window histogram).  The moving-window histogram
+ * after chunk c is the sum of the histograms of chunks c-W+1 .. c (those that
+ * exist), exact in uint64; the kernel of chunk c+1 in AUTO mode is its switch
+ * (max bin * 1000 >= theta * total).  The binning pattern still comes from
+ * chunk c alone.  W = 1 is the previous chunk. */
+#define HIST_WINDOW_MAX 256u
+
 typedef struct hist_config {
   uint32_t budget;      /* sub-bin table slots, HIST_BUDGET_MIN..MAX (default MAX) */
   uint32_t theta_milli; /* critical degeneracy per mille, 0..1000 (default 450) */
   uint32_t mode;        /* HIST_MODE_* (default AUTO) */
-  uint32_t grid;        /* CTAs per chunk launch; 0 = one per SM */
-  uint32_t reserved[4]; /* zero */
+  uint32_t grid;        /* CTAs per chunk launch; 0 = the kernel's default */
+  uint32_t window;      /* chunks in the moving window, 1..HIST_WINDOW_MAX (default 1) */
+  uint32_t reserved[3]; /* zero */
 } hist_config;
 
 void hist_config_init(hist_config* cfg);
@@ -200,6 +210,10 @@ int hist_stream_push_many(hist_stream* st, uint32_t count, const uint8_t* const*
 int hist_stream_flush(hist_stream* st, hist_cuda_stream s);
 /* Flush, then copy the running totals (uint64_t[256]) to d_totals. */
 int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s);
+/* Flush, then copy the moving-window histogram after the last pushed chunk
+ * (uint64_t[256]; all zero before the first chunk) to d_window.  A stream
+ * resumed with hist_stream_set_state restarts its window at that point. */
+int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s);
 
 /* Host-fed chunks (Sec. III.B: double-buffered transfers to the GPU overlapped
  * with the kernels).  attach_staging allocates `depth` (2..4) device staging
@@ -307,7 +321,8 @@ int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uin
  *   d_status      optional uint32_t: 0, or 4 if a bounded device wait ran out.
  * d_chunks / sizes are host arrays of `count` device pointers and sizes; each
  * size is below 2^32, and count is 1..HIST_NOALLOC_MAX_CHUNKS (more ->
- * HIST_EINVAL).  cfg->grid is ignored.
+ * HIST_EINVAL).  cfg->grid is ignored; cfg->window must be 1 (HIST_EINVAL
+ * otherwise).
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
  * -- the partial sums of three chunks in flight and their counters, about

@@ -150,14 +150,14 @@ class Stream:
     """Chunked stream with device-resident adaptive state (Sec. III.B / III.C)."""
 
     def __init__(self, budget: int = BUDGET_MAX, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO,
-                 grid: int = 0):
+                 grid: int = 0, window: int = 1):
         cfg = _abi.HistConfig()
         lib().hist_config_init(ctypes.byref(cfg))
-        cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid = budget, theta_milli, mode, grid
+        cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid, cfg.window = budget, theta_milli, mode, grid, window
         h = ctypes.c_void_p()
         _abi.check("hist_stream_create", lib().hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
-        self.budget, self.theta_milli, self.mode = budget, theta_milli, mode
+        self.budget, self.theta_milli, self.mode, self.window_chunks = budget, theta_milli, mode, window
 
     def close(self) -> None:
         if self._h:
@@ -212,6 +212,12 @@ class Stream:
     def totals(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
         _abi.check("hist_stream_totals", lib().hist_stream_totals(self._h, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def window(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """The moving-window histogram after the last pushed chunk (uint64 in an int64 tensor)."""
+        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
+        _abi.check("hist_stream_window", lib().hist_stream_window(self._h, out.data_ptr(), _stream_ptr(stream)))
         return out
 
     def state(self, stream=None) -> StreamState:

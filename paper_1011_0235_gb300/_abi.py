@@ -34,6 +34,7 @@ ESTATE = -7
 
 HIST_NOALLOC_MAX_CHUNKS = 128
 HIST_BATCH_MAX_IMAGES = 4096
+HIST_WINDOW_MAX = 256
 HIST_SERVER_MAX_STREAMS = 4096
 HIST_SERVER_MAX_BATCH = 1024
 HIST_SERVER_MAX_INFLIGHT = 8
@@ -63,7 +64,8 @@ class HistConfig(ctypes.Structure):
         ("theta_milli", ctypes.c_uint32),
         ("mode", ctypes.c_uint32),
         ("grid", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("window", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
@@ -164,6 +166,7 @@ SIGNATURES = [
     ("hist_stream_attach_staging", _I, [_P, _Z, _U32]),
     ("hist_stream_push_host", _I, [_P, _P, _Z, _P, _P]),
     ("hist_stream_totals", _I, [_P, _P, _P]),
+    ("hist_stream_window", _I, [_P, _P, _P]),
     ("hist_stream_get_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_set_state", _I, [_P, ctypes.POINTER(StreamState), _P]),
     ("hist_stream_run_noalloc", _I, [_P, _P, _U32, ctypes.POINTER(HistConfig), _P, _P, _P, _P]),

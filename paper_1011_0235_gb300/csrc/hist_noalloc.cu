@@ -272,7 +272,7 @@ extern "C" int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const siz
                                        uint32_t* d_status, hist_cuda_stream s) {
   if (!cfg || !d_totals || count == 0 || count > HIST_NOALLOC_MAX_CHUNKS || !d_chunks || !sizes) return HIST_EINVAL;
   if (cfg->budget < HIST_BUDGET_MIN || cfg->budget > HIST_BUDGET_MAX || cfg->theta_milli > 1000 ||
-      cfg->mode > HIST_MODE_ADAPTIVE)
+      cfg->mode > HIST_MODE_ADAPTIVE || cfg->window != 1)
     return HIST_EINVAL;
   for (uint32_t i = 0; i < count; ++i)
     if ((!d_chunks[i] && sizes[i]) || sizes[i] >= ((size_t)1 << 32)) return HIST_EINVAL;

@@ -60,6 +60,10 @@ struct StreamDev {
   uint32_t racc[kChunkRing][HIST_BINS];        // by flat chunk number mod kChunkRing
   unsigned long long rdone[kChunkRing];
   unsigned long long rcnt[kChunkRing];         // auto batches: CTA arrivals, never reset
+  // moving window (synced batches, window > 1): the window histogram after
+  // chunk c in mw[c mod 2], chunk c's histogram in wring[c mod (W + 1)]
+  unsigned long long mw[2][HIST_BINS];
+  uint32_t wring[HIST_WINDOW_MAX + 1][HIST_BINS];
   unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
   hist_pattern lpat[kLaunchRing][2];
   uint32_t lflag[kLaunchRing];
@@ -99,6 +103,9 @@ struct BatchArgs {
   uint32_t chunk0_full;             // flat: the stream's pattern is known to be the full table
   unsigned long long first_chunk;   // flat: number of this batch's first chunk among the stream's flat chunks
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
+  unsigned long long chunk_index;   // synced: index of this batch's first chunk in the stream
+  uint32_t window;                  // chunks in the moving window
+  uint32_t pad3;
   ChunkDesc c[kMaxBatch];
 };
 
@@ -294,6 +301,53 @@ __device__ __forceinline__ uint32_t publish_partials(CtaShared& cs, const ChunkD
   return c;
 }
 
+// Moving window (window > 1): chunk c's histogram is in cs.hist.  The
+// window histogram after chunk c is the one after chunk c-1 plus chunk c
+// minus chunk c-W (missing chunks count as empty); it replaces the switch
+// in cs.flag.  Every CTA computes it; CTA k of `ctas` stores the bins whose
+// index is k modulo `ctas` (window histogram by the parity of c, chunk
+// histogram in ring slot c mod (W + 1), so the slot read here, (c - W) mod
+// (W + 1), is never the one written).  A CTA's stores precede its next
+// publication, which every later reader waits for.  All threads call.
+__device__ __noinline__ void window_switch(StreamDev* st, unsigned long long c, uint32_t W, uint32_t theta,
+                                           uint32_t k, uint32_t ctas, CtaShared& cs) {
+  unsigned long long* red = cs.red;  // 16 of its words
+  const int t = threadIdx.x;
+  unsigned long long v = 0, mx = 0, tot = 0;
+  if (t < HIST_BINS) {
+    const unsigned long long prev = c >= 1 ? __ldcg(&st->mw[(c - 1) & 1][t]) : 0ull;
+    const unsigned long long old = c >= W ? (unsigned long long)__ldcg(&st->wring[(c - W) % (W + 1)][t]) : 0ull;
+    const uint32_t h = cs.hist[t];
+    v = prev + h - old;
+    if ((uint32_t)t % ctas == k) {
+      st->mw[c & 1][t] = v;
+      st->wring[c % (W + 1)][t] = h;
+    }
+    mx = v;
+    tot = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = m2 > mx ? m2 : mx;
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((t & 31) == 0) {
+      red[t >> 5] = mx;
+      red[8 + (t >> 5)] = tot;
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long m = 0, s = 0;
+    for (int i = 0; i < 8; ++i) {
+      m = red[i] > m ? red[i] : m;
+      s += red[8 + i];
+    }
+    cs.flag = reaches_theta(m, s, theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  }
+  __syncthreads();
+}
+
 // Synchronised batch: chunk j+1's kernel and pattern come from chunk j's
 // histogram, so every CTA waits for it (see the file comment).
 __global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_constant__ BatchArgs a) {
@@ -332,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_
         return;
       mark(j, 1);
       epilogue(pn, a.budget, a.theta, cs, es);
+      if (a.window > 1) window_switch(st, a.chunk_index + j - 1, a.window, a.theta, blockIdx.x, gridDim.x, cs);
     }
     mark(j, 2);
     {
@@ -896,13 +951,23 @@ __global__ void __launch_bounds__(kThreads, 2) batch_auto_kernel(const __grid_co
 
 // Epilogue of the last pushed chunk (one CTA of 1024 threads).
 __global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t ctas,
-                                                          uint32_t* out, uint32_t budget, uint32_t theta, uint32_t mode) {
+                                                          uint32_t* out, uint32_t budget, uint32_t theta, uint32_t mode,
+                                                          unsigned long long chunk, uint32_t window) {
   __shared__ uint32_t part[kThreads];
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
   if (!poll_gather(st, &st->rep[buf][0][0], &st->cnt[buf][0], complete_count(ctas, n), part, cs, nullptr)) return;
   epilogue(n, budget, theta, cs, es);
+  if (window > 1) window_switch(st, chunk, window, theta, 0, 1, cs);
   write_epilogue(st, out, mode, cs.flag, cs, 0, 1);
+}
+
+// The moving-window histogram after chunk `last` (none: zeros).
+__global__ void window_copy_kernel(const StreamDev* st, unsigned long long last, uint32_t window, bool any,
+                                   unsigned long long* out) {
+  const int b = threadIdx.x;
+  if (b >= HIST_BINS) return;
+  out[b] = !any ? 0ull : (window > 1 ? st->mw[last & 1][b] : (unsigned long long)st->last_hist[b]);
 }
 
 __global__ void init_kernel(StreamDev* st, uint32_t budget) {
@@ -931,6 +996,7 @@ struct hist_stream {
   bool flat_full;  // the stream's pattern is the full table (known on the host)
   unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
   unsigned long long flat_chunks;    // chunks of those launches
+  unsigned long long resume_chunk;   // first chunk after the last set_state
   bool pending;
   uint32_t* pending_out;
   uint32_t pending_n;
@@ -964,6 +1030,8 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   a->first_buf = (uint32_t)(st->chunks_launched % 3);
   a->chunk0_full = st->flat_full ? 1u : 0u;
   a->first_chunk = st->flat_chunks;
+  a->chunk_index = st->chunks_launched;
+  a->window = st->cfg.window;
   a->launch = st->flat_launches + 1;
   a->budget = st->cfg.budget;
   a->theta = st->cfg.theta_milli;
@@ -1035,7 +1103,8 @@ int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, cons
 int do_flush(hist_stream* st, cudaStream_t s) {
   if (!st->pending) return HIST_OK;
   finish_kernel<<<1, kThreads, 0, s>>>(st->d, st->pending_buf, st->pending_n, (uint32_t)st->grid, st->pending_out,
-                                       st->cfg.budget, st->cfg.theta_milli, st->cfg.mode);
+                                       st->cfg.budget, st->cfg.theta_milli, st->cfg.mode, st->chunks_launched - 1,
+                                       st->cfg.window);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);
   st->pending = false;
@@ -1045,7 +1114,7 @@ int do_flush(hist_stream* st, cudaStream_t s) {
 
 bool config_ok(const hist_config* c) {
   return c && c->budget >= HIST_BUDGET_MIN && c->budget <= HIST_BUDGET_MAX && c->theta_milli <= 1000 &&
-         c->mode <= HIST_MODE_ADAPTIVE;
+         c->mode <= HIST_MODE_ADAPTIVE && c->window >= 1 && c->window <= HIST_WINDOW_MAX;
 }
 
 int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem, bool flat) {
@@ -1085,6 +1154,7 @@ void hist_config_init(hist_config* c) {
   c->theta_milli = HIST_THETA_MILLI_DEFAULT;
   c->mode = HIST_MODE_AUTO;
   c->grid = 0;
+  c->window = 1;
 }
 
 int hist_stream_create(const hist_config* cfg, hist_stream** out) {
@@ -1095,8 +1165,10 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   st->cfg = *cfg;
   st->sms = sm_count();
   // modes whose chunk layouts never depend on the previous chunk's histogram
-  st->flat = cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX);
-  st->autok = cfg->mode == HIST_MODE_AUTO && cfg->budget == HIST_BUDGET_MAX;
+  // a window of more than one chunk needs the chunks in order: the synced kernel
+  const bool w1 = cfg->window == 1;
+  st->flat = w1 && (cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX));
+  st->autok = w1 && cfg->mode == HIST_MODE_AUTO && cfg->budget == HIST_BUDGET_MAX;
   const void* fn = st->flat ? (const void*)batch_flat_kernel
                             : (st->autok ? (const void*)batch_auto_kernel : (const void*)batch_synced_kernel);
   static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_auto[kMaxDevices];
@@ -1216,6 +1288,17 @@ int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s) 
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 
+int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s) {
+  if (!st || !d_window) return HIST_EINVAL;
+  int rc = do_flush(st, (cudaStream_t)s);
+  if (rc) return rc;
+  const bool any = st->chunks_launched > st->resume_chunk;
+  window_copy_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
+                                                            reinterpret_cast<unsigned long long*>(d_window));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
 int hist_stream_get_state(hist_stream* st, hist_stream_state* h, hist_cuda_stream s) {
   if (!st || !h) return HIST_EINVAL;
   int rc = do_flush(st, (cudaStream_t)s);
@@ -1263,6 +1346,7 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h, hist_cuda
   st->flat_full = false;  // the next flat launch reads the restored pattern
   st->flat_launches = 0;   // the rings restart with the zeroed scratch
   st->flat_chunks = 0;
+  st->resume_chunk = st->chunks_launched;  // and so does the moving window
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 

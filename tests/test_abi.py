@@ -53,7 +53,7 @@ def test_strerror_and_config(lib):
     assert lib.hist_strerror(-1) == b"invalid argument"
     cfg = _abi.HistConfig()
     lib.hist_config_init(ctypes.byref(cfg))
-    assert (cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid) == (8192, 450, 0, 0)
+    assert (cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid, cfg.window) == (8192, 450, 0, 0, 1)
 
 
 def _to_c(p):
@@ -105,6 +105,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == _abi.EINVAL
     cfg.theta_milli, cfg.mode = 450, 3
     assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == _abi.EINVAL
+    cfg.mode = 0
+    for w in (0, _abi.HIST_WINDOW_MAX + 1):
+        cfg.window = w
+        assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == _abi.EINVAL
+    assert lib.hist_stream_window(None, None, None) == _abi.EINVAL
 
 
 def test_server_argument_errors_without_gpu(lib):

@@ -139,6 +139,95 @@ def test_back_to_back_batches(mode):
     st.close()
 
 
+def _window_chunks(count, seed, sizes=(0, 1, 4095, 65_536, 300_001)):
+    rng = np.random.default_rng(seed)
+    sz = [int(x) for x in rng.choice(sizes, size=count)]
+    return _phase_chunks(count, lambda c: sz[c], 6, SEED + seed)
+
+
+@pytest.mark.parametrize("window", [2, 4, 32])
+@pytest.mark.parametrize("mode,budget", [(hl.MODE_AUTO, 8192), (hl.MODE_AUTO, 960), (hl.MODE_PLAIN, 8192),
+                                         (hl.MODE_ADAPTIVE, 8192), (hl.MODE_ADAPTIVE, 2048)])
+def test_moving_window_stream(window, mode, budget):
+    """The switch follows the moving-window histogram of the last W chunks
+    (Sec. III.B / III.C): every chunk's output, the state and the window
+    histogram after every push_many call match the oracle."""
+    chunks = _window_chunks(70, window + 3 * mode + budget % 7)
+    ref = oracle.StreamOracle(budget, mode=mode, window=window)
+    offs, pos = [], 0
+    for c, ch in enumerate(chunks):
+        pos += c % 16
+        offs.append(pos)
+        pos += ch.size
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=budget, mode=mode, window=window)
+    assert not np.any(u64(st.window()))
+    rng = np.random.default_rng(window)
+    i = 0
+    while i < len(chunks):
+        idx = list(range(i, min(i + int(rng.integers(1, 9)), len(chunks))))
+        st.push_many([bd.data_ptr() + offs[j] for j in idx], [chunks[j].size for j in idx],
+                      [outs[j].data_ptr() for j in idx])
+        for j in idx:
+            rec = ref.push(chunks[j])
+        i += len(idx)
+        _check_state(st.state(), ref, rec)
+        assert np.array_equal(u64(st.window()), ref.mw), i
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, ch in enumerate(chunks):
+        assert np.array_equal(got[j], oracle.hist_u32(ch)), j
+    st.close()
+
+
+def test_moving_window_of_256_chunks():
+    # more chunks than the window: every slot of the window's ring is reused
+    chunks = _window_chunks(300, 99, sizes=(0, 17, 4096, 20_000))
+    ref = oracle.StreamOracle(8192, window=256)
+    recs = [ref.push(ch) for ch in chunks]
+    flat = np.concatenate(chunks) if chunks else np.zeros(0, np.uint8)
+    bd = dev(np.concatenate([flat, np.zeros(16, np.uint8)]))
+    st = hl.Stream(budget=8192, window=256)
+    pos = 0
+    ptrs, sizes = [], []
+    for ch in chunks:
+        ptrs.append(bd.data_ptr() + pos)
+        sizes.append(ch.size)
+        pos += ch.size
+    for k in range(0, len(chunks), 100):
+        st.push_many(ptrs[k:k + 100], sizes[k:k + 100])
+    _check_state(st.state(), ref, recs[-1])
+    assert np.array_equal(u64(st.window()), ref.mw)
+    st.close()
+
+
+def test_moving_window_restarts_after_resume():
+    chunks = _window_chunks(20, 7)
+    ref_a = oracle.StreamOracle(8192, window=4)
+    st = hl.Stream(budget=8192, window=4)
+    for ch in chunks[:10]:
+        ref_a.push(ch)
+        st.push(dev(ch) if ch.size else torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    saved = st.state()
+    st2 = hl.Stream(budget=8192, window=4)
+    st2.set_state(saved)
+    assert not np.any(u64(st2.window()))
+    # the resumed stream's window holds only chunks pushed after the resume;
+    # its first switch comes from the restored state
+    ref_b = oracle.StreamOracle(8192, window=4)
+    ref_b.totals, ref_b.pattern, ref_b.flag, ref_b.chunks = ref_a.totals.copy(), ref_a.pattern, ref_a.flag, ref_a.chunks
+    for ch in chunks[10:]:
+        rec = ref_b.push(ch)
+        st2.push(dev(ch) if ch.size else torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    _check_state(st2.state(), ref_b, rec)
+    assert np.array_equal(u64(st2.window()), ref_b.mw)
+    st.close()
+    st2.close()
+
+
 def test_stream_checkpoint_resume():
     chunks = _phase_chunks(10, lambda c: 200_000 + c, 3, SEED + 6)
     ref = oracle.StreamOracle(960)
