@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
-    ap.add_argument("--profile-part", default=None, choices=["serving", "batch"],
+    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
                          "(4000 requests) or the 4096-image batch")
     return ap.parse_args()
@@ -254,6 +254,39 @@ def batch_extras(torch, hl, synth, hbm, steps, autotune=True):
                              "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}}
 
 
+def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
+    """Table 1 on this GPU: GB/s of the five cumulative kernel variants on
+    n bytes (1 GiB) of uniform pixels (the paper's random input) and of N(128, 8), for
+    the per-warp kernel, the adaptive kernel with the 960-slot default
+    pattern (the paper's table) and with the full 8192-slot table."""
+    import oracle
+    from paper_1011_0235_gb300 import _abi
+    lib = hl.lib()
+    full = ([32 * b for b in range(256)], [5] * 256, 8192, 8192)
+    d960 = oracle.default_pattern(960)
+    pats = {"plain": None, "adaptive_960": hl.pattern_from_host(d960.off, d960.log2k, 960, d960.used),
+            "adaptive_8192": hl.pattern_from_host(*full)}
+    sink = torch.empty(lib.hist_ablation_grid(n) * 256, dtype=torch.int32, device="cuda")
+    out = torch.empty(256, dtype=torch.int32, device="cuda")
+    res = {"bytes": n, "stages": ["read+write", "+init", "+pattern", "+atomics", "+reduce"]}
+    for law_name, law in (("uniform", synth.uniform()), ("normal_sigma8", synth.normal(128, 8))):
+        x = torch.empty(n, dtype=torch.uint8, device="cuda")
+        synth.device_fill(x.data_ptr(), n, law, synth.SEED_BASE + 13, 0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        for name, pd in pats.items():
+            row = []
+            for stage in range(1, 6):
+                def step(stage=stage, pd=pd):
+                    _abi.check("hist_ablation", lib.hist_ablation(
+                        x.data_ptr(), n, pd.data_ptr() if pd is not None else None, stage,
+                        out.data_ptr(), sink.data_ptr(), torch.cuda.current_stream().cuda_stream))
+                el = time_steps(torch, step, 2, steps)
+                row.append(round(n * steps / el / 1e9, 1))
+            res["%s_%s_gbs" % (law_name, name)] = row
+        del x
+    return res
+
+
 def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     """The serving workload: Poisson arrivals over 256 streams with 64 MiB
     payload regions each (16 GiB resident), sizes log-uniform in 4 KiB ..
@@ -385,6 +418,8 @@ def run_part(args):
     hl.lib()
     if args.profile_part == "serving":
         out = serving_extras(torch, np, hl, synth, 6800.0, rates=())
+    elif args.profile_part == "ablation":
+        out = ablation_extras(torch, hl, synth, 6800.0, steps=1, n=256 << 20)
     else:
         out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=False)
     print(json.dumps({"profile_part": args.profile_part, "result": out}))
@@ -489,6 +524,7 @@ def run_native(args):
         del xdg
         extras.update(batch_extras(torch, hl, synth, hbm, steps=max(3, min(args.steps, 10))))
         extras["serving"] = serving_extras(torch, np, hl, synth, hbm)
+        extras["ablation_table1"] = ablation_extras(torch, hl, synth, hbm)
         # one-shot kernels on the whole 1 GiB at once (no stream)
         full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
         o = hl.empty_hist()

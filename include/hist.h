@@ -338,6 +338,22 @@ int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes,
                             const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals,
                             uint32_t* d_status, hist_cuda_stream s);
 
+/* ------------------------------------------------------------- ablation -- */
+/* The adaptive kernel built up in Table 1's five cumulative steps, for
+ * measuring what each step costs (with d_pat null: the per-warp kernel):
+ *   1  read every packed pixel, write a 256-word result per CTA;
+ *   2  + clear the shared sub-histogram;
+ *   3  + read the binning pattern and compute every pixel's sub-bin address;
+ *   4  + the shared-memory increments;
+ *   5  + sum the sub-bins per bin and write the histogram (= hist_adaptive,
+ *        or hist_plain without a pattern).
+ * Stage 5 overwrites d_out (uint32_t[256]); stages 1-4 write
+ * hist_ablation_grid(n) x 256 words of scratch to d_sink, contents
+ * unspecified.  n < 2^32; HIST_EINVAL for a bad stage or a missing buffer. */
+int hist_ablation_grid(size_t n);
+int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t stage, uint32_t* d_out,
+                  uint32_t* d_sink, hist_cuda_stream s);
+
 /* --------------------------------------------------------------- server -- */
 /* A serving loop (Sec. III.B's stream, for many independent streams whose
  * chunks arrive as requests).  Each of `streams` streams keeps its adaptive

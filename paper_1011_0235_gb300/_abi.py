@@ -176,6 +176,8 @@ SIGNATURES = [
     ("hist_batch_graph_launch", _I, [_P, _P]),
     ("hist_batch_graph_destroy", _I, [_P]),
     ("hist_batch_autotune", _I, [_P, _P, _U32, _P, _U32, ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_float)]),
+    ("hist_ablation_grid", _I, [_Z]),
+    ("hist_ablation", _I, [_P, _Z, _P, _U32, _P, _P, _P]),
     ("hist_server_config_init", None, [ctypes.POINTER(ServerConfig)]),
     ("hist_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
     ("hist_server_destroy", _I, [_P]),

@@ -1,0 +1,179 @@
+// hist_ablation.cu -- the kernel built up step by step (Table 1).
+//
+// Table 1 measures the adaptive kernel as five cumulative variants: read the
+// packed pixels and write a block result; + clear the shared sub-histogram;
+// + read the binning pattern; + the sub-histogram atomics; + sum the sub-bins
+// and write the histogram.  This file builds the same five variants on the
+// one-shot kernel's structure (2 CTAs of 1024 threads per SM, each CTA one
+// contiguous range of 16-byte vectors), so that the time each step adds can
+// be measured on this hardware:
+//   stage 1: load every vector and fold it into a register; each CTA writes
+//            256 words (its "block result") to a scratch sink;
+//   stage 2: + clear the 32 KiB shared table;
+//   stage 3: + read the binning pattern into shared memory and compute every
+//            pixel's sub-bin address (the lookup or shift of the layout),
+//            folding the addresses into the register instead of counting;
+//   stage 4: + the shared-memory increments (the full counting);
+//   stage 5: + reduce the table per bin and add it into the histogram: the
+//            complete kernel (hist_plain / hist_adaptive).
+// Without a pattern the variants are those of the per-warp (plain) kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hist.h"
+#include "hist_device.cuh"
+#include "hist_internal.h"
+
+using namespace histdev;
+using namespace histlib;
+
+namespace {
+
+// Sub-bin address of pixel v (PATH/LK as in count_word), or the increment.
+template <int STAGE, int PATH, int LK>
+__device__ __forceinline__ void ablate_word(uint32_t w, uint32_t base, uint32_t lutb, uint32_t table, uint32_t& acc) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t v = (w >> (8 * k)) & 0xffu;
+    if (STAGE <= 2) {
+      acc += v;
+    } else {
+      const uint32_t a = PATH == PATH_LUT ? table + (shared_ld(lutb + (v << 7)) << 2) : base + (v << (LK + 2));
+      if (STAGE == 3) acc ^= a;
+      else shared_inc(a);
+    }
+  }
+}
+
+template <int STAGE, int PATH, int LK>
+__device__ void ablate_range(const uint4* __restrict__ p, size_t begin, size_t end, uint32_t* table,
+                             const uint32_t* lut, uint32_t& acc) {
+  uint32_t base, lutb, tab;
+  thread_bases<PATH, LK>(table, lut, base, lutb, tab);
+  size_t i = begin + threadIdx.x;
+  for (; i + kThreads < end; i += 2 * kThreads) {
+    const uint4 a = ldg_stream(p + i), b = ldg_stream(p + i + kThreads);
+    ablate_word<STAGE, PATH, LK>(a.x, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.y, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.z, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.w, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(b.x, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(b.y, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(b.z, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(b.w, base, lutb, tab, acc);
+  }
+  for (; i < end; i += kThreads) {
+    const uint4 a = ldg_stream(p + i);
+    ablate_word<STAGE, PATH, LK>(a.x, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.y, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.z, base, lutb, tab, acc);
+    ablate_word<STAGE, PATH, LK>(a.w, base, lutb, tab, acc);
+  }
+}
+
+template <int STAGE>
+__device__ void ablate_dispatch(int path, int lk, const uint4* p, size_t begin, size_t end, uint32_t* table,
+                                const uint32_t* lut, uint32_t& acc) {
+  if (begin >= end) return;
+  if (STAGE <= 2 || path == PATH_PLAIN) ablate_range<STAGE, PATH_PLAIN, 0>(p, begin, end, table, lut, acc);
+  else if (path == PATH_LUT) ablate_range<STAGE, PATH_LUT, 0>(p, begin, end, table, lut, acc);
+  else {
+    switch (lk) {
+      case 5: ablate_range<STAGE, PATH_SHIFT, 5>(p, begin, end, table, lut, acc); break;
+      case 4: ablate_range<STAGE, PATH_SHIFT, 4>(p, begin, end, table, lut, acc); break;
+      case 3: ablate_range<STAGE, PATH_SHIFT, 3>(p, begin, end, table, lut, acc); break;
+      case 2: ablate_range<STAGE, PATH_SHIFT, 2>(p, begin, end, table, lut, acc); break;
+      case 1: ablate_range<STAGE, PATH_SHIFT, 1>(p, begin, end, table, lut, acc); break;
+      default: ablate_range<STAGE, PATH_SHIFT, 0>(p, begin, end, table, lut, acc); break;
+    }
+  }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kThreads, 2)
+    ablation_kernel(const uint8_t* __restrict__ in, size_t n, const hist_pattern* __restrict__ pat,
+                    uint32_t* __restrict__ out, uint32_t* __restrict__ sink) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* table = smem;
+  uint32_t* lut = smem + kTableWords;
+  __shared__ CtaShared cs;
+  __shared__ uint32_t wacc[kWarps];
+
+  if (STAGE >= 2) zero_table(table);
+  if (STAGE >= 3 && pat) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(pat);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&cs.pat);
+    for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += kThreads) dst[i] = src[i];
+    __syncthreads();
+    classify_pattern(cs.pat, lut, cs);
+  } else {
+    if (threadIdx.x == 0) {
+      cs.path = PATH_PLAIN;
+      cs.lk = 0;
+    }
+    __syncthreads();
+  }
+  const Split sp = split_bytes(in, n);
+  const uint4* body = reinterpret_cast<const uint4*>(in + sp.head);
+  const size_t per = (sp.nvec + gridDim.x - 1) / gridDim.x;
+  const size_t begin = per * blockIdx.x;
+  const size_t end = begin + per < sp.nvec ? begin + per : sp.nvec;
+  uint32_t acc = 0;
+  ablate_dispatch<STAGE>(cs.path, cs.lk, body, begin, end, table, lut, acc);
+  if (STAGE == 5) {
+    flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
+    if (blockIdx.x == 0) {
+      count_edges(in, sp, cs);
+      __syncthreads();
+    }
+    if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x]) atomicAdd(out + threadIdx.x, cs.res[threadIdx.x]);
+  } else {
+    // the block result: 256 words per CTA, built from every thread's register
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) wacc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < HIST_BINS) sink[(size_t)blockIdx.x * HIST_BINS + threadIdx.x] = wacc[threadIdx.x & 31] ^ threadIdx.x;
+  }
+}
+
+const void* ablation_fn(uint32_t stage) {
+  switch (stage) {
+    case 1: return (const void*)ablation_kernel<1>;
+    case 2: return (const void*)ablation_kernel<2>;
+    case 3: return (const void*)ablation_kernel<3>;
+    case 4: return (const void*)ablation_kernel<4>;
+    default: return (const void*)ablation_kernel<5>;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int hist_ablation_grid(size_t n) {
+  const size_t nvec = n / 16 + 1;
+  const size_t want = (nvec + 4 * kThreads - 1) / (4 * kThreads);
+  const size_t cap = 2 * (size_t)sm_count();
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t stage, uint32_t* d_out,
+                  uint32_t* d_sink, hist_cuda_stream s) {
+  if ((!d_in && n) || n >= ((size_t)1 << 32) || stage < 1 || stage > 5) return HIST_EINVAL;
+  if (stage == 5 && !d_out) return HIST_EINVAL;
+  if (stage < 5 && !d_sink) return HIST_EINVAL;
+  static int attr_done[5][kMaxDevices];
+  const void* fn = ablation_fn(stage);
+  int rc = ensure_smem_attr_bytes(fn, attr_done[stage - 1], kSmemBytes);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (stage == 5) e = cudaMemsetAsync(d_out, 0, HIST_BINS * sizeof(uint32_t), (cudaStream_t)s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int grid = hist_ablation_grid(n);
+  void* args[] = {(void*)&d_in, (void*)&n, (void*)&d_pat, (void*)&d_out, (void*)&d_sink};
+  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, kSmemBytes, (cudaStream_t)s);
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
+}  // extern "C"
