@@ -67,10 +67,9 @@ def workload_config(chunks):
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1011_0235_gb300 import shard
+
+    return shard.env()
 
 
 # ------------------------------------------------------------- clocks ----
@@ -171,11 +170,14 @@ def recorded_traffic(kernel):
     return k.get("dram_bytes_per_launch")
 
 
-def gen_workload_device(torch, synth, chunks, seed, thr_fn):
+def gen_workload_device(torch, synth, chunks, seed, thr_fn, first_chunk=0):
+    """Chunks first_chunk .. first_chunk + chunks - 1 of the synthetic stream
+    (a rank's own slice of one long stream)."""
     x = torch.empty(chunks * CHUNK, dtype=torch.uint8, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     for c in range(chunks):
-        synth.device_fill(x.data_ptr() + c * CHUNK, CHUNK, thr_fn(c), seed, c * CHUNK, s)
+        g = first_chunk + c
+        synth.device_fill(x.data_ptr() + c * CHUNK, CHUNK, thr_fn(g), seed, g * CHUNK, s)
     torch.cuda.synchronize()
     return x
 
@@ -452,7 +454,7 @@ def run_native(args):
     nbytes = chunks * CHUNK
     thr = synth.normal(128, 8)
     seed = synth.SEED_BASE + 2
-    x = gen_workload_device(torch, synth, chunks, seed, lambda c: thr)
+    x = gen_workload_device(torch, synth, chunks, seed, lambda c: thr, first_chunk=rank * chunks)
     ptrs = [x.data_ptr() + c * CHUNK for c in range(chunks)]
     sizes = [CHUNK] * chunks
 
@@ -474,10 +476,8 @@ def run_native(args):
             torch.cuda.synchronize()
     el = time_steps(torch, step, args.warmup, args.steps, barrier)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([el], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    from paper_1011_0235_gb300 import shard
+    el = shard.slowest(el, device="cuda")
     value = world * nbytes * args.steps / el / 1e9
     # the adaptive stream at the full table runs batch_flat_kernel: one launch per
     # push_many of up to STREAM_MAX_BATCH chunks, nothing left for flush
@@ -555,10 +555,7 @@ def run_native(args):
 
         ksteps = max(3, min(args.steps, 20))
         el_e = time_steps(torch, e2e_step, max(args.warmup, 3), ksteps, barrier)
-        if world > 1:
-            t = torch.tensor([el_e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el_e = float(t.item())
+        el_e = shard.slowest(el_e, device="cuda")
         e2e = {"value": round(world * nbytes * ksteps / el_e / 1e9, 2), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 256 * 8, "steps": ksteps,
                "path": "hist_stream_push_host: pinned host -> 3 staging buffers, copies overlapped with kernels"}
