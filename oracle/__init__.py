@@ -236,3 +236,32 @@ class StreamOracle:
         self.pattern = binning_pattern(rec.hist, self.budget)
         self.chunks += 1
         return rec
+
+
+# ------------------------------------------------------- change detection ----
+
+CHANGE_TAU_MILLI_DEFAULT = 250
+
+
+def change_distance(acc, window):
+    """Total-variation distance between the accumulated histogram and the
+    moving-window histogram, each normalised to sum 1 (Sec. III.B compares
+    the two to detect a change; the paper gives no rule, this is the reading
+    used here): 1/2 sum_b |acc_b / sum(acc) - window_b / sum(window)|, as an
+    exact fraction.  0 if either histogram is empty."""
+    from fractions import Fraction
+
+    a = [int(v) for v in np.asarray(acc, dtype=np.uint64)]
+    m = [int(v) for v in np.asarray(window, dtype=np.uint64)]
+    assert len(a) == len(m) == BINS
+    sa, sm = sum(a), sum(m)
+    if sa == 0 or sm == 0:
+        return Fraction(0)
+    return sum(abs(Fraction(x, sa) - Fraction(y, sm)) for x, y in zip(a, m)) / 2
+
+
+def change(acc, window, tau_milli: int = CHANGE_TAU_MILLI_DEFAULT) -> int:
+    """1 iff the distance reaches tau_milli / 1000."""
+    from fractions import Fraction
+
+    return int(change_distance(acc, window) >= Fraction(tau_milli, 1000))

@@ -488,3 +488,58 @@ def test_moving_window_of_one_is_the_previous_chunk():
 def test_moving_window_rejects_zero():
     with pytest.raises(ValueError):
         oracle.StreamOracle(budget=960, window=0)
+
+
+# ------------------------------------------------------ change detection ----
+
+def _h(d):
+    h = np.zeros(256, np.uint64)
+    for k, v in d.items():
+        h[k] = v
+    return h
+
+
+def test_change_distance_special_cases():
+    from fractions import Fraction
+    a = _h({5: 10, 9: 30})
+    assert oracle.change_distance(a, a) == 0
+    assert oracle.change_distance(a, a * 7) == 0  # normalised: scale does not matter
+    assert oracle.change_distance(_h({1: 4}), _h({2: 9})) == 1  # disjoint supports
+    assert oracle.change_distance(np.zeros(256, np.uint64), a) == 0
+    assert oracle.change_distance(a, np.zeros(256, np.uint64)) == 0
+    # hand-worked: (3/4, 1/4) against (1/2, 1/2): (1/4 + 1/4) / 2
+    assert oracle.change_distance(_h({0: 3, 1: 1}), _h({0: 1, 1: 1})) == Fraction(1, 4)
+    # symmetric
+    x, y = _h({0: 5, 7: 2, 200: 9}), _h({0: 1, 7: 11})
+    assert oracle.change_distance(x, y) == oracle.change_distance(y, x)
+
+
+def test_change_threshold_is_inclusive():
+    a, m = _h({0: 3, 1: 1}), _h({0: 1, 1: 1})  # distance exactly 1/4
+    assert oracle.change(a, m, 250) == 1
+    assert oracle.change(a, m, 251) == 0
+    assert oracle.change(a, a, 0) == 1  # distance 0 reaches a threshold of 0
+
+
+def test_change_distance_matches_brute_force_on_random_histograms():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a = rng.integers(0, 1 << 40, 256).astype(np.uint64)
+        m = rng.integers(0, 1 << 30, 256).astype(np.uint64)
+        m[rng.integers(0, 256, 100)] = 0
+        d = float(oracle.change_distance(a, m))
+        ref = 0.5 * np.abs(a / a.sum(dtype=np.float64) - m / m.sum(dtype=np.float64)).sum()
+        assert abs(d - ref) < 1e-12
+
+
+def test_change_after_a_phase_change():
+    # a long uniform stream, then a degenerate phase: the window sees the new
+    # phase long before the accumulated histogram does
+    st = oracle.StreamOracle(8192, window=4)
+    flags = []
+    for c in range(30):
+        law = synth.uniform() if c < 20 else synth.degenerate(90, 0.95)
+        st.push(synth.host(20_000, law, SEED + 50, c * 20_000))
+        flags.append(oracle.change(st.totals, st.mw, 250))
+    assert flags[:20] == [0] * 20
+    assert all(flags[21:])
