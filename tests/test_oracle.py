@@ -492,7 +492,7 @@ def test_moving_window_rejects_zero():
 
 # ------------------------------------------------------ change detection ----
 
-def _h(d):
+def _hd(d):
     h = np.zeros(256, np.uint64)
     for k, v in d.items():
         h[k] = v
@@ -501,21 +501,21 @@ def _h(d):
 
 def test_change_distance_special_cases():
     from fractions import Fraction
-    a = _h({5: 10, 9: 30})
+    a = _hd({5: 10, 9: 30})
     assert oracle.change_distance(a, a) == 0
     assert oracle.change_distance(a, a * 7) == 0  # normalised: scale does not matter
-    assert oracle.change_distance(_h({1: 4}), _h({2: 9})) == 1  # disjoint supports
+    assert oracle.change_distance(_hd({1: 4}), _hd({2: 9})) == 1  # disjoint supports
     assert oracle.change_distance(np.zeros(256, np.uint64), a) == 0
     assert oracle.change_distance(a, np.zeros(256, np.uint64)) == 0
     # hand-worked: (3/4, 1/4) against (1/2, 1/2): (1/4 + 1/4) / 2
-    assert oracle.change_distance(_h({0: 3, 1: 1}), _h({0: 1, 1: 1})) == Fraction(1, 4)
+    assert oracle.change_distance(_hd({0: 3, 1: 1}), _hd({0: 1, 1: 1})) == Fraction(1, 4)
     # symmetric
-    x, y = _h({0: 5, 7: 2, 200: 9}), _h({0: 1, 7: 11})
+    x, y = _hd({0: 5, 7: 2, 200: 9}), _hd({0: 1, 7: 11})
     assert oracle.change_distance(x, y) == oracle.change_distance(y, x)
 
 
 def test_change_threshold_is_inclusive():
-    a, m = _h({0: 3, 1: 1}), _h({0: 1, 1: 1})  # distance exactly 1/4
+    a, m = _hd({0: 3, 1: 1}), _hd({0: 1, 1: 1})  # distance exactly 1/4
     assert oracle.change(a, m, 250) == 1
     assert oracle.change(a, m, 251) == 0
     assert oracle.change(a, a, 0) == 1  # distance 0 reaches a threshold of 0
