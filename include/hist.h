@@ -338,6 +338,29 @@ int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes,
                             const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals,
                             uint32_t* d_status, hist_cuda_stream s);
 
+/* ------------------------------------------------------ change detection -- */
+/* Sec. III.B keeps an accumulated histogram and a moving-window histogram and
+ * compares them to detect a change in the stream; it gives no rule.  The rule
+ * here: the total-variation distance between the two histograms normalised
+ * to sum 1, 1/2 sum_b |acc_b / sum(acc) - win_b / sum(win)|, against a
+ * threshold tau (per mille; change iff distance >= tau / 1000), evaluated
+ * exactly in 128-bit integers while sum(acc) < 2^56 and sum(win) < 2^40
+ * (in_range says so; beyond it the result is unspecified).  Either histogram
+ * empty: distance 0. */
+#define HIST_CHANGE_TAU_MILLI_DEFAULT 250u
+
+typedef struct hist_change_result {
+  uint64_t dist_ppm; /* floor(10^6 x distance) */
+  uint32_t flag;     /* 1: distance >= tau */
+  uint32_t in_range; /* 1: the sums were within the exact range */
+} hist_change_result;
+
+/* d_acc, d_win: uint64_t[256] on the device; d_res: one result on the device. */
+int hist_change(const uint64_t* d_acc, const uint64_t* d_win, uint32_t tau_milli, hist_change_result* d_res,
+                hist_cuda_stream s);
+/* Flush, then compare the stream's totals with its moving-window histogram. */
+int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* d_res, hist_cuda_stream s);
+
 /* ------------------------------------------------------------- ablation -- */
 /* The adaptive kernel built up in Table 1's five cumulative steps, for
  * measuring what each step costs (with d_pat null: the per-warp kernel):

@@ -146,6 +146,23 @@ def degeneracy_to_host(res: torch.Tensor) -> tuple[int, int, int, int]:
 
 # ------------------------------------------------------------------ stream --
 
+def change(acc: torch.Tensor, window: torch.Tensor, tau_milli: int = _abi.HIST_CHANGE_TAU_MILLI_DEFAULT,
+           stream=None) -> torch.Tensor:
+    """Change detection between two uint64[256] histograms (int64 device
+    tensors): a device tensor holding one hist_change_result."""
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    _abi.check("hist_change", lib().hist_change(acc.data_ptr(), window.data_ptr(), tau_milli, out.data_ptr(),
+                                                _stream_ptr(stream)))
+    return out
+
+
+def change_to_host(res: torch.Tensor) -> tuple[int, int, int]:
+    """(distance in parts per million, flag, in_range) of a change result."""
+    torch.cuda.synchronize()
+    r = _abi.ChangeResult.from_buffer_copy(res.cpu().numpy().tobytes())
+    return int(r.dist_ppm), int(r.flag), int(r.in_range)
+
+
 class Stream:
     """Chunked stream with device-resident adaptive state (Sec. III.B / III.C)."""
 
@@ -218,6 +235,14 @@ class Stream:
         """The moving-window histogram after the last pushed chunk (uint64 in an int64 tensor)."""
         out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
         _abi.check("hist_stream_window", lib().hist_stream_window(self._h, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def change(self, tau_milli: int = _abi.HIST_CHANGE_TAU_MILLI_DEFAULT, stream=None) -> torch.Tensor:
+        """Change detection between the totals and the moving window: a device
+        tensor holding one hist_change_result (see change_to_host)."""
+        out = torch.zeros(2, dtype=torch.int64, device="cuda")
+        _abi.check("hist_stream_change", lib().hist_stream_change(self._h, tau_milli, out.data_ptr(),
+                                                                  _stream_ptr(stream)))
         return out
 
     def state(self, stream=None) -> StreamState:

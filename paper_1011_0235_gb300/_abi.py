@@ -35,6 +35,7 @@ ESTATE = -7
 HIST_NOALLOC_MAX_CHUNKS = 128
 HIST_BATCH_MAX_IMAGES = 4096
 HIST_WINDOW_MAX = 256
+HIST_CHANGE_TAU_MILLI_DEFAULT = 250
 HIST_SERVER_MAX_STREAMS = 4096
 HIST_SERVER_MAX_BATCH = 1024
 HIST_SERVER_MAX_INFLIGHT = 8
@@ -90,6 +91,14 @@ class StreamState(ctypes.Structure):
         ("last_kernel", ctypes.c_uint32),
         ("status", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32 * 7),
+    ]
+
+
+class ChangeResult(ctypes.Structure):
+    _fields_ = [
+        ("dist_ppm", ctypes.c_uint64),
+        ("flag", ctypes.c_uint32),
+        ("in_range", ctypes.c_uint32),
     ]
 
 
@@ -176,6 +185,8 @@ SIGNATURES = [
     ("hist_batch_graph_launch", _I, [_P, _P]),
     ("hist_batch_graph_destroy", _I, [_P]),
     ("hist_batch_autotune", _I, [_P, _P, _U32, _P, _U32, ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_float)]),
+    ("hist_change", _I, [_P, _P, _U32, _P, _P]),
+    ("hist_stream_change", _I, [_P, _U32, _P, _P]),
     ("hist_ablation_grid", _I, [_Z]),
     ("hist_ablation", _I, [_P, _Z, _P, _U32, _P, _P, _P]),
     ("hist_server_config_init", None, [ctypes.POINTER(ServerConfig)]),

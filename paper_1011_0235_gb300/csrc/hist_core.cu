@@ -52,6 +52,16 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x]) atomicAdd(out + threadIdx.x, cs.res[threadIdx.x]);
 }
 
+// Change detection between two uint64 histograms (256 threads).
+__global__ void __launch_bounds__(HIST_BINS) change_kernel(const unsigned long long* __restrict__ acc,
+                                                          const unsigned long long* __restrict__ win,
+                                                          uint32_t tau_milli, hist_change_result* __restrict__ res) {
+  __shared__ ChangeShared sh;
+  const int t = threadIdx.x;
+  const hist_change_result r = change_eval(acc[t], win[t], tau_milli, sh);
+  if (t == 0) *res = r;
+}
+
 // One warp: the binning pattern of h (or the default pattern if h is null).
 __global__ void __launch_bounds__(32) pattern_kernel(const uint32_t* __restrict__ h, uint32_t budget,
                                                      hist_pattern* __restrict__ out) {
@@ -199,6 +209,16 @@ int degeneracy(const uint32_t* d_hist, uint32_t theta_milli, hist_degeneracy_res
   if (!d_hist || !d_res || theta_milli > 1000) return HIST_EINVAL;
   degeneracy_kernel<uint32_t><<<1, 32, 0, (cudaStream_t)s>>>(d_hist, theta_milli, d_res);
   cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
+int hist_change(const uint64_t* d_acc, const uint64_t* d_win, uint32_t tau_milli, hist_change_result* d_res,
+                hist_cuda_stream s) {
+  if (!d_acc || !d_win || !d_res || tau_milli > 1000) return HIST_EINVAL;
+  change_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(reinterpret_cast<const unsigned long long*>(d_acc),
+                                                      reinterpret_cast<const unsigned long long*>(d_win), tau_milli,
+                                                      d_res);
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 

@@ -536,3 +536,67 @@ static __device__ __noinline__ hist_degeneracy_result block_epilogue(const uint3
 }
 
 }  // namespace histdev
+
+namespace histdev {
+
+// ------------------------------------------------------ change detection --
+
+// Shared scratch of change_eval.
+struct ChangeShared {
+  unsigned __int128 term[HIST_BINS];
+  unsigned long long sa[8], sm[8];
+};
+
+// Total-variation distance between two histograms normalised to sum 1:
+// D = sum_b |a_b SM - m_b SA| over 2 SA SM.  Threads 0..255 pass bin t of
+// each (a, m); all threads of the CTA call (three barriers).  Thread 0 gets
+// the result: the flag (1000 D >= 2 tau SA SM, exact in 128 bits while
+// SA < 2^56 and SM < 2^40), floor(10^6 D / (2 SA SM)), and whether the sums
+// were in that range.  Either histogram empty: distance 0.
+__device__ __forceinline__ hist_change_result change_eval(unsigned long long a, unsigned long long m,
+                                                          uint32_t tau_milli, ChangeShared& sh) {
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t < HIST_BINS) {
+    unsigned long long x = a, y = m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) {
+      sh.sa[w] = x;
+      sh.sm[w] = y;
+    }
+  }
+  __syncthreads();
+  unsigned long long SA = 0, SM = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    SA += sh.sa[i];
+    SM += sh.sm[i];
+  }
+  if (t < HIST_BINS) {
+    const unsigned __int128 p = (unsigned __int128)a * SM, q = (unsigned __int128)m * SA;
+    sh.term[t] = p > q ? p - q : q - p;
+  }
+  __syncthreads();
+  for (int half = HIST_BINS / 2; half > 0; half >>= 1) {
+    if (t < half) sh.term[t] += sh.term[t + half];
+    __syncthreads();
+  }
+  hist_change_result r;
+  r.flag = 0;
+  r.in_range = (SA < (1ull << 56) && SM < (1ull << 40)) ? 1u : 0u;
+  r.dist_ppm = 0;
+  if (t == 0 && SA != 0 && SM != 0) {
+    const unsigned __int128 D = sh.term[0];
+    const unsigned __int128 den = (unsigned __int128)SA * SM * 2u;
+    r.flag = (unsigned __int128)1000u * D >= den * tau_milli ? 1u : 0u;
+    r.dist_ppm = (unsigned long long)((D * 1000000u) / den);
+  } else if (t == 0) {
+    r.flag = tau_milli == 0 ? 1u : 0u;  // distance 0 reaches only a threshold of 0
+  }
+  return r;
+}
+
+}  // namespace histdev

@@ -970,6 +970,18 @@ __global__ void window_copy_kernel(const StreamDev* st, unsigned long long last,
   out[b] = !any ? 0ull : (window > 1 ? st->mw[last & 1][b] : (unsigned long long)st->last_hist[b]);
 }
 
+// Change detection between the stream's totals and its moving-window
+// histogram after chunk `last` (256 threads).
+__global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDev* st, unsigned long long last,
+                                                                  uint32_t window, bool any, uint32_t tau_milli,
+                                                                  hist_change_result* res) {
+  __shared__ ChangeShared sh;
+  const int b = threadIdx.x;
+  const unsigned long long m = !any ? 0ull : (window > 1 ? st->mw[last & 1][b] : (unsigned long long)st->last_hist[b]);
+  const hist_change_result r = change_eval(st->totals[b], m, tau_milli, sh);
+  if (b == 0) *res = r;
+}
+
 __global__ void init_kernel(StreamDev* st, uint32_t budget) {
   __shared__ CtaShared cs;
   __shared__ uint32_t zero[HIST_BINS];
@@ -1295,6 +1307,17 @@ int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s) 
   const bool any = st->chunks_launched > st->resume_chunk;
   window_copy_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
                                                             reinterpret_cast<unsigned long long*>(d_window));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
+int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* d_res, hist_cuda_stream s) {
+  if (!st || !d_res || tau_milli > 1000) return HIST_EINVAL;
+  int rc = do_flush(st, (cudaStream_t)s);
+  if (rc) return rc;
+  const bool any = st->chunks_launched > st->resume_chunk;
+  stream_change_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
+                                                             tau_milli, d_res);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }

@@ -144,6 +144,7 @@ _STRUCTS = {
     "hist_server_stats": "ServerStats",
     "hist_completion": "Completion",
     "hist_request": "Request",
+    "hist_change_result": "ChangeResult",
 }
 
 
