@@ -512,8 +512,9 @@ def run_native(args):
         xdg = gen_workload_device(torch, synth, chunks, synth.SEED_BASE + 3,
                                   lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform())
         pd = [xdg.data_ptr() + c * CHUNK for c in range(chunks)]
-        for name, mode in (("auto", hl.MODE_AUTO), ("plain", hl.MODE_PLAIN), ("adaptive", hl.MODE_ADAPTIVE)):
-            s2 = hl.Stream(budget=8192, mode=mode)
+        for name, mode, window in (("auto", hl.MODE_AUTO, 1), ("plain", hl.MODE_PLAIN, 1),
+                                   ("adaptive", hl.MODE_ADAPTIVE, 1), ("auto_window32", hl.MODE_AUTO, 32)):
+            s2 = hl.Stream(budget=8192, mode=mode, window=window)
 
             def st2(s2=s2):
                 s2.push_many(pd, sizes)
