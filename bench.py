@@ -557,9 +557,14 @@ def run_native(args):
         ksteps = max(3, min(args.steps, 20))
         el_e = time_steps(torch, e2e_step, max(args.warmup, 3), ksteps, barrier)
         el_e = shard.slowest(el_e, device="cuda")
+        # the link's own ceiling: a plain 1 GiB pinned-host -> device copy
+        dx = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        el_c = time_steps(torch, lambda: dx.copy_(hx, non_blocking=True), 1, 3)
+        del dx
         e2e = {"value": round(world * nbytes * ksteps / el_e / 1e9, 2), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 256 * 8, "steps": ksteps,
-               "path": "hist_stream_push_host: pinned host -> 3 staging buffers, copies overlapped with kernels"}
+               "path": "hist_stream_push_host: pinned host -> 3 staging buffers, copies overlapped with kernels",
+               "h2d_copy_gbs": round(nbytes * 3 / el_c / 1e9, 2)}
         st_e.close()
         del hx
     except Exception as exc:  # report, do not hide
