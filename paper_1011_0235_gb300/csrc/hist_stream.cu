@@ -59,7 +59,11 @@ struct StreamDev {
   // last chunks and its completed-chunk count in slot L mod kLaunchRing.
   uint32_t racc[kChunkRing][HIST_BINS];        // by flat chunk number mod kChunkRing
   unsigned long long rdone[kChunkRing];
-  unsigned long long rcnt[kChunkRing];         // auto batches: CTA arrivals, never reset
+  uint32_t rpred[kChunkRing];                  // AUTO flat batches: a chunk's predicted switch
+  uint32_t rflag[kChunkRing];                  // AUTO flat batches: a chunk's switch
+  uint32_t lredo_n[kLaunchRing];               // AUTO flat batches: chunks counted with the wrong kernel
+  uint32_t lk0[kLaunchRing];                   // AUTO flat batches: the stream's switch before the launch
+  uint32_t lredo[kLaunchRing][kMaxBatch];
   // moving window (synced batches, window > 1): the window histogram after
   // chunk c in mw[c mod 2], chunk c's histogram in wring[c mod (W + 1)]
   unsigned long long mw[2][HIST_BINS];
@@ -471,10 +475,26 @@ constexpr size_t kFlatSmemBytes = (size_t)(kTableWords + kLutWords) * 4 + (size_
 static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
 
 // pre[j] = sum over chunks before j of (n + kFlatChunkCost); pre[count] = total.
-__device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre) {
+// The kernel a flat launch runs chunk j with: the mode's, or in AUTO mode
+// the predicted switch of chunk j-1 (chunk 0: the stream's switch, exact, as
+// auto_predict_kernel copied it before the launch; the launch rewrites the
+// stream's switch at its end).
+__device__ __forceinline__ uint32_t flat_kernel_of(const BatchArgs& a, uint32_t j) {
+  if (a.mode == HIST_MODE_PLAIN) return HIST_FLAG_PLAIN;
+  if (a.mode == HIST_MODE_ADAPTIVE) return HIST_FLAG_ADAPTIVE;
+  return j == 0 ? a.st->lk0[a.launch % kLaunchRing] : a.st->rpred[(a.first_chunk + j - 1) % kChunkRing];
+}
+
+// In AUTO mode a chunk predicted to run the plain kernel costs twice its
+// bytes (the plain kernel's rate on wide data is about half the full
+// table's); wt[j] holds chunk j's weight.
+__device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre, uint32_t* wt) {
   __shared__ unsigned long long wsum[kWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const unsigned long long c = t < (int)a.count ? (unsigned long long)a.c[t].n + kFlatChunkCost : 0ull;
+  uint32_t weight = 1;
+  if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = 2;
+  if (t < (int)a.count) wt[t] = weight;
+  const unsigned long long c = t < (int)a.count ? (unsigned long long)a.c[t].n * weight + kFlatChunkCost : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -506,6 +526,11 @@ __device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j,
   classify_pattern(cs.pat, lut, cs);
 }
 
+__device__ __forceinline__ uint32_t flat_check(const BatchArgs& a);
+__device__ __forceinline__ uint32_t flat_last_kernel(const BatchArgs& a) {
+  return a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;  // AUTO: set by the last epilogue
+}
+
 __device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool adaptive, uint32_t* lut,
                                             CtaShared& cs, EpiShared& es, int& path, int& lk) {
   if (!adaptive) {
@@ -535,7 +560,15 @@ __device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pa
 // switch chose the adaptive kernel); the CTA that completes the batch's last
 // epilogue writes the stream state, `last_kernel` being the kernel the last
 // chunk ran.  All threads call.
-constexpr uint32_t kCheckNever = 0, kCheckAlways = 1, kCheckIfAdaptive = 2;
+// kCheckPredicted (AUTO flat batches): chunk j+1 ran the full table when
+// chunk j's predicted switch chose the adaptive kernel; the epilogue also
+// records chunk j's switch, and the last one lists the chunks whose
+// predicted kernel was not the one the switch chose (for a recount) and
+// sets the last kernel itself.
+constexpr uint32_t kCheckNever = 0, kCheckAlways = 1, kCheckPredicted = 3;
+__device__ __forceinline__ uint32_t flat_check(const BatchArgs& a) {
+  return a.mode == HIST_MODE_PLAIN ? kCheckNever : (a.mode == HIST_MODE_ADAPTIVE ? kCheckAlways : kCheckPredicted);
+}
 __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint32_t check, uint32_t last_kernel,
                                            hist_pattern& next, CtaShared& cs, EpiShared& es) {
   StreamDev* st = a.st;
@@ -552,7 +585,10 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
     if (h) atomicAdd(&st->totals[t], (unsigned long long)h);
     if (j + 1 == a.count) st->last_hist[t] = h;
   }
-  if (j + 1 < a.count && (check == kCheckAlways || (check == kCheckIfAdaptive && flag == HIST_FLAG_ADAPTIVE))) {
+  const uint32_t rs = (uint32_t)((a.first_chunk + j) % kChunkRing);
+  if (check == kCheckPredicted && t == 0) st->rflag[rs] = flag;
+  if (j + 1 < a.count &&
+      (check == kCheckAlways || (check == kCheckPredicted && __ldcg(&st->rpred[rs]) == HIST_FLAG_ADAPTIVE))) {
     // chunk j+1 was counted with the layout the rule gives after n pixels
     saturated_pattern(n, a.budget, cs, es);
     if (!same_pattern(next, cs.pat) && t == 0) atomicExch(&st->status, kStatusPattern);
@@ -571,6 +607,19 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
     else copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
     __syncthreads();
     copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
+    if (check == kCheckPredicted && t == 0) {
+      // chunk j's kernel had to be chunk j-1's switch (chunk 0: the stream's)
+      const uint32_t before = st->lk0[ls];
+      uint32_t nr = 0, kern = before;
+      for (uint32_t i = 0; i < a.count; ++i) {
+        const uint32_t prev = (uint32_t)((a.first_chunk + i + kChunkRing - 1) % kChunkRing);
+        kern = i == 0 ? before : __ldcg(&st->rflag[prev]);
+        const uint32_t used = i == 0 ? before : __ldcg(&st->rpred[prev]);
+        if (used != kern) st->lredo[ls][nr++] = i;
+      }
+      st->lredo_n[ls] = nr;
+      last_kernel = kern;
+    }
     if (t == 0) {
       st->flag = __ldcg(&st->lflag[ls]);
       st->last_kernel = last_kernel;
@@ -595,6 +644,7 @@ struct FlatShared {
   int last;
   int released;  // this CTA has waited for the previous launch
   int ring_ok;   // the chunk ring slots of this launch are free
+  uint32_t wt[kMaxBatch];  // cost weight of each chunk (flat_prefix)
 };
 
 __device__ __forceinline__ void flat_mark(const BatchArgs& a, uint32_t j, int phase) {
@@ -641,7 +691,7 @@ __device__ __noinline__ void flat_ring_ready(const BatchArgs& a, FlatShared& fs)
 // chunk's accumulator and byte counter, or, when the table holds the whole
 // chunk, straight into the chunk's epilogue.  The CTA whose bytes complete
 // the chunk runs the epilogue.  All threads call.
-__device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint32_t* table, uint32_t* lut,
+__device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uint32_t* lut,
                                         FlatShared& fs) {
   __syncthreads();
   const int j = fs.cur;
@@ -663,7 +713,7 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint3
     // the whole chunk
     if (t < HIST_BINS) fs.cs.hist[t] = fs.cs.res[t];
     flat_release(fs);
-    flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
     flat_mark(a, j, 7);
     return;
   }
@@ -684,7 +734,7 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint3
     }
     if (t == 0) st->rdone[slot] = 0;
     flat_release(fs);
-    flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
   }
   flat_mark(a, j, 7);
   __syncthreads();
@@ -692,13 +742,13 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, bool adaptive, uint3
 
 // Count bytes [b0, e0) of chunk j (not empty) into the table, reducing the
 // table first if it holds another chunk.  All threads call.
-__device__ __forceinline__ void flat_piece(const BatchArgs& a, bool adaptive, uint32_t j, uint32_t b0, uint32_t e0,
+__device__ __forceinline__ void flat_piece(const BatchArgs& a, uint32_t j, uint32_t b0, uint32_t e0,
                                            uint32_t* table, uint32_t* lut, FlatShared& fs) {
   if (fs.cur != (int)j) {
-    flat_flush(a, adaptive, table, lut, fs);
+    flat_flush(a, table, lut, fs);
     flat_mark(a, j, 0);
     int path, lk;
-    flat_layout(a, j, adaptive, lut, fs.cs, fs.es, path, lk);
+    flat_layout(a, j, flat_kernel_of(a, j) == HIST_FLAG_ADAPTIVE, lut, fs.cs, fs.es, path, lk);
     __syncthreads();
     if (threadIdx.x == 0) {
       fs.cur = (int)j;
@@ -716,9 +766,12 @@ __device__ __forceinline__ void flat_piece(const BatchArgs& a, bool adaptive, ui
   if (threadIdx.x == 0) fs.bytes += e0 - b0;
 }
 
-// Count the cost range [x0, x1) of the batch.  All threads call.
-__device__ void flat_range(const BatchArgs& a, bool adaptive, const unsigned long long* pre, unsigned long long x0,
-                           unsigned long long x1, uint32_t* table, uint32_t* lut, FlatShared& fs) {
+// Count the cost range [x0, x1) of the batch.  Chunk j's byte b sits at
+// cost pre[j] + b wt[j]; a range takes the bytes whose cost position it
+// holds.  All threads call.
+__device__ void flat_range(const BatchArgs& a, const unsigned long long* pre, const uint32_t* wt,
+                           unsigned long long x0, unsigned long long x1, uint32_t* table, uint32_t* lut,
+                           FlatShared& fs) {
   uint32_t j = 0, jh = a.count;
   while (j + 1 < jh) {
     const uint32_t mid = (j + jh) >> 1;
@@ -727,22 +780,23 @@ __device__ void flat_range(const BatchArgs& a, bool adaptive, const unsigned lon
   }
   for (; j < a.count && pre[j] < x1; ++j) {
     const unsigned long long p0 = pre[j];
-    const uint32_t n = a.c[j].n;
+    const uint32_t n = a.c[j].n, w = wt[j];
     if (n == 0) {
       // no bytes: the range holding the chunk's first cost position folds it
       if (p0 >= x0) {
-        flat_flush(a, adaptive, table, lut, fs);
+        flat_flush(a, table, lut, fs);
         flat_mark(a, j, 0);
         if (threadIdx.x < HIST_BINS) fs.cs.hist[threadIdx.x] = 0;
         flat_release(fs);
-        flat_epilogue(a, j, adaptive ? kCheckAlways : kCheckNever, adaptive ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN, fs.next, fs.cs, fs.es);
+        flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
         flat_mark(a, j, 7);
       }
       continue;
     }
-    const unsigned long long b0 = x0 > p0 ? x0 - p0 : 0ull;
-    const unsigned long long e0 = x1 - p0 < (unsigned long long)n ? x1 - p0 : (unsigned long long)n;
-    if (b0 < e0) flat_piece(a, adaptive, j, (uint32_t)b0, (uint32_t)e0, table, lut, fs);
+    const unsigned long long c0 = x0 > p0 ? (x0 - p0 + w - 1) / w : 0ull;
+    const unsigned long long c1 = (x1 - p0 + w - 1) / w;
+    const unsigned long long e0 = c1 < (unsigned long long)n ? c1 : (unsigned long long)n;
+    if (c0 < e0) flat_piece(a, j, (uint32_t)c0, (uint32_t)e0, table, lut, fs);
   }
 }
 
@@ -752,7 +806,6 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
   unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
   __shared__ FlatShared fs;
-  const bool adaptive = a.mode != HIST_MODE_PLAIN;
   const int t = threadIdx.x;
 
   pdl_launch_dependents();
@@ -763,189 +816,119 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
     fs.ring_ok = 0;
   }
   zero_table(table);
-  flat_prefix(a, pre);
+  flat_prefix(a, pre, fs.wt);
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-  if (lo < hi) flat_range(a, adaptive, pre, lo, hi, table, lut, fs);
-  flat_flush(a, adaptive, table, lut, fs);
+  if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, table, lut, fs);
+  flat_flush(a, table, lut, fs);
 }
 
-// AUTO mode at the full budget.  Chunk j's kernel is chunk j-1's switch,
-// and the layout that kernel then uses is fixed -- the full table after a
-// non-empty chunk (R3 saturates at the full budget), while an empty chunk
-// always switches to the plain kernel -- so the one value a chunk depends on
-// is one bit.  One cooperative launch per batch, every CTA resident.  For
-// each chunk j every CTA
-//   1. streams its slice of chunk j+1 into L2 (bulk prefetch);
-//   2. counts its slice of chunk j with a guess of the kernel: the latest
-//      switch it knows (chunk j-2's);
-//   3. waits (bounded) until every CTA has published chunk j-1, reads that
-//      histogram and takes its largest bin against the threshold: chunk j's
-//      switch.  If the guess was wrong it clears the table and counts its
-//      slice again, from L2, with the kernel the switch chose, so chunk j's
-//      counts always come from that kernel;
-//   4. adds its per-bin sums into chunk j's ring accumulator and, after a
-//      fence, one arrival into the chunk's ring counter (never reset: use u
-//      of a slot is complete at (u + 1) x the CTA count).
-// The wait of step 3 overlaps the counting of step 2.  The chunk epilogues
-// (pattern, output, totals, and the stream state at the end) run after the
-// last chunk, chunk j in CTA j mod the CTA count.
+// AUTO mode at the full budget with a window of one chunk.  Chunk j's
+// kernel is chunk j-1's switch, and the layout that kernel then uses is
+// fixed (the full table after a non-empty chunk: R3 saturates at the full
+// budget; an empty chunk always switches to the plain kernel).  Since a
+// chunk's histogram does not depend on the kernel that counts it, the one-bit
+// dependency is broken by prediction:
+//   1. auto_predict_kernel takes each chunk's switch from a 4096-pixel sample
+//      (every pixel of a smaller chunk);
+//   2. batch_flat_kernel counts every chunk, all at once, with the kernel the
+//      predictions give it (chunk 0: the stream's switch, exact); each
+//      chunk's epilogue records its exact switch, and the last one lists the
+//      chunks whose kernel was not the one their predecessor's exact switch
+//      chose;
+//   3. auto_redo_kernel counts each listed chunk again with that kernel and
+//      rewrites its output, so every chunk's counts come from the kernel the
+//      method chooses.  The list is empty unless a sample misjudged a chunk.
 
-// Wait until ring counter `slot` has every CTA's arrival for use `use`, then
-// take chunk n's switch from the ring accumulator.  All threads call;
-// returns false if the wait ran out or another CTA aborted.
-__device__ __noinline__ bool auto_switch(StreamDev* st, uint32_t slot, unsigned long long target, uint32_t n,
-                                         uint32_t theta, uint32_t* wmax, FlatShared& fs) {
+constexpr uint32_t kSampleVecs = HIST_BINS;  // 16-byte vectors per sample: 4096 pixels
+
+__global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ uint32_t h[HIST_BINS];
+  __shared__ uint32_t wm[HIST_BINS / 32];
   const int t = threadIdx.x;
-  if (t == 0) {
-    uint32_t ok = 0;
-    for (uint32_t it = 0;; ++it) {
-      if (ld_acquire(&st->rcnt[slot]) >= target) {
-        ok = 1;
-        break;
-      }
-      if (it >= kPollLimit) {
-        atomicExch(&st->abort, 1u);
-        atomicExch(&st->status, kStatusTimeout);
-        break;
-      }
-      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
-      __nanosleep(32);
+  const ChunkDesc d = a.c[blockIdx.x];
+  h[t] = 0;
+  __syncthreads();
+  const Split sp = split_bytes(d.in, d.n);
+  const uint4* body = reinterpret_cast<const uint4*>(d.in + sp.head);
+  uint32_t sampled;
+  if (sp.nvec >= kSampleVecs) {
+    const uint4 q = ldg_stream(body + (size_t)t * sp.nvec / kSampleVecs);
+    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) atomicAdd(&h[(w4[k >> 2] >> (8 * (k & 3))) & 0xffu], 1u);
+    sampled = 16 * kSampleVecs;
+  } else {
+    for (size_t i = t; i < sp.nvec; i += HIST_BINS) {
+      const uint4 q = ldg_stream(body + i);
+      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 16; ++k) atomicAdd(&h[(w4[k >> 2] >> (8 * (k & 3))) & 0xffu], 1u);
     }
-    fs.last = (int)ok;
+    count_edges_into(d.in, sp, h);
+    sampled = d.n;
   }
   __syncthreads();
-  if (!fs.last) return false;
-  __threadfence();
-  if (t < HIST_BINS) {
-    const uint32_t m = __reduce_max_sync(0xffffffffu, __ldcg(&st->racc[slot][t]));
-    if ((t & 31) == 0) wmax[t >> 5] = m;
-  }
+  const uint32_t m = __reduce_max_sync(0xffffffffu, h[t]);
+  if ((t & 31) == 0) wm[t >> 5] = m;
   __syncthreads();
   if (t == 0) {
     uint32_t mx = 0;
 #pragma unroll
-    for (int i = 0; i < HIST_BINS / 32; ++i) mx = wmax[i] > mx ? wmax[i] : mx;
-    fs.cs.flag = reaches_theta(mx, n, theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    for (int i = 0; i < HIST_BINS / 32; ++i) mx = wm[i] > mx ? wm[i] : mx;
+    a.st->rpred[(a.first_chunk + blockIdx.x) % kChunkRing] =
+        reaches_theta(mx, sampled, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    if (blockIdx.x == 0) a.st->lk0[a.launch % kLaunchRing] = a.st->flag;  // chunk 0's kernel
   }
-  __syncthreads();
-  return true;
 }
 
-__device__ __forceinline__ void auto_layout(uint32_t kern, uint32_t j, StreamDev* st, uint32_t* lut, FlatShared& fs,
-                                            int& path, int& lk) {
-  path = PATH_PLAIN;
-  lk = 0;
-  if (kern != HIST_FLAG_ADAPTIVE) return;
-  if (j > 0) {
-    path = PATH_SHIFT;  // after a non-empty chunk: the full table
-    lk = 5;
-    return;
-  }
-  __syncthreads();
-  copy_pattern(&fs.cs.pat, &st->pattern);  // chunk 0: the stream's pattern
-  __syncthreads();
-  classify_pattern(fs.cs.pat, lut, fs.cs);
-  path = fs.cs.path;
-  lk = fs.cs.lk;
-}
-
-__global__ void __launch_bounds__(kThreads, 2) batch_auto_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;  // slot table of chunk 0, then scratch of the reduction
-  __shared__ FlatShared fs;
-  __shared__ uint32_t wmax[HIST_BINS / 32];
+  uint32_t* lut = smem + kTableWords;  // scratch of the reduction
+  __shared__ CtaShared cs;
+  __shared__ int last;
   StreamDev* st = a.st;
-  const int t = threadIdx.x;
-  const unsigned long long G = gridDim.x;
-  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
-  auto mark = [&](uint32_t j, int phase) {
-    if (a.trace && tslot >= 0 && t == 0 && a.trace_first + j < a.trace_cap)
-      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
-  };
-  auto target = [&](uint32_t j) { return ((a.first_chunk + j) / kChunkRing + 1) * G; };
-  auto slot_of = [&](uint32_t j) { return (uint32_t)((a.first_chunk + j) % kChunkRing); };
-
-  uint32_t known = st->flag;  // the latest switch known: chunk 0's kernel
-  prefetch_slice(a.c[0]);
+  const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+  const uint32_t nr = st->lredo_n[ls];
+  if (nr == 0) return;
   zero_table(table);
   __syncthreads();
-  uint32_t kern = known;  // kernel of the current chunk (uniform)
-  for (uint32_t j = 0; j < a.count; ++j) {
+  for (uint32_t r = 0; r < nr; ++r) {
+    const uint32_t j = st->lredo[ls][r];  // never chunk 0: its kernel is known exactly
     const ChunkDesc d = a.c[j];
-    mark(j, 0);
-    int path, lk;
-    auto_layout(known, j, st, lut, fs, path, lk);
-    mark(j, 2);
-    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
+    const uint32_t slot = (uint32_t)((a.first_chunk + j) % kChunkRing);
+    const uint32_t kern = st->rflag[(a.first_chunk + j - 1) % kChunkRing];
+    // the adaptive kernel after a non-empty chunk: the full table
+    const int path = kern == HIST_FLAG_ADAPTIVE ? PATH_SHIFT : PATH_PLAIN;
+    const int lk = kern == HIST_FLAG_ADAPTIVE ? 5 : 0;
     const Geo g = chunk_geo(d);
     count_geo(path, lk, g, table, lut);
-    mark(j, 3);
-    kern = known;
-    if (j > 0) {
-      // chunk j's kernel: chunk j-1's switch
-      if (!auto_switch(st, slot_of(j - 1), target(j - 1), a.c[j - 1].n, a.theta, wmax, fs)) return;
-      kern = fs.cs.flag;
-      mark(j, 1);
-      if (kern != known) {
-        // wrong guess: count again with the chosen kernel
-        zero_table(table);
-        auto_layout(kern, j, st, lut, fs, path, lk);
-        __syncthreads();
-        count_geo(path, lk, g, table, lut);
-        known = kern;
-      }
-    }
-    // per-bin sums (CTA 0 adds the chunk's unaligned head and tail)
-    flush_table(path, lk, table, fs.cs.pat, lut, fs.cs);
-    mark(j, 4);
+    flush_table(path, lk, table, cs.pat, lut, cs);
+    const Split sp = split_bytes(d.in, d.n);
     if (blockIdx.x == 0) {
-      count_edges(d.in, split_bytes(d.in, d.n), fs.cs);
+      count_edges(d.in, sp, cs);
       __syncthreads();
     }
-    const uint32_t slot = slot_of(j);
-    if (t < HIST_BINS) {
-      if (fs.cs.res[t]) atomicAdd(&st->racc[slot][t], fs.cs.res[t]);
+    zero_table(table);
+    const uint32_t mine = (g.end - g.begin) * 16u + (blockIdx.x == 0 ? (uint32_t)(sp.head + sp.tail) : 0u);
+    if (threadIdx.x < HIST_BINS) {
+      if (cs.res[threadIdx.x]) atomicAdd(&st->racc[slot][threadIdx.x], cs.res[threadIdx.x]);
       __threadfence();
     }
     __syncthreads();
-    mark(j, 5);
-    if (t == 0) red_release_add(&st->rcnt[slot], 1ull);
-    mark(j, 6);
-    zero_table(table);
+    if (threadIdx.x == 0) last = mine && atomicAdd(&st->rdone[slot], (unsigned long long)mine) + mine == d.n;
     __syncthreads();
-    mark(j, 7);
-  }
-  // every CTA's sums of the last chunk; then every CTA has also read every
-  // histogram it needed, so the accumulators are free for the epilogues
-  if (t == 0) {
-    uint32_t ok = 0;
-    for (uint32_t it = 0;; ++it) {
-      if (ld_acquire(&st->rcnt[slot_of(a.count - 1)]) >= target(a.count - 1)) {
-        ok = 1;
-        break;
+    if (last) {
+      __threadfence();
+      if (threadIdx.x < HIST_BINS) {
+        const uint32_t v = __ldcg(&st->racc[slot][threadIdx.x]);
+        if (d.out) d.out[threadIdx.x] = v;
+        st->racc[slot][threadIdx.x] = 0;
       }
-      if (it >= kPollLimit) {
-        atomicExch(&st->abort, 1u);
-        atomicExch(&st->status, kStatusTimeout);
-        break;
-      }
-      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
-      __nanosleep(32);
+      if (threadIdx.x == 0) st->rdone[slot] = 0;
     }
-    fs.last = (int)ok;
-  }
-  __syncthreads();
-  if (!fs.last) return;
-  __threadfence();
-  for (uint32_t j = blockIdx.x; j < a.count; j += (uint32_t)G) {
-    const uint32_t slot = slot_of(j);
-    if (t < HIST_BINS) {
-      fs.cs.hist[t] = __ldcg(&st->racc[slot][t]);
-      st->racc[slot][t] = 0;
-    }
-    flat_epilogue(a, j, kCheckIfAdaptive, kern, fs.next, fs.cs, fs.es);
+    __syncthreads();
   }
 }
 
@@ -1004,7 +987,7 @@ struct hist_stream {
   int grid;
   unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
   bool flat;   // batches run batch_flat_kernel
-  bool autok;  // batches run batch_auto_kernel
+  bool autok;  // AUTO at the full budget, window 1: predict, flat launch, recount
   bool flat_full;  // the stream's pattern is the full table (known on the host)
   unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
   unsigned long long flat_chunks;    // chunks of those launches
@@ -1059,9 +1042,14 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   void* params[] = {a};
   cudaError_t e;
   if (st->autok) {
-    // CTAs wait on one another for every chunk: all must be resident
-    e = cudaLaunchCooperativeKernel((const void*)batch_auto_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
-                                    kSmemBytes, s);
+    // predictions, the flat launch with the predicted kernels, the recount
+    e = cudaLaunchKernel((const void*)auto_predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                           kFlatSmemBytes, s);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel((const void*)auto_redo_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                           kSmemBytes, s);
   } else if (st->flat) {
     // may start while the previous launch on `s` finishes (see batch_flat_kernel)
     cudaLaunchConfig_t lc = {};
@@ -1085,6 +1073,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   if (st->autok) {
     st->flat_launches += 1;
     st->flat_chunks += count;
+    st->flat_full = ns[count - 1] > 0;  // the pattern after a non-empty chunk is the full table
   } else if (st->flat) {
     st->flat_launches += 1;
     st->flat_chunks += count;
@@ -1181,11 +1170,12 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   const bool w1 = cfg->window == 1;
   st->flat = w1 && (cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX));
   st->autok = w1 && cfg->mode == HIST_MODE_AUTO && cfg->budget == HIST_BUDGET_MAX;
-  const void* fn = st->flat ? (const void*)batch_flat_kernel
-                            : (st->autok ? (const void*)batch_auto_kernel : (const void*)batch_synced_kernel);
-  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_auto[kMaxDevices];
-  const size_t smem = st->flat ? kFlatSmemBytes : kSmemBytes;
-  int rc = ensure_smem_attr_bytes(fn, st->flat ? attr_flat : (st->autok ? attr_auto : attr_sync), smem);
+  const bool flat_kernel = st->flat || st->autok;
+  const void* fn = flat_kernel ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
+  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_redo[kMaxDevices];
+  const size_t smem = flat_kernel ? kFlatSmemBytes : kSmemBytes;
+  int rc = ensure_smem_attr_bytes(fn, flat_kernel ? attr_flat : attr_sync, smem);
+  if (rc == HIST_OK && st->autok) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel, attr_redo, kSmemBytes);
   if (rc) {
     free(st);
     return rc;
