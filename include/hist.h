@@ -254,7 +254,10 @@ typedef struct hist_stream_state {
   uint32_t status;              /* 0, or device-side error bits: 4 = a bounded wait
                                    ran out, 8 = a chunk's layout differed from the
                                    pattern rule (never expected) */
-  uint32_t reserved[7];
+  uint32_t recounted;           /* AUTO streams at the full budget: chunks counted a
+                                   second time because their kernel was predicted
+                                   from a sample that misjudged the chunk before */
+  uint32_t reserved[6];
 } hist_stream_state;
 
 /* Flush, copy the state to the host and synchronize `s`. */

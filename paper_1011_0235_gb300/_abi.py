@@ -90,7 +90,8 @@ class StreamState(ctypes.Structure):
         ("flag", ctypes.c_uint32),
         ("last_kernel", ctypes.c_uint32),
         ("status", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 7),
+        ("recounted", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 6),
     ]
 
 

@@ -80,6 +80,7 @@ struct StreamDev {
   uint32_t flag;              // switch computed from the last completed chunk
   uint32_t last_kernel;       // kernel the last completed chunk ran
   uint32_t status;            // 0, or kStatusTimeout
+  uint32_t recounted;         // AUTO flat batches: chunks recounted after a misprediction
   uint32_t abort;             // set by a CTA whose wait ran out
 };
 
@@ -618,6 +619,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
         if (used != kern) st->lredo[ls][nr++] = i;
       }
       st->lredo_n[ls] = nr;
+      st->recounted += nr;
       last_kernel = kern;
     }
     if (t == 0) {
@@ -1333,6 +1335,7 @@ int hist_stream_get_state(hist_stream* st, hist_stream_state* h, hist_cuda_strea
   h->flag = tmp->flag;
   h->last_kernel = tmp->last_kernel;
   h->status = tmp->status;
+  h->recounted = tmp->recounted;
   free(tmp);
   return HIST_OK;
 }

@@ -228,6 +228,55 @@ def test_moving_window_restarts_after_resume():
     st2.close()
 
 
+def _misleading_chunk(n, value, sampled_law_seed):
+    """n pixels equal to `value` except on the 16-byte vectors the switch's
+    sample reads (every (nvec / 256)-th vector), which are uniform: the
+    sample calls the chunk flat while it is almost all one value."""
+    x = np.full(n, value, np.uint8)
+    nvec = n // 16
+    rng = np.random.default_rng(sampled_law_seed)
+    for k in range(256):
+        v = k * nvec // 256
+        x[16 * v:16 * v + 16] = rng.integers(0, 256, 16)
+    return x
+
+
+def test_auto_recounts_chunks_whose_sample_misled():
+    # chunks alternate: a misleading degenerate chunk (exact switch ADAPTIVE,
+    # sample PLAIN), then flat uniform chunks.  Every chunk after a misleading
+    # one was counted with the plain kernel first and must be counted again
+    # with the adaptive kernel; results and state stay exact.
+    n = 1 << 20
+    chunks = []
+    for c in range(12):
+        if c % 3 == 0:
+            chunks.append(_misleading_chunk(n, 40 + c, c))
+        else:
+            chunks.append(synth.host(n, synth.uniform(), SEED + 60, c * n))
+    ref = oracle.StreamOracle(8192)
+    recs = [ref.push(ch) for ch in chunks]
+    bd = dev(np.concatenate(chunks))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
+    st.push_many([bd.data_ptr() + c * n for c in range(len(chunks))], [n] * len(chunks),
+                 [outs[c].data_ptr() for c in range(len(chunks))])
+    s = st.state()
+    _check_state(s, ref, recs[-1])
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    # chunks 1, 4, 7, 10 follow a misleading chunk
+    assert s.recounted == 4
+    # ordinary data: the samples agree with the chunks
+    st2 = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
+    phase = _phase_chunks(16, lambda c: 1 << 20, 4, SEED + 61)
+    bp = dev(np.concatenate(phase))
+    st2.push_many([bp.data_ptr() + c * (1 << 20) for c in range(16)], [1 << 20] * 16)
+    assert st2.state().recounted == 0
+    st.close()
+    st2.close()
+
+
 def test_stream_checkpoint_resume():
     chunks = _phase_chunks(10, lambda c: 200_000 + c, 3, SEED + 6)
     ref = oracle.StreamOracle(960)
