@@ -44,26 +44,34 @@ constexpr uint32_t kSrvMaxSlots = HIST_SERVER_MAX_INFLIGHT;
 constexpr unsigned long long kReqCost = 64ull << 10;
 // cost units per CTA of a batch (the grid is at most every resident CTA)
 constexpr unsigned long long kCtaCost = 64ull << 10;
-// dynamic shared memory: table, slot table, request cost prefix (u64 per request + 1)
-constexpr size_t kSrvSmem = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kSrvMaxBatch + 1) * 8;
+// dynamic shared memory: table, slot table, request cost prefix (u64 per
+// request + 1), each request's stream ctl word
+constexpr size_t kSrvSmem = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kSrvMaxBatch + 1) * 8 +
+                            (size_t)kSrvMaxBatch * 4;
 // request-table capacities of the two kernel variants (the table travels in
 // the launch's parameters: 24 bytes per request)
 constexpr uint32_t kSmallCap = 32;
 
 static_assert(kSrvMaxBatch <= (uint32_t)kThreads, "one prefix lane per request");
 
-// Per-stream state on the device.
+// Per-stream state on the device.  The two patterns sit in two slots: the
+// next request's in pat[cur], the last request's in the other; a request's
+// epilogue writes the new pattern over the older one and flips cur, so no
+// pattern is ever copied.  ctl packs what a batch reads about a stream
+// before counting: the switch (bit 0), whether pat[cur] is a uniform shift
+// (bit 1), cur (bit 2) and the shift's log2 k (bits 8..15).
 struct SrvStream {
   unsigned long long totals[HIST_BINS];
   uint32_t last_hist[HIST_BINS];
-  hist_pattern pattern;       // pattern for the stream's next request
-  hist_pattern last_pattern;  // pattern its last request was given
+  hist_pattern pat[2];
   unsigned long long chunks;
-  uint32_t flag;              // switch from the last request
-  uint32_t last_kernel;       // kernel the last request ran
-  uint32_t shift;             // 1 if `pattern` has one k = 2^lk for all bins at off = b k
-  uint32_t lk;
+  uint32_t ctl;
+  uint32_t last_kernel;  // kernel the last request ran
 };
+
+__host__ __device__ __forceinline__ uint32_t srv_ctl(uint32_t flag, uint32_t shift, uint32_t cur, uint32_t lk) {
+  return (flag & 1u) | ((shift & 1u) << 1) | ((cur & 1u) << 2) | ((lk & 0xffu) << 8);
+}
 
 struct SrvReq {
   const uint8_t* in;
@@ -113,10 +121,13 @@ __device__ __forceinline__ void srv_copy_words(void* dst, const void* src, int w
   for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
 }
 
-// pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total.
-__device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, unsigned long long* pre) {
+// pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total;
+// ctl[r] = request r's stream ctl word (its load overlaps the scan).
+__device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, const SrvStream* streams,
+                                unsigned long long* pre, uint32_t* ctl) {
   __shared__ unsigned long long wsum[kWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint32_t cw = t < (int)count ? __ldcg(&streams[req[t].stream].ctl) : 0u;
   const unsigned long long c = t < (int)count ? (unsigned long long)req[t].n + kReqCost : 0ull;
   unsigned long long x = c;
 #pragma unroll
@@ -128,34 +139,35 @@ __device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, unsigned long
   __syncthreads();
   unsigned long long before = 0;
   for (int i = 0; i < w; ++i) before += wsum[i];
-  if (t < (int)count) pre[t] = before + x - c;
+  if (t < (int)count) {
+    pre[t] = before + x - c;
+    ctl[t] = cw;
+  }
   if (t == (int)count - 1) pre[count] = before + x;
   __syncthreads();
 }
 
 // Request q is complete and cs.hist holds its histogram: write its output
 // and advance its stream's state.  All threads of the CTA call.
-__device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, CtaShared& cs, EpiShared& es) {
+__device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, uint32_t ctl, CtaShared& cs,
+                                          EpiShared& es) {
   SrvStream* st = a.streams + q.stream;
-  const uint32_t kernel = srv_kernel_for(a.mode, st->flag);
-  __syncthreads();  // cs.hist is written; every thread has read the old flag
+  const uint32_t kernel = srv_kernel_for(a.mode, ctl & 1u), cur = (ctl >> 2) & 1u;
+  __syncthreads();  // cs.hist is written
   const hist_degeneracy_result d = block_epilogue(cs.hist, q.n, a.budget, a.theta, cs.pat, es);
   __syncthreads();
   if (threadIdx.x < HIST_BINS) {
     const uint32_t h = cs.hist[threadIdx.x];
     if (q.out) q.out[threadIdx.x] = h;
-    st->totals[threadIdx.x] += h;
+    if (h) atomicAdd(&st->totals[threadIdx.x], (unsigned long long)h);
     st->last_hist[threadIdx.x] = h;
   }
-  srv_copy_words(&st->last_pattern, &st->pattern, (int)(sizeof(hist_pattern) / 4));
-  __syncthreads();
-  srv_copy_words(&st->pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
+  // the new pattern replaces the older of the two
+  srv_copy_words(&st->pat[cur ^ 1u], &cs.pat, (int)(sizeof(hist_pattern) / 4));
   const bool shift = srv_is_shift(cs.pat);
   if (threadIdx.x == 0) {
-    st->shift = shift ? 1u : 0u;
-    st->lk = shift ? cs.pat.log2k[0] : 0u;
+    st->ctl = srv_ctl(d.flag, shift ? 1u : 0u, cur ^ 1u, shift ? cs.pat.log2k[0] : 0u);
     st->last_kernel = kernel;
-    st->flag = d.flag;
     st->chunks += 1;
   }
   __syncthreads();
@@ -163,9 +175,9 @@ __device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, C
 
 // The slot table of a stream's pattern that is not a uniform shift (all
 // threads call).
-__device__ __noinline__ void srv_layout_general(const SrvStream* st, uint32_t* lut, CtaShared& cs) {
+__device__ __noinline__ void srv_layout_general(const SrvStream* st, uint32_t cur, uint32_t* lut, CtaShared& cs) {
   __syncthreads();
-  srv_copy_words(&cs.pat, &st->pattern, (int)(sizeof(hist_pattern) / 4));
+  srv_copy_words(&cs.pat, &st->pat[cur], (int)(sizeof(hist_pattern) / 4));
   __syncthreads();
   classify_pattern(cs.pat, lut, cs);
 }
@@ -176,13 +188,14 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
   unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
+  uint32_t* ctl = reinterpret_cast<uint32_t*>(pre + kSrvMaxBatch + 1);
   __shared__ CtaShared cs;
   __shared__ EpiShared es;
   __shared__ int last;
   const SrvCommon& a = args.c;
 
   zero_table(table);
-  srv_cost_prefix(args.req, a.count, pre);
+  srv_cost_prefix(args.req, a.count, a.streams, pre, ctl);
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x;
   const unsigned long long hi = W * (blockIdx.x + 1) / gridDim.x;
@@ -201,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
       // no bytes: the CTA holding the request's first cost position folds it
       if (p0 >= lo) {
         if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
-        srv_epilogue(a, q, cs, es);
+        srv_epilogue(a, q, ctl[r], cs, es);
       }
       continue;
     }
@@ -209,14 +222,14 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     const unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
     const unsigned long long e0 = hi - p0 < (unsigned long long)q.n ? hi - p0 : (unsigned long long)q.n;
     if (b0 >= e0) continue;
-    const SrvStream* st = a.streams + q.stream;
+    const uint32_t c = ctl[r];
     int path = PATH_PLAIN, lk = 0;
-    if (srv_kernel_for(a.mode, st->flag) == HIST_FLAG_ADAPTIVE) {
-      if (st->shift) {
+    if (srv_kernel_for(a.mode, c & 1u) == HIST_FLAG_ADAPTIVE) {
+      if ((c >> 1) & 1u) {
         path = PATH_SHIFT;
-        lk = (int)st->lk;
+        lk = (int)((c >> 8) & 0xffu);
       } else {
-        srv_layout_general(st, lut, cs);
+        srv_layout_general(a.streams + q.stream, (c >> 2) & 1u, lut, cs);
         path = cs.path;
         lk = cs.lk;
       }
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     if (b0 == 0 && e0 == q.n) {
       // the whole request
       if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = cs.res[threadIdx.x];
-      srv_epilogue(a, q, cs, es);
+      srv_epilogue(a, q, ctl[r], cs, es);
       continue;
     }
     if (threadIdx.x < HIST_BINS) {
@@ -251,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
         a.slot->acc[r][threadIdx.x] = 0;
       }
       if (threadIdx.x == 0) a.slot->done[r] = 0;
-      srv_epilogue(a, q, cs, es);
+      srv_epilogue(a, q, ctl[r], cs, es);
     }
   }
 }
@@ -268,12 +281,10 @@ __global__ void server_init_kernel(SrvStream* s, uint32_t streams, uint32_t budg
   const bool shift = srv_is_shift(cs.pat);
   for (uint32_t i = 0; i < streams; ++i) {
     SrvStream* st = s + i;
-    srv_copy_words(&st->pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
-    srv_copy_words(&st->last_pattern, &cs.pat, (int)(sizeof(hist_pattern) / 4));
+    srv_copy_words(&st->pat[0], &cs.pat, (int)(sizeof(hist_pattern) / 4));
+    srv_copy_words(&st->pat[1], &cs.pat, (int)(sizeof(hist_pattern) / 4));
     if (threadIdx.x == 0) {
-      st->shift = shift ? 1u : 0u;
-      st->lk = shift ? cs.pat.log2k[0] : 0u;
-      st->flag = HIST_FLAG_PLAIN;
+      st->ctl = srv_ctl(HIST_FLAG_PLAIN, shift ? 1u : 0u, 0u, shift ? cs.pat.log2k[0] : 0u);
       st->last_kernel = HIST_FLAG_PLAIN;
     }
   }
@@ -589,10 +600,11 @@ int hist_server_stream_state(hist_server* s, uint32_t stream, hist_stream_state*
   memset(h, 0, sizeof(*h));
   memcpy(h->totals, tmp.totals, sizeof(h->totals));
   memcpy(h->last_hist, tmp.last_hist, sizeof(h->last_hist));
-  h->pattern = tmp.pattern;
-  h->last_pattern = tmp.last_pattern;
+  const uint32_t cur = (tmp.ctl >> 2) & 1u;
+  h->pattern = tmp.pat[cur];
+  h->last_pattern = tmp.pat[cur ^ 1u];
   h->chunks = tmp.chunks;
-  h->flag = tmp.flag;
+  h->flag = tmp.ctl & 1u;
   h->last_kernel = tmp.last_kernel;
   return HIST_OK;
 }
