@@ -63,6 +63,15 @@ struct StreamDev {
   uint32_t rflag[kChunkRing];                  // AUTO flat batches: a chunk's switch
   uint32_t lredo_n[kLaunchRing];               // AUTO flat batches: chunks counted with the wrong kernel
   uint32_t lk0[kLaunchRing];                   // AUTO flat batches: the stream's switch before the launch
+  // flat batches with a window of more than one chunk: every chunk's
+  // histogram (by chunk number mod kChunkRing: a window of up to 256 chunks
+  // plus a batch of 128 fit), its sample histogram and sample size (AUTO),
+  // and the window histogram after the last chunk of the last launch
+  uint32_t whist[kChunkRing][HIST_BINS];
+  uint32_t wsamp[kChunkRing][HIST_BINS];
+  uint32_t wsn[kChunkRing];                    // pixels in chunk g's sample
+  uint32_t wn[kChunkRing];                     // chunk g's size
+  unsigned long long wmw[HIST_BINS];
   uint32_t lredo[kLaunchRing][kMaxBatch];
   // moving window (synced batches, window > 1): the window histogram after
   // chunk c in mw[c mod 2], chunk c's histogram in wring[c mod (W + 1)]
@@ -588,6 +597,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
   }
   const uint32_t rs = (uint32_t)((a.first_chunk + j) % kChunkRing);
   if (check == kCheckPredicted && t == 0) st->rflag[rs] = flag;
+  if (a.window > 1 && t < HIST_BINS) st->whist[rs][t] = cs.hist[t];
   if (j + 1 < a.count &&
       (check == kCheckAlways || (check == kCheckPredicted && __ldcg(&st->rpred[rs]) == HIST_FLAG_ADAPTIVE))) {
     // chunk j+1 was counted with the layout the rule gives after n pixels
@@ -608,7 +618,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
     else copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
     __syncthreads();
     copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
-    if (check == kCheckPredicted && t == 0) {
+    if (check == kCheckPredicted && a.window == 1 && t == 0) {
       // chunk j's kernel had to be chunk j-1's switch (chunk 0: the stream's)
       const uint32_t before = st->lk0[ls];
       uint32_t nr = 0, kern = before;
@@ -623,8 +633,10 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
       last_kernel = kern;
     }
     if (t == 0) {
-      st->flag = __ldcg(&st->lflag[ls]);
-      st->last_kernel = last_kernel;
+      if (a.window == 1) {  // with a window the window kernel sets both
+        st->flag = __ldcg(&st->lflag[ls]);
+        st->last_kernel = last_kernel;
+      }
       st->chunks += a.count;
       st->lchunks[ls] = 0;
       __threadfence();
@@ -877,6 +889,15 @@ __global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_co
     sampled = d.n;
   }
   __syncthreads();
+  if (a.window > 1) {
+    // the window's prediction needs every sample (window_predict_kernel)
+    const uint32_t slot = (uint32_t)((a.first_chunk + blockIdx.x) % kChunkRing);
+    a.st->wsamp[slot][t] = h[t];
+    if (t == 0) {
+      a.st->wsn[slot] = sampled;
+      a.st->wn[slot] = d.n;
+    }
+  }
   const uint32_t m = __reduce_max_sync(0xffffffffu, h[t]);
   if ((t & 31) == 0) wm[t >> 5] = m;
   __syncthreads();
@@ -890,11 +911,151 @@ __global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_co
   }
 }
 
+// A window of W > 1 chunks on the flat path.  The window histogram after
+// chunk g is the one after chunk g-1 plus chunk g minus chunk g-W, so one
+// CTA runs through the batch's chunks in order, bin b in thread b; per chunk
+// each warp reduces its 32 bins' maximum and sum without a barrier, and the
+// switches come after the loop.  Chunks are numbered from the stream's first
+// flat chunk (a resumed stream restarts at 0), and a chunk before number 0
+// counts as empty.
+
+// Predicted window switches (AUTO): the same running sum over the chunks'
+// samples, each scaled by its chunk's bytes over its sample's pixels, in
+// FP32 (a prediction: FP64 is slow on this part, and a wrong guess costs a
+// recount, never a wrong result).  The loads of eight chunks are issued
+// before any is added.
+__device__ __forceinline__ float window_est(const StreamDev* st, unsigned long long g, int b) {
+  const uint32_t slot = (uint32_t)(g % kChunkRing);
+  const uint32_t sn = __ldcg(&st->wsn[slot]);
+  return sn ? (float)__ldcg(&st->wsamp[slot][b]) * ((float)__ldcg(&st->wn[slot]) / (float)sn) : 0.0f;
+}
+
+__global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ float smax[kMaxBatch][HIST_BINS / 32], ssum[kMaxBatch][HIST_BINS / 32];
+  const StreamDev* st = a.st;
+  const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  const unsigned long long W = a.window, g0 = a.first_chunk;
+  // the window before the batch: chunks g0-W+1 .. g0-1
+  float v = 0.0f;
+  const unsigned long long first = g0 >= W - 1 ? g0 - (W - 1) : 0ull;
+  for (unsigned long long g = first; g < g0; g += 8) {
+    float e[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e[k] = g + k < g0 ? window_est(st, g + k, b) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += e[k];
+  }
+  for (uint32_t j0 = 0; j0 < a.count; j0 += 8) {
+    float add[8], sub[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned long long g = g0 + j0 + k;
+      add[k] = j0 + k < a.count ? window_est(st, g, b) : 0.0f;
+      sub[k] = j0 + k < a.count && g >= W ? window_est(st, g - W, b) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (j0 + k >= a.count) break;
+      v = fmaxf(v + add[k] - sub[k], 0.0f);
+      float m = v, sm = v;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      }
+      if (lane == 0) {
+        smax[j0 + k][w] = m;
+        ssum[j0 + k][w] = sm;
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = b; j < a.count; j += HIST_BINS) {
+    float m = 0.0f, sm = 0.0f;
+    for (int i = 0; i < HIST_BINS / 32; ++i) {
+      m = fmaxf(m, smax[j][i]);
+      sm += ssum[j][i];
+    }
+    a.st->rpred[(g0 + j) % kChunkRing] =
+        (sm > 0.0f && m * 1000.0f >= sm * (float)a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  }
+}
+
+// Exact window switches after the flat launch; the stream's switch and last
+// kernel; in AUTO mode the list of chunks whose predicted kernel was not the
+// one their predecessor's window switch chose.
+__global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ unsigned long long smax[kMaxBatch][HIST_BINS / 32], ssum[kMaxBatch][HIST_BINS / 32];
+  StreamDev* st = a.st;
+  const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  const unsigned long long W = a.window, g0 = a.first_chunk;
+  unsigned long long v = g0 > 0 ? __ldcg(&st->wmw[b]) : 0ull;
+  for (uint32_t j0 = 0; j0 < a.count; j0 += 8) {
+    // the loads of eight chunks before any is added
+    uint32_t add[8], sub[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned long long g = g0 + j0 + k;
+      add[k] = j0 + k < a.count ? __ldcg(&st->whist[g % kChunkRing][b]) : 0u;
+      sub[k] = j0 + k < a.count && g >= W ? __ldcg(&st->whist[(g - W) % kChunkRing][b]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (j0 + k >= a.count) break;
+      v += add[k];
+      v -= sub[k];
+      unsigned long long m = v, sm = v;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        m = m2 > m ? m2 : m;
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      }
+      if (lane == 0) {
+        smax[j0 + k][w] = m;
+        ssum[j0 + k][w] = sm;
+      }
+    }
+  }
+  st->wmw[b] = v;
+  __syncthreads();
+  for (uint32_t j = b; j < a.count; j += HIST_BINS) {
+    unsigned long long m = 0, sm = 0;
+    for (int i = 0; i < HIST_BINS / 32; ++i) {
+      m = smax[j][i] > m ? smax[j][i] : m;
+      sm += ssum[j][i];
+    }
+    st->rflag[(g0 + j) % kChunkRing] = reaches_theta(m, sm, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  }
+  __threadfence();
+  __syncthreads();
+  if (b == 0) {
+    const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+    uint32_t kern = a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    if (a.mode == HIST_MODE_AUTO) {
+      // chunk j's kernel had to be chunk j-1's window switch (chunk 0: the stream's)
+      const uint32_t before = st->lk0[ls];
+      uint32_t nr = 0;
+      for (uint32_t i = 0; i < a.count; ++i) {
+        const uint32_t prev = (uint32_t)((g0 + i + kChunkRing - 1) % kChunkRing);
+        kern = i == 0 ? before : st->rflag[prev];
+        const uint32_t used = i == 0 ? before : st->rpred[prev];
+        if (used != kern) st->lredo[ls][nr++] = i;
+      }
+      st->lredo_n[ls] = nr;
+      st->recounted += nr;
+    }
+    st->flag = st->rflag[(g0 + a.count - 1) % kChunkRing];
+    st->last_kernel = kern;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;  // scratch of the reduction
+  uint32_t* lut = smem + kTableWords;  // slot table of a default-pattern layout, then scratch of the reduction
   __shared__ CtaShared cs;
+  __shared__ EpiShared es;
   __shared__ int last;
   StreamDev* st = a.st;
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
@@ -907,9 +1068,17 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
     const ChunkDesc d = a.c[j];
     const uint32_t slot = (uint32_t)((a.first_chunk + j) % kChunkRing);
     const uint32_t kern = st->rflag[(a.first_chunk + j - 1) % kChunkRing];
-    // the adaptive kernel after a non-empty chunk: the full table
-    const int path = kern == HIST_FLAG_ADAPTIVE ? PATH_SHIFT : PATH_PLAIN;
-    const int lk = kern == HIST_FLAG_ADAPTIVE ? 5 : 0;
+    // the adaptive kernel: the full table after a non-empty chunk, the
+    // default pattern after an empty one (with a window of more than one
+    // chunk the switch can choose it there)
+    int path = kern == HIST_FLAG_ADAPTIVE ? PATH_SHIFT : PATH_PLAIN;
+    int lk = kern == HIST_FLAG_ADAPTIVE ? 5 : 0;
+    if (kern == HIST_FLAG_ADAPTIVE && a.c[j - 1].n == 0) {
+      saturated_pattern(0, a.budget, cs, es);
+      classify_pattern(cs.pat, lut, cs);
+      path = cs.path;
+      lk = cs.lk;
+    }
     const Geo g = chunk_geo(d);
     count_geo(path, lk, g, table, lut);
     flush_table(path, lk, table, cs.pat, lut, cs);
@@ -954,21 +1123,31 @@ __global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_
 }
 
 // The moving-window histogram after chunk `last` (none: zeros).
-__global__ void window_copy_kernel(const StreamDev* st, unsigned long long last, uint32_t window, bool any,
+// The moving-window histogram after chunk `last` (none: zeros): the last
+// chunk's histogram for a window of one; else the flat path's window
+// histogram, or the synced path's by the parity of the chunk.
+__device__ __forceinline__ unsigned long long window_bin(const StreamDev* st, unsigned long long last, uint32_t window,
+                                                         bool any, bool flat, int b) {
+  if (!any) return 0ull;
+  if (window == 1) return st->last_hist[b];
+  return flat ? st->wmw[b] : st->mw[last & 1][b];
+}
+
+__global__ void window_copy_kernel(const StreamDev* st, unsigned long long last, uint32_t window, bool any, bool flat,
                                    unsigned long long* out) {
   const int b = threadIdx.x;
   if (b >= HIST_BINS) return;
-  out[b] = !any ? 0ull : (window > 1 ? st->mw[last & 1][b] : (unsigned long long)st->last_hist[b]);
+  out[b] = window_bin(st, last, window, any, flat, b);
 }
 
 // Change detection between the stream's totals and its moving-window
 // histogram after chunk `last` (256 threads).
 __global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDev* st, unsigned long long last,
-                                                                  uint32_t window, bool any, uint32_t tau_milli,
-                                                                  hist_change_result* res) {
+                                                                  uint32_t window, bool any, bool flat,
+                                                                  uint32_t tau_milli, hist_change_result* res) {
   __shared__ ChangeShared sh;
   const int b = threadIdx.x;
-  const unsigned long long m = !any ? 0ull : (window > 1 ? st->mw[last & 1][b] : (unsigned long long)st->last_hist[b]);
+  const unsigned long long m = window_bin(st, last, window, any, flat, b);
   const hist_change_result r = change_eval(st->totals[b], m, tau_milli, sh);
   if (b == 0) *res = r;
 }
@@ -1049,15 +1228,26 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   }
   void* params[] = {a};
   cudaError_t e;
+  const bool windowed = st->cfg.window > 1;
   if (st->autok) {
-    // predictions, the flat launch with the predicted kernels, the recount
+    // predictions, the flat launch with the predicted kernels, (the window,)
+    // the recount
     e = cudaLaunchKernel((const void*)auto_predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
+    if (e == cudaSuccess && windowed)
+      e = cudaLaunchKernel((const void*)window_predict_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
                            kFlatSmemBytes, s);
+    if (e == cudaSuccess && windowed)
+      e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)auto_redo_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
                            kSmemBytes, s);
+  } else if (st->flat && windowed) {
+    e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                         kFlatSmemBytes, s);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
   } else if (st->flat) {
     // may start while the previous launch on `s` finishes (see batch_flat_kernel)
     cudaLaunchConfig_t lc = {};
@@ -1174,10 +1364,12 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
   st->cfg = *cfg;
   st->sms = sm_count();
   // modes whose chunk layouts never depend on the previous chunk's histogram
-  // a window of more than one chunk needs the chunks in order: the synced kernel
-  const bool w1 = cfg->window == 1;
-  st->flat = w1 && (cfg->mode == HIST_MODE_PLAIN || (cfg->mode == HIST_MODE_ADAPTIVE && cfg->budget == HIST_BUDGET_MAX));
-  st->autok = w1 && cfg->mode == HIST_MODE_AUTO && cfg->budget == HIST_BUDGET_MAX;
+  // the flat kernel when no chunk's layout depends on its predecessor's
+  // pattern: the plain mode, or the full budget (AUTO adds predictions and a
+  // recount; a window of more than one chunk adds the window kernels)
+  const bool flatable = cfg->mode == HIST_MODE_PLAIN || cfg->budget == HIST_BUDGET_MAX;
+  st->flat = flatable && cfg->mode != HIST_MODE_AUTO;
+  st->autok = flatable && cfg->mode == HIST_MODE_AUTO;
   const bool flat_kernel = st->flat || st->autok;
   const void* fn = flat_kernel ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
   static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_redo[kMaxDevices];
@@ -1304,6 +1496,7 @@ int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s) 
   if (rc) return rc;
   const bool any = st->chunks_launched > st->resume_chunk;
   window_copy_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
+                                                            st->flat || st->autok,
                                                             reinterpret_cast<unsigned long long*>(d_window));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
@@ -1315,7 +1508,7 @@ int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* 
   if (rc) return rc;
   const bool any = st->chunks_launched > st->resume_chunk;
   stream_change_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
-                                                             tau_milli, d_res);
+                                                             st->flat || st->autok, tau_milli, d_res);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }

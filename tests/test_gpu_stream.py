@@ -241,11 +241,13 @@ def _misleading_chunk(n, value, sampled_law_seed):
     return x
 
 
-def test_auto_recounts_chunks_whose_sample_misled():
+@pytest.mark.parametrize("window", [1, 2])
+def test_auto_recounts_chunks_whose_sample_misled(window):
     # chunks alternate: a misleading degenerate chunk (exact switch ADAPTIVE,
-    # sample PLAIN), then flat uniform chunks.  Every chunk after a misleading
-    # one was counted with the plain kernel first and must be counted again
-    # with the adaptive kernel; results and state stay exact.
+    # sample PLAIN), then flat uniform chunks.  Every chunk whose exact
+    # switch (over its window) chose the adaptive kernel was predicted plain,
+    # counted with the plain kernel first and must be counted again with the
+    # adaptive kernel; results and state stay exact.
     n = 1 << 20
     chunks = []
     for c in range(12):
@@ -253,11 +255,11 @@ def test_auto_recounts_chunks_whose_sample_misled():
             chunks.append(_misleading_chunk(n, 40 + c, c))
         else:
             chunks.append(synth.host(n, synth.uniform(), SEED + 60, c * n))
-    ref = oracle.StreamOracle(8192)
+    ref = oracle.StreamOracle(8192, window=window)
     recs = [ref.push(ch) for ch in chunks]
     bd = dev(np.concatenate(chunks))
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
-    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
+    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO, window=window)
     st.push_many([bd.data_ptr() + c * n for c in range(len(chunks))], [n] * len(chunks),
                  [outs[c].data_ptr() for c in range(len(chunks))])
     s = st.state()
@@ -265,8 +267,12 @@ def test_auto_recounts_chunks_whose_sample_misled():
     got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
     for j, r in enumerate(recs):
         assert np.array_equal(got[j], r.hist), j
-    # chunks 1, 4, 7, 10 follow a misleading chunk
-    assert s.recounted == 4
+    # the samples look flat, so every chunk the switch sent to the adaptive
+    # kernel was recounted (window 1: chunks 1, 4, 7, 10)
+    expect = sum(1 for r in recs[1:] if r.kernel == oracle.FLAG_ADAPTIVE)
+    assert expect >= 4
+    assert s.recounted == expect
+    assert np.array_equal(u64(st.window()), ref.mw)
     # ordinary data: the samples agree with the chunks
     st2 = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
     phase = _phase_chunks(16, lambda c: 1 << 20, 4, SEED + 61)
