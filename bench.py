@@ -289,6 +289,41 @@ def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
     return res
 
 
+def table2_extras(torch, hl, synth, steps=10, n=1 << 30):
+    """Table 2 on this GPU: GB/s of the per-warp kernel and of the adaptive
+    kernel (with the 960-slot pattern the rule derives from the input's own
+    histogram, and with the full 8192-slot table) on the paper's inputs:
+    random (uniform), sequential (x[i] = i mod 256), all 127, all 1 and
+    clamp(round(N(128, 8))) for the missing X-ray data.  Each input is 1 GiB
+    of that law (the paper's 8192 x 8192 slice would sit in the 129 MB L2)."""
+    import oracle
+    out = {"bytes": n, "inputs": ["random", "sequential", "all127", "all1", "xray_normal_sigma8"]}
+    full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
+    x = torch.empty(n, dtype=torch.uint8, device="cuda")
+    cs = torch.cuda.current_stream().cuda_stream
+    o = hl.empty_hist()
+    rows = {"plain_gbs": [], "adaptive_960_gbs": [], "adaptive_8192_gbs": []}
+    for name in out["inputs"]:
+        if name == "sequential":
+            synth.device_ramp(x.data_ptr(), n, 0, cs)
+        else:
+            law = {"random": synth.uniform(), "all127": synth.constant(127), "all1": synth.constant(1),
+                   "xray_normal_sigma8": synth.normal(128, 8)}[name]
+            synth.device_fill(x.data_ptr(), n, law, synth.SEED_BASE + 17, 0, cs)
+        h = hl.as_u32(hl.hist_plain(x, o))
+        p960 = oracle.binning_pattern(h, 960)
+        pd = hl.pattern_from_host(p960.off, p960.log2k, 960, p960.used)
+        torch.cuda.synchronize()
+        for key, fn in (("plain_gbs", lambda: hl.hist_plain(x, o)),
+                        ("adaptive_960_gbs", lambda: hl.hist_adaptive(x, pd, o)),
+                        ("adaptive_8192_gbs", lambda: hl.hist_adaptive(x, full, o))):
+            el = time_steps(torch, fn, 2, steps)
+            rows[key].append(round(n * steps / el / 1e9, 1))
+    out.update(rows)
+    del x
+    return out
+
+
 def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     """The serving workload: Poisson arrivals over 256 streams with 64 MiB
     payload regions each (16 GiB resident), sizes log-uniform in 4 KiB ..
@@ -531,6 +566,7 @@ def run_native(args):
         extras.update(batch_extras(torch, hl, synth, hbm, steps=max(3, min(args.steps, 10))))
         extras["serving"] = serving_extras(torch, np, hl, synth, hbm)
         extras["ablation_table1"] = ablation_extras(torch, hl, synth, hbm)
+        extras["table2"] = table2_extras(torch, hl, synth)
         # one-shot kernels on the whole 1 GiB at once (no stream)
         full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
         o = hl.empty_hist()
