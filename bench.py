@@ -261,12 +261,10 @@ def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
     n bytes (1 GiB) of uniform pixels (the paper's random input) and of N(128, 8), for
     the per-warp kernel, the adaptive kernel with the 960-slot default
     pattern (the paper's table) and with the full 8192-slot table."""
-    import oracle
     from paper_1011_0235_gb300 import _abi
     lib = hl.lib()
     full = ([32 * b for b in range(256)], [5] * 256, 8192, 8192)
-    d960 = oracle.default_pattern(960)
-    pats = {"plain": None, "adaptive_960": hl.pattern_from_host(d960.off, d960.log2k, 960, d960.used),
+    pats = {"plain": None, "adaptive_960": hl.default_pattern(960),
             "adaptive_8192": hl.pattern_from_host(*full)}
     sink = torch.empty(lib.hist_ablation_grid(n) * 256, dtype=torch.int32, device="cuda")
     out = torch.empty(256, dtype=torch.int32, device="cuda")
@@ -296,7 +294,6 @@ def table2_extras(torch, hl, synth, steps=10, n=1 << 30):
     random (uniform), sequential (x[i] = i mod 256), all 127, all 1 and
     clamp(round(N(128, 8))) for the missing X-ray data.  Each input is 1 GiB
     of that law (the paper's 8192 x 8192 slice would sit in the 129 MB L2)."""
-    import oracle
     out = {"bytes": n, "inputs": ["random", "sequential", "all127", "all1", "xray_normal_sigma8"]}
     full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
     x = torch.empty(n, dtype=torch.uint8, device="cuda")
@@ -310,9 +307,8 @@ def table2_extras(torch, hl, synth, steps=10, n=1 << 30):
             law = {"random": synth.uniform(), "all127": synth.constant(127), "all1": synth.constant(1),
                    "xray_normal_sigma8": synth.normal(128, 8)}[name]
             synth.device_fill(x.data_ptr(), n, law, synth.SEED_BASE + 17, 0, cs)
-        h = hl.as_u32(hl.hist_plain(x, o))
-        p960 = oracle.binning_pattern(h, 960)
-        pd = hl.pattern_from_host(p960.off, p960.log2k, 960, p960.used)
+        # the rule's 960-slot pattern from the input's own histogram, on the device
+        pd = hl.binning_pattern(hl.hist_plain(x, o), 960)
         torch.cuda.synchronize()
         for key, fn in (("plain_gbs", lambda: hl.hist_plain(x, o)),
                         ("adaptive_960_gbs", lambda: hl.hist_adaptive(x, pd, o)),
