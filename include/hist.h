@@ -233,13 +233,13 @@ int hist_stream_push_host(hist_stream* st, const uint8_t* h_chunk, size_t n, uin
  * published, end -- for three CTAs (the first, middle and last) into
  * d_trace, a uint64_t array laid out [chunk][3][8] for
  * capacity_chunks chunks counted from this call; later chunks are not
- * recorded.  Streams whose chunk layouts do not depend on the data (plain
- * mode; adaptive mode at HIST_BUDGET_MAX) count each CTA's contiguous range
- * of the chunks placed end to end: a traced CTA records phases 0, 2, 4, 5, 6
- * and 7 (start, layout ready, counted, reduced, published, end) of the
- * chunks its range touches and leaves the other entries unchanged.  d_trace
- * null turns tracing off.  The caller keeps d_trace alive while tracing is
- * on. */
+ * recorded.  Streams that count all of a batch's chunks in one launch (the
+ * plain mode at any budget, every mode at HIST_BUDGET_MAX) give each CTA a
+ * contiguous range of the chunks placed end to end: a traced CTA records
+ * phases 0, 5 and 7 (start of its first piece of the chunk, table reduced,
+ * end) of the chunks its range touches and leaves the other entries
+ * unchanged.  d_trace null turns tracing off.  The caller keeps d_trace
+ * alive while tracing is on. */
 int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chunks);
 
 /* Stream state, for inspection and for checkpoint / resume. */
