@@ -186,9 +186,10 @@ void hist_config_init(hist_config* cfg);
 
 typedef struct hist_stream hist_stream;
 
-/* Allocates the stream's device state (about 56 KiB, cudaMalloc on the
- * current device) and initialises it; synchronous (the device is
- * synchronized), so call it outside stream capture. */
+/* Allocates the stream's device state (about 1.9 MiB, cudaMalloc on the
+ * current device: the state, the scratch rings of the one-launch paths and
+ * the moving window's chunk histograms) and initialises it; synchronous (the
+ * device is synchronized), so call it outside stream capture. */
 int hist_stream_create(const hist_config* cfg, hist_stream** out);
 /* Waits for the stream's work, frees its device state. */
 int hist_stream_destroy(hist_stream* st);
@@ -196,9 +197,11 @@ int hist_stream_destroy(hist_stream* st);
 /* Push one chunk (d_chunk, n pixels, n < 2^32).  d_chunk_out: optional
  * uint32_t[256] that receives the chunk's histogram, or null.  The chunk's
  * results (d_chunk_out, the totals, the next pattern and switch) are
- * completed by the next push on the stream or by hist_stream_flush, both in
- * order on `s`: the epilogue of chunk i runs at the head of chunk i+1's
- * kernel.  The caller keeps d_chunk and d_chunk_out alive until then.
+ * complete once the push's own work on `s` is (streams counted in one launch
+ * per push: the plain mode, every mode at HIST_BUDGET_MAX) or else once the
+ * next push on the stream or hist_stream_flush is, in order on `s`: there
+ * the epilogue of chunk i runs at the head of chunk i+1's kernel.  The
+ * caller keeps d_chunk and d_chunk_out alive until then.
  * Consecutive calls on one stream object must use the same `s`. */
 int hist_stream_push(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t* d_chunk_out,
                      hist_cuda_stream s);
