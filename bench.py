@@ -46,9 +46,9 @@ def parse():
     ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
-    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation"],
+    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation", "table2"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
-                         "(4000 requests) or the 4096-image batch")
+                         "(4000 requests), the 4096-image batch, or 256 MiB cases of Table 1 and Table 2")
     return ap.parse_args()
 
 
@@ -458,6 +458,8 @@ def run_part(args):
         out = serving_extras(torch, np, hl, synth, 6800.0, rates=())
     elif args.profile_part == "ablation":
         out = ablation_extras(torch, hl, synth, 6800.0, steps=1, n=256 << 20)
+    elif args.profile_part == "table2":
+        out = table2_extras(torch, hl, synth, steps=1, n=256 << 20)
     else:
         out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=False)
     print(json.dumps({"profile_part": args.profile_part, "result": out}))
