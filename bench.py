@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
-    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation", "table2"],
+    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation", "table2", "auto"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
-                         "(4000 requests), the 4096-image batch, or 256 MiB cases of Table 1 and Table 2")
+                         "(4000 requests), the 4096-image batch, 256 MiB cases of Table 1 and Table 2, "
+                         "or the degenerate workload through an AUTO stream")
     return ap.parse_args()
 
 
@@ -460,6 +461,15 @@ def run_part(args):
         out = ablation_extras(torch, hl, synth, 6800.0, steps=1, n=256 << 20)
     elif args.profile_part == "table2":
         out = table2_extras(torch, hl, synth, steps=1, n=256 << 20)
+    elif args.profile_part == "auto":
+        # the degenerate workload (95 % = 90, switching to uniform every 8
+        # chunks) through an AUTO stream: 3 pushes of 64 chunks
+        xdg = gen_workload_device(torch, synth, 64, synth.SEED_BASE + 3,
+                                  lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform())
+        st = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
+        ptrs = [xdg.data_ptr() + c * CHUNK for c in range(64)]
+        el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
+        out = {"auto_gbs": round(64 * CHUNK * 2 / el / 1e9, 1), "recounted": st.state().recounted}
     else:
         out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=False)
     print(json.dumps({"profile_part": args.profile_part, "result": out}))
