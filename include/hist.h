@@ -283,8 +283,8 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h_state, his
 #define HIST_BATCH_MAX_IMAGES 4096u
 
 typedef struct hist_batch_tuning {
-  uint32_t ctas_per_sm; /* 1 or 2 (default 1) */
-  uint32_t unroll;      /* 16-byte loads in flight per thread: 2 or 4 (4 needs ctas_per_sm 1; default 4) */
+  uint32_t ctas_per_sm; /* 1 or 2 (default 2) */
+  uint32_t unroll;      /* 16-byte loads in flight per thread: 2 or 4 (4 needs ctas_per_sm 1; default 2) */
   uint32_t small_bytes; /* images below this size use small_log2k (default 0: none) */
   uint32_t small_log2k; /* 0..5 (default 5) */
   uint32_t reserved[4];

@@ -60,7 +60,7 @@ def _oracle(im):
     return oracle.hist_u32(synth.host(im.n, im.thr, synth.SEED_BASE + 4, im.counter0))
 
 
-TUNINGS = [dict(), dict(ctas_per_sm=2, unroll=2), dict(unroll=2), dict(small_bytes=1 << 16, small_log2k=0),
+TUNINGS = [dict(), dict(ctas_per_sm=1, unroll=4), dict(ctas_per_sm=1, unroll=2), dict(small_bytes=1 << 16, small_log2k=0),
            dict(small_bytes=1 << 18, small_log2k=3), dict(ctas_per_sm=2, unroll=2, small_bytes=1 << 20, small_log2k=2)]
 
 
