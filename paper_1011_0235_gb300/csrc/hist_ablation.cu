@@ -46,29 +46,34 @@ __device__ __forceinline__ void ablate_word(uint32_t w, uint32_t base, uint32_t 
 }
 
 template <int STAGE, int PATH, int LK>
+__device__ __forceinline__ void ablate_vec(const uint4& q, uint32_t base, uint32_t lutb, uint32_t table, uint32_t& acc) {
+  ablate_word<STAGE, PATH, LK>(q.x, base, lutb, table, acc);
+  ablate_word<STAGE, PATH, LK>(q.y, base, lutb, table, acc);
+  ablate_word<STAGE, PATH, LK>(q.z, base, lutb, table, acc);
+  ablate_word<STAGE, PATH, LK>(q.w, base, lutb, table, acc);
+}
+
+template <int STAGE, int PATH, int LK>
 __device__ void ablate_range(const uint4* __restrict__ p, size_t begin, size_t end, uint32_t* table,
                              const uint32_t* lut, uint32_t& acc) {
   uint32_t base, lutb, tab;
   thread_bases<PATH, LK>(table, lut, base, lutb, tab);
+  // the loop of count_range (two vectors per group, the next group's loads
+  // issued before the current group is processed)
   size_t i = begin + threadIdx.x;
-  for (; i + kThreads < end; i += 2 * kThreads) {
-    const uint4 a = ldg_stream(p + i), b = ldg_stream(p + i + kThreads);
-    ablate_word<STAGE, PATH, LK>(a.x, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.y, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.z, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.w, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(b.x, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(b.y, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(b.z, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(b.w, base, lutb, tab, acc);
+  if (i + kThreads < end) {
+    uint4 a = ldg_stream(p + i), b = ldg_stream(p + i + kThreads);
+    for (i += 2 * kThreads; i + kThreads < end; i += 2 * kThreads) {
+      const uint4 c = ldg_stream(p + i), d = ldg_stream(p + i + kThreads);
+      ablate_vec<STAGE, PATH, LK>(a, base, lutb, tab, acc);
+      ablate_vec<STAGE, PATH, LK>(b, base, lutb, tab, acc);
+      a = c;
+      b = d;
+    }
+    ablate_vec<STAGE, PATH, LK>(a, base, lutb, tab, acc);
+    ablate_vec<STAGE, PATH, LK>(b, base, lutb, tab, acc);
   }
-  for (; i < end; i += kThreads) {
-    const uint4 a = ldg_stream(p + i);
-    ablate_word<STAGE, PATH, LK>(a.x, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.y, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.z, base, lutb, tab, acc);
-    ablate_word<STAGE, PATH, LK>(a.w, base, lutb, tab, acc);
-  }
+  for (; i < end; i += kThreads) ablate_vec<STAGE, PATH, LK>(ldg_stream(p + i), base, lutb, tab, acc);
 }
 
 template <int STAGE>

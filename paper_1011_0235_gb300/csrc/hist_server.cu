@@ -237,8 +237,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     const uint8_t* base = q.in + b0;
     const uint32_t len = (uint32_t)(e0 - b0);
     const Split sp = split_bytes(base, len);
-    count_range_dispatch<2>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut,
-                            threadIdx.x, kThreads);
+    count_call(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut);
     flush_table(path, lk, table, cs.pat, lut, cs);
     count_edges(base, sp, cs);
     zero_table(table);

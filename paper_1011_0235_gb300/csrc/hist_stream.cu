@@ -754,13 +754,6 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uin
   __syncthreads();
 }
 
-// The counting loop in a function of its own, so that the loop gets the
-// registers and the rest of the kernel spills around the call instead.
-__device__ __noinline__ void flat_count(int path, int lk, const uint4* p, size_t nvec, uint32_t* table,
-                                        const uint32_t* lut) {
-  count_range_dispatch<2>(path, lk, p, 0, nvec, table, lut, threadIdx.x, kThreads);
-}
-
 // Count bytes [b0, e0) of chunk j (not empty) into the table, reducing the
 // table first if it holds another chunk.  All threads call.
 __device__ __forceinline__ void flat_piece(const BatchArgs& a, uint32_t j, uint32_t b0, uint32_t e0,
@@ -781,7 +774,7 @@ __device__ __forceinline__ void flat_piece(const BatchArgs& a, uint32_t j, uint3
   }
   const uint8_t* base = a.c[j].in + b0;
   const Split sp = split_bytes(base, e0 - b0);
-  flat_count(fs.path, fs.lk, reinterpret_cast<const uint4*>(base + sp.head), sp.nvec, table, lut);
+  count_call(fs.path, fs.lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut);
   count_edges_into(base, sp, fs.eh);
   if (threadIdx.x == 0) fs.bytes += e0 - b0;
 }
@@ -1080,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
       lk = cs.lk;
     }
     const Geo g = chunk_geo(d);
-    count_geo(path, lk, g, table, lut);
+    count_call(path, lk, g.body, g.begin, g.end, table, lut);
     flush_table(path, lk, table, cs.pat, lut, cs);
     const Split sp = split_bytes(d.in, d.n);
     if (blockIdx.x == 0) {
