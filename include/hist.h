@@ -393,13 +393,19 @@ int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  *
  * Continuous batching on the host (no device-side waits):
  *   submit  queues a request (FIFO); nothing is enqueued on the GPU.
- *   poll    retires batches whose completion event has fired, writing one
- *           hist_completion per finished request, then admits the next batch
- *           if one of max_inflight batch slots is free: in FIFO order, every
- *           queued request whose stream has no request on the GPU and whose
- *           bytes fit the HBM budget (bytes of all requests on the GPU <=
- *           hbm_budget), up to max_batch requests.  The batch is one kernel
- *           on the slot's own CUDA stream, so batches overlap on the device.
+ *   poll    writes one hist_completion per request that has finished since
+ *           the last poll -- a request's epilogue on the GPU writes its
+ *           completion word in pinned host memory once the request's output
+ *           and its stream's state are written, so a request completes
+ *           without waiting for the rest of its batch -- and releases the
+ *           batch slots whose completion event has fired (with them, their
+ *           streams and their bytes of the budget); then it admits the next
+ *           batch if one of max_inflight batch slots is free: in FIFO order,
+ *           every queued request whose stream has no request on the GPU and
+ *           whose bytes fit the HBM budget (bytes of all requests on the GPU
+ *           <= hbm_budget), up to max_batch requests.  The batch is one
+ *           kernel on the slot's own CUDA stream, so batches overlap on the
+ *           device.
  *   drain   polls until nothing is queued or in flight (bounded by
  *           timeout_ms; HIST_ETIMEDOUT when it runs out).
  * A request's bytes (d_in, n < 2^32, any alignment) must stay valid and
@@ -443,14 +449,15 @@ typedef struct hist_completion {
   uint64_t bytes;
   uint64_t submit_ns; /* submitted (replay: scheduled arrival) */
   uint64_t admit_ns;  /* its batch was launched */
-  uint64_t done_ns;   /* poll saw its batch complete */
+  uint64_t done_ns;   /* poll saw the request complete */
 } hist_completion;
 
 typedef struct hist_server hist_server;
 
 void hist_server_config_init(hist_server_config* c);
 /* Allocates the per-stream state, max_inflight batch slots (about 1.1 MiB of
- * device memory each) and their CUDA streams; synchronizes the device.
+ * device memory each) and their CUDA streams, and 32 KiB of pinned, mapped
+ * host memory for the requests' completion words; synchronizes the device.
  * HIST_EINVAL for a bad config. */
 int hist_server_create(const hist_server_config* cfg, hist_server** out);
 /* Waits for the GPU, then frees everything. */
@@ -459,8 +466,9 @@ int hist_server_destroy(hist_server* srv);
  * alone exceeds the HBM budget (it could never be admitted). */
 int hist_server_submit(hist_server* srv, uint32_t stream, const uint8_t* d_in, size_t n, uint32_t* d_out,
                        uint64_t tag);
-/* Retire finished batches (at most `cap` completions are written; the rest
- * stay for the next poll) and admit one batch.  *n_done = completions written. */
+/* Return finished requests (at most `cap` completions are written; the rest
+ * stay for the next poll), release finished batches and admit one batch.
+ * *n_done = completions written. */
 int hist_server_poll(hist_server* srv, hist_completion* h_done, uint32_t cap, uint32_t* n_done);
 /* Poll until idle; timeout_ms 0 = no limit.  Completions are discarded. */
 int hist_server_drain(hist_server* srv, uint32_t timeout_ms);
@@ -470,7 +478,8 @@ int hist_server_get_stats(hist_server* srv, hist_server_stats* h_stats);
 
 /* Replay a schedule in real time on the calling thread: request i is
  * submitted once arrival_ns (ns after the start of the call, non-decreasing)
- * has passed, and the loop polls until every request has completed;
+ * has passed, and the loop polls until every request has completed and
+ * every batch has retired (the server is idle again when it returns);
  * h_done[i] receives request i's completion (tag = the request's tag).
  * Latency of request i = h_done[i].done_ns - h_done[i].submit_ns.
  * timeout_ms bounds the whole replay (0 = no limit). */

@@ -15,8 +15,12 @@
 // its stream's layout and add it into the request's accumulator; the CTA
 // that completes a request (a done-bytes counter) computes its degeneracy
 // and next pattern and updates the stream's state.  A request counted whole
-// by one CTA skips the accumulator.  Completion is seen by polling the
-// slot's event.
+// by one CTA skips the accumulator.  When a request's epilogue is done it
+// writes the batch's sequence number into the request's completion word in
+// pinned host memory, so the host sees each request complete without waiting
+// for the rest of its batch; the slot itself (its scratch, the streams it
+// holds and its bytes of the budget) is released when the slot's event shows
+// the whole batch done.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -90,10 +94,13 @@ struct SrvSlot {
 struct SrvCommon {
   SrvStream* streams;
   SrvSlot* slot;
+  uint32_t* done;  // the slot's completion words (pinned host memory, mapped): request r's in done[r]
+  uint32_t seq;    // the batch's sequence number, written into done[r] when request r completes
   uint32_t count;
   uint32_t budget;
   uint32_t theta;
   uint32_t mode;
+  uint32_t pad;
 };
 
 template <uint32_t CAP>
@@ -147,10 +154,11 @@ __device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, const SrvStre
   __syncthreads();
 }
 
-// Request q is complete and cs.hist holds its histogram: write its output
-// and advance its stream's state.  All threads of the CTA call.
-__device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, uint32_t ctl, CtaShared& cs,
-                                          EpiShared& es) {
+// Request r (q) is complete and cs.hist holds its histogram: write its
+// output, advance its stream's state, then publish the request's completion
+// word.  All threads of the CTA call.
+__device__ __noinline__ void srv_epilogue(const SrvCommon& a, uint32_t r, const SrvReq& q, uint32_t ctl,
+                                          CtaShared& cs, EpiShared& es) {
   SrvStream* st = a.streams + q.stream;
   const uint32_t kernel = srv_kernel_for(a.mode, ctl & 1u), cur = (ctl >> 2) & 1u;
   __syncthreads();  // cs.hist is written
@@ -170,7 +178,13 @@ __device__ __noinline__ void srv_epilogue(const SrvCommon& a, const SrvReq& q, u
     st->last_kernel = kernel;
     st->chunks += 1;
   }
+  // every write above precedes the completion word (the barrier orders the
+  // CTA's writes before thread 0's system-scope fence and release store)
   __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.done + r), "r"(a.seq) : "memory");
+  }
 }
 
 // The slot table of a stream's pattern that is not a uniform shift (all
@@ -214,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
       // no bytes: the CTA holding the request's first cost position folds it
       if (p0 >= lo) {
         if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = 0;
-        srv_epilogue(a, q, ctl[r], cs, es);
+        srv_epilogue(a, r, q, ctl[r], cs, es);
       }
       continue;
     }
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     if (b0 == 0 && e0 == q.n) {
       // the whole request
       if (threadIdx.x < HIST_BINS) cs.hist[threadIdx.x] = cs.res[threadIdx.x];
-      srv_epilogue(a, q, ctl[r], cs, es);
+      srv_epilogue(a, r, q, ctl[r], cs, es);
       continue;
     }
     if (threadIdx.x < HIST_BINS) {
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
         a.slot->acc[r][threadIdx.x] = 0;
       }
       if (threadIdx.x == 0) a.slot->done[r] = 0;
-      srv_epilogue(a, q, ctl[r], cs, es);
+      srv_epilogue(a, r, q, ctl[r], cs, es);
     }
   }
 }
@@ -310,7 +324,12 @@ struct BatchSlot {
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;
   SrvSlot* d_slot = nullptr;
+  uint32_t* h_done = nullptr;  // completion words of the batch's requests (pinned, mapped)
+  uint32_t* d_done = nullptr;  // the same words as the device sees them
+  uint32_t seq = 0;            // the running batch's sequence number
   std::vector<PendingReq> reqs;
+  std::vector<uint8_t> reported;  // the request's completion has been returned
+  uint32_t n_reported = 0;
   uint64_t admit_ns = 0;
   uint64_t bytes = 0;
 };
@@ -326,6 +345,8 @@ struct hist_server {
   std::list<PendingReq> queue;  // FIFO; admission erases from the middle
   BatchSlot slot[kSrvMaxSlots];
   uint64_t inflight_bytes = 0;
+  uint32_t* h_done = nullptr;  // pinned: kSrvMaxBatch completion words per batch slot
+  uint32_t seq = 0;            // sequence number of the last batch launched
   int sms = 0;
   int max_grid = 0;                          // resident CTAs of the batch kernel
   SrvArgs<kSrvMaxBatch>* args = nullptr;     // parameter block of the next launch
@@ -341,23 +362,29 @@ bool server_config_ok(const hist_server_config* c) {
          c->pattern_budget <= HIST_BUDGET_MAX && c->mode <= HIST_MODE_ADAPTIVE;
 }
 
-// Retire finished batches, writing at most `cap` completions to `out` (out
-// null: discard them); returns how many were written or discarded.
+// Return the completions of finished requests -- those whose completion word
+// holds their batch's sequence number, and every request of a batch whose
+// event shows it done -- writing at most `cap` of them to `out` (out null:
+// discard them), and release the slots of finished batches; returns how
+// many completions were written or discarded.
 uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
   uint32_t n = 0;
   for (uint32_t k = 0; k < s->cfg.max_inflight; ++k) {
     BatchSlot& f = s->slot[k];
     if (!f.busy) continue;
-    if (out && n + f.reqs.size() > cap) continue;  // no room for this batch's records yet
     const cudaError_t q = f.waited ? cudaSuccess : cudaEventQuery(f.done);
-    if (q == cudaErrorNotReady) continue;
-    if (q != cudaSuccess) {
+    if (q != cudaSuccess && q != cudaErrorNotReady) {
       *err = cuda_fail(q);
       return n;
     }
-    const uint64_t t = now_ns();
-    for (const PendingReq& r : f.reqs) {
-      s->stream_busy[r.stream] = 0;
+    const bool all = q == cudaSuccess;
+    const uint32_t count = (uint32_t)f.reqs.size();
+    for (uint32_t i = 0; i < count && f.n_reported < count && (!out || n < cap); ++i) {
+      if (f.reported[i]) continue;
+      // the acquire pairs with the epilogue's release: the request's output
+      // and its stream's state are written before the word is
+      if (!all && __atomic_load_n(f.h_done + i, __ATOMIC_ACQUIRE) != f.seq) continue;
+      const PendingReq& r = f.reqs[i];
       if (out) {
         hist_completion& c = out[n];
         c.tag = r.tag;
@@ -366,12 +393,17 @@ uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
         c.bytes = r.n;
         c.submit_ns = r.submit_ns;
         c.admit_ns = f.admit_ns;
-        c.done_ns = t;
+        c.done_ns = now_ns();
       }
       ++n;
+      f.reported[i] = 1;
+      f.n_reported += 1;
       s->stats.completed += 1;
       s->stats.bytes += r.n;
     }
+    if (!all || f.n_reported < count) continue;
+    // the whole batch is done: its streams and bytes go back to admission
+    for (const PendingReq& r : f.reqs) s->stream_busy[r.stream] = 0;
     s->inflight_bytes -= f.bytes;
     f.reqs.clear();
     f.busy = false;
@@ -414,9 +446,15 @@ int admit(hist_server* s) {
   if (f->reqs.empty()) return HIST_OK;
   const uint32_t count = (uint32_t)f->reqs.size();
   // the launch's parameters: common fields, then the request table
+  if (++s->seq == 0) s->seq = 1;  // completion words start at 0: never a batch's number
+  f->seq = s->seq;
+  f->reported.assign(count, 0);
+  f->n_reported = 0;
   SrvArgs<kSrvMaxBatch>* a = s->args;
   a->c.streams = s->d_streams;
   a->c.slot = f->d_slot;
+  a->c.done = f->d_done;
+  a->c.seq = f->seq;
   a->c.count = count;
   a->c.budget = s->cfg.pattern_budget;
   a->c.theta = s->cfg.theta_milli;
@@ -512,9 +550,14 @@ int hist_server_create(const hist_server_config* cfg, hist_server** out) {
   if (rc == HIST_OK) {
     cudaError_t e = cudaMalloc((void**)&s->d_streams, sizeof(SrvStream) * cfg->streams);
     if (e == cudaSuccess) e = cudaMemset(s->d_streams, 0, sizeof(SrvStream) * cfg->streams);
+    const size_t done_bytes = sizeof(uint32_t) * kSrvMaxBatch * kSrvMaxSlots;
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_done, done_bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) memset(s->h_done, 0, done_bytes);
     for (uint32_t k = 0; e == cudaSuccess && k < cfg->max_inflight; ++k) {
       BatchSlot& f = s->slot[k];
-      e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
+      f.h_done = s->h_done + (size_t)k * kSrvMaxBatch;
+      e = cudaHostGetDevicePointer((void**)&f.d_done, f.h_done, 0);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.cs, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaMalloc((void**)&f.d_slot, sizeof(SrvSlot));
       if (e == cudaSuccess) e = cudaMemset(f.d_slot, 0, sizeof(SrvSlot));
@@ -551,6 +594,7 @@ int hist_server_destroy(hist_server* s) {
     if (f.cs) cudaStreamDestroy(f.cs);
   }
   if (s->d_streams) cudaFree(s->d_streams);
+  if (s->h_done) cudaFreeHost(s->h_done);
   delete s->args;
   delete s;
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
@@ -652,6 +696,13 @@ int hist_server_replay(hist_server* s, const hist_request* reqs, uint32_t count,
       out[idx] = c;
     }
     done += n;
+  }
+  // every request has completed; the last batches retire once their events fire
+  while (!server_idle(s)) {
+    if (timeout_ms && now_ns() - t0 > (uint64_t)timeout_ms * 1000000ull) return HIST_ETIMEDOUT;
+    int err = HIST_OK;
+    retire(s, nullptr, 0, &err);
+    if (err) return err;
   }
   return HIST_OK;
 }

@@ -66,6 +66,24 @@ def test_ragged_sizes(n):
     assert np.array_equal(u32(hl.hist_adaptive(xd, mixed)), ref)
 
 
+# 16-byte vector counts around the counting loop's steps: a thread reads
+# vectors tid, tid + 1024, ... in groups of two, loading its next group before
+# it counts the current one; one CTA takes up to 4096 vectors, so these sizes
+# put one or several CTAs' ranges just below, at and above each step.
+@pytest.mark.parametrize("nvec", [1, 1023, 1024, 1025, 2047, 2048, 2049, 3071, 3072, 3073, 4095, 4096, 4097,
+                                  6143, 6144, 6145, 8191, 8193, 12287, 12289])
+def test_loop_group_boundaries(nvec):
+    for tail in (0, 9):
+        n = 16 * nvec + tail
+        x = synth.host(n, synth.mixture([0.5, 0.5], [40, 200], [3, 30]), SEED + 11, nvec)
+        ref = oracle.hist_u32(x)
+        xd = dev(x)
+        assert np.array_equal(u32(hl.hist_plain(xd)), ref), (nvec, tail)
+        for p in (oracle.binning_pattern(np.ones(256, np.uint32), 8192), oracle.binning_pattern(ref, 1500),
+                  oracle.default_pattern(960)):
+            assert np.array_equal(u32(hl.hist_adaptive(xd, pattern_dev(p))), ref), (nvec, tail, p.used)
+
+
 def test_unaligned_bases():
     base = synth.host((1 << 20) + 64, synth.degenerate(7, 0.5), SEED + 8)
     bd = dev(base)

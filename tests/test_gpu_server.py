@@ -184,6 +184,34 @@ def test_admission_budget_bounds_bytes_in_flight(pool16):
     srv.close()
 
 
+def test_outputs_are_final_when_polled(pool16):
+    """poll returns a request as soon as its epilogue has written its
+    completion word, possibly while the rest of its batch still runs: the
+    output must be final by then.  Each output is read right after its
+    completion is returned, by a copy on another CUDA stream than the
+    batch's, and compared with the oracle."""
+    reqs = workloads.serving_schedule(5000, 300, streams=16, region=4 << 20, size_lo=4 << 10, size_hi=4 << 20,
+                                      seed=SEED + 40)
+    hists, refs, last = _oracle(pool16, reqs)
+    srv = hl.Server(streams=16, max_batch=64, max_inflight=4)
+    out = torch.full((len(reqs), 256), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for i, r in enumerate(reqs):
+        srv.submit_ptr(r.stream, pool16.ptr(r), r.n, out[i].data_ptr(), tag=i)
+    seen = np.zeros((len(reqs), 256), np.uint32)
+    got, t0 = 0, time.monotonic()
+    while got < len(reqs):
+        assert time.monotonic() - t0 < 120, "requests did not complete"
+        for c in srv.poll():
+            seen[c.tag] = out[c.tag].cpu().numpy().view(np.uint32)
+            got += 1
+    assert np.array_equal(seen, hists)
+    assert srv.stats().completed == len(reqs)
+    for s in sorted(refs):
+        _check_state(srv.stream_state(s), refs[s], last[s])
+    srv.close()
+
+
 def test_replay_poisson_schedule(pool16):
     reqs = workloads.serving_schedule(5000, 400, streams=16, region=4 << 20, size_lo=4 << 10, size_hi=4 << 20,
                                       seed=SEED + 30)
@@ -207,6 +235,11 @@ def test_replay_poisson_schedule(pool16):
         assert t == sorted(t)
     for s in sorted(refs):
         _check_state(srv.stream_state(s), refs[s], last[s])
+    # the replay returns with the server idle: another one can start at once
+    st = srv.stats()
+    assert st.queued == 0 and st.inflight_bytes == 0
+    again = srv.replay((_abi.Request * 20)(*R[:20]), timeout_ms=60000)
+    assert [c.tag for c in again] == [1000 + i for i in range(20)]
     srv.close()
 
 
