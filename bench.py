@@ -149,24 +149,30 @@ def measured_peaks():
         return None
 
 
-def csrc_hash():
+# The sources a kernel is compiled from (its translation unit and headers).
+KERNEL_SOURCES = {
+    "batch_flat_kernel": ["paper_1011_0235_gb300/csrc/hist_stream.cu", "paper_1011_0235_gb300/csrc/hist_device.cuh",
+                          "paper_1011_0235_gb300/csrc/hist_internal.h", "include/hist.h"],
+}
+
+
+def sources_hash(kernel):
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1011_0235_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(f.encode())
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources."""
+    the kernel's current sources."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except (OSError, ValueError):
         return None
     k = rec.get(kernel)
-    if not k or k.get("csrc_hash") != csrc_hash():
+    if not k or k.get("sources_hash") != sources_hash(kernel):
         return None
     return k.get("dram_bytes_per_launch")
 
