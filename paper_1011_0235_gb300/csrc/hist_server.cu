@@ -129,13 +129,26 @@ __device__ __forceinline__ void srv_copy_words(void* dst, const void* src, int w
 }
 
 // pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total;
-// ctl[r] = request r's stream ctl word (its load overlaps the scan).
+// ctl[r] = request r's stream ctl word (its load overlaps the scan).  The
+// request table sits in the kernel's parameters, read through the constant
+// cache, which serves a warp's distinct addresses one after another: each
+// warp first copies its requests' sizes and streams into pre[] and ctl[]
+// with a warp-uniform index, and thread r then reads entry r from there.
 __device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, const SrvStream* streams,
                                 unsigned long long* pre, uint32_t* ctl) {
   __shared__ unsigned long long wsum[kWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const uint32_t cw = t < (int)count ? __ldcg(&streams[req[t].stream].ctl) : 0u;
-  const unsigned long long c = t < (int)count ? (unsigned long long)req[t].n + kReqCost : 0ull;
+  for (uint32_t r = (uint32_t)w; r < count; r += kWarps) {
+    const uint32_t n = req[r].n, sid = req[r].stream;
+    if (lane == 0) {
+      pre[r] = n;
+      ctl[r] = sid;
+    }
+  }
+  __syncthreads();
+  // thread t reads entry t and later overwrites only entry t (and pre[count])
+  const uint32_t cw = t < (int)count ? __ldcg(&streams[ctl[t]].ctl) : 0u;
+  const unsigned long long c = t < (int)count ? pre[t] + kReqCost : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {

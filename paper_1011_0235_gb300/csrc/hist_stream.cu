@@ -498,13 +498,23 @@ __device__ __forceinline__ uint32_t flat_kernel_of(const BatchArgs& a, uint32_t 
 // In AUTO mode a chunk predicted to run the plain kernel costs twice its
 // bytes (the plain kernel's rate on wide data is about half the full
 // table's); wt[j] holds chunk j's weight.
+// The chunk table sits in the kernel's parameters, which are read through the
+// constant cache: the distinct addresses of one warp's load are served one
+// after another (4 us per launch when thread t read chunk t's size), so each
+// warp reads its chunks' sizes with a warp-uniform index into shared memory.
 __device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre, uint32_t* wt) {
   __shared__ unsigned long long wsum[kWarps];
+  __shared__ uint32_t sz[kMaxBatch];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (uint32_t j = (uint32_t)w; j < a.count; j += kWarps) {
+    const uint32_t n = a.c[j].n;
+    if (lane == 0) sz[j] = n;
+  }
+  __syncthreads();
   uint32_t weight = 1;
   if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = 2;
   if (t < (int)a.count) wt[t] = weight;
-  const unsigned long long c = t < (int)a.count ? (unsigned long long)a.c[t].n * weight + kFlatChunkCost : 0ull;
+  const unsigned long long c = t < (int)a.count ? (unsigned long long)sz[t] * weight + kFlatChunkCost : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -704,9 +714,10 @@ __device__ __noinline__ void flat_ring_ready(const BatchArgs& a, FlatShared& fs)
 // Reduce the table (the pieces of chunk fs.cur) and publish them: into the
 // chunk's accumulator and byte counter, or, when the table holds the whole
 // chunk, straight into the chunk's epilogue.  The CTA whose bytes complete
-// the chunk runs the epilogue.  All threads call.
-__device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uint32_t* lut,
-                                        FlatShared& fs) {
+// the chunk runs the epilogue.  The CTA's last flush leaves the table as it
+// is.  All threads call.
+__device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uint32_t* lut, FlatShared& fs,
+                                        bool last_flush = false) {
   __syncthreads();
   const int j = fs.cur;
   if (j < 0) return;
@@ -718,7 +729,7 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uin
     fs.cs.res[t] += fs.eh[t];
     fs.eh[t] = 0;
   }
-  zero_table(table);
+  if (!last_flush) zero_table(table);
   const uint32_t n = a.c[j].n, len = fs.bytes;
   __syncthreads();
   flat_mark(a, j, 5);
@@ -833,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
   if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, table, lut, fs);
-  flat_flush(a, table, lut, fs);
+  flat_flush(a, table, lut, fs, true);
 }
 
 // AUTO mode at the full budget with a window of one chunk.  Chunk j's
