@@ -35,6 +35,7 @@ CPU_SAMPLE_SECONDS = 10.0
 STREAM_MAX_BATCH = 128  # chunks per launch of the stream kernels
 SERVE_RATES = (2000, 5000, 10000, 20000, 50000)  # requests per second
 SERVE_SECONDS = 0.5  # of arrivals per rate
+CPU_THREADS_SECONDS = 3.0  # of the threaded oracle count
 
 
 def parse():
@@ -224,6 +225,71 @@ def cpu_oracle_rate(host_chunks, seconds):
         el = time.perf_counter() - t0
         if el >= seconds:
             return done / el / 1e9, done, el
+
+
+def cpu_oracle_threads_rate(buf, seconds, threads):
+    """The oracle's counting loop on `threads` host threads at once: each
+    thread counts its own contiguous slice of `buf` into a private u64[256]
+    (ctypes releases the GIL during the call) and the slices' histograms are
+    summed; repeated until `seconds` have passed.  Returns the rate, the bytes
+    counted, the time and the summed histogram of one pass."""
+    from concurrent.futures import ThreadPoolExecutor
+    import numpy as np
+    import oracle
+
+    lib = oracle.lib()
+    n = buf.size
+    cuts = [n * k // threads for k in range(threads + 1)]
+    hs = [np.zeros(256, np.uint64) for _ in range(threads)]
+
+    def work(k):
+        lib.oracle_hist_u64(buf.ctypes.data + cuts[k], cuts[k + 1] - cuts[k], hs[k].ctypes.data)
+
+    done = 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        while True:
+            list(ex.map(work, range(threads)))
+            total = np.sum(hs, axis=0, dtype=np.uint64)
+            done += n
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                return done / el / 1e9, done, el, total
+
+
+def host_fed_extras(torch, hl, hx, chunks, steps):
+    """Sec. III.B's host-fed stream on this machine (Table 3's question: how
+    much of the transfer the kernels hide): GB/s of the adaptive stream fed
+    from pinned host memory, sequentially (each chunk copied, then counted,
+    on one CUDA stream) and pipelined through 2, 3 and 4 staging buffers
+    (copies on their own stream, overlapped with the kernels)."""
+    res = {}
+    d = torch.empty(CHUNK, dtype=torch.uint8, device="cuda")
+    st = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+
+    def seq_step():
+        for c in range(chunks):
+            d.copy_(hx[c * CHUNK:(c + 1) * CHUNK], non_blocking=True)
+            st.push(d)
+        st.flush()
+
+    el = time_steps(torch, seq_step, 2, steps)
+    res["sequential_gbs"] = round(chunks * CHUNK * steps / el / 1e9, 2)
+    st.close()
+    del d
+    for depth in (2, 3, 4):
+        st = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+        st.attach_staging(CHUNK, depth)
+
+        def pipe_step():
+            for c in range(chunks):
+                st.push_host(hx.data_ptr() + c * CHUNK, CHUNK)
+            st.flush()
+
+        el = time_steps(torch, pipe_step, 2, steps)
+        res["staging_depth_%d_gbs" % depth] = round(chunks * CHUNK * steps / el / 1e9, 2)
+        st.close()
+    return res
 
 
 def batch_extras(torch, hl, synth, hbm, steps, autotune=True):
@@ -621,6 +687,9 @@ def run_native(args):
                "path": "hist_stream_push_host: pinned host -> 3 staging buffers, copies overlapped with kernels",
                "h2d_copy_gbs": round(nbytes * 3 / el_c / 1e9, 2)}
         st_e.close()
+        if world == 1:
+            extras["host_fed"] = host_fed_extras(torch, hl, hx, chunks, 5)
+            extras["host_fed"]["h2d_copy_gbs"] = e2e["h2d_copy_gbs"]
         del hx
     except Exception as exc:  # report, do not hide
         e2e = {"value": None, "unit": UNIT, "error": repr(exc)}
@@ -637,6 +706,17 @@ def run_native(args):
                "sample": "the first %d chunks (%d MiB) of the workload, repeated for %.1f s (%d MiB processed); "
                          "single-threaded C counting loop + degeneracy + binning pattern per chunk"
                          % (sample, sample * 16, secs, done // MiB)}
+        # the oracle's counting loop on every host core (its own slice and
+        # histogram per thread, summed): a second, parallel CPU reference point
+        threads = os.cpu_count() or 1
+        hbuf = np.concatenate(host_chunks)
+        trate, tdone, tsecs, thist = cpu_oracle_threads_rate(hbuf, CPU_THREADS_SECONDS, threads)
+        if not np.array_equal(thist, oracle.hist(hbuf)):
+            raise RuntimeError("threaded oracle count differs from the oracle")
+        extras["cpu_oracle_threads"] = {
+            "value": round(trate, 3), "unit": UNIT, "cores": threads, "kind": "oracle counting loop per thread",
+            "sample": "the first %d chunks (%d MiB), split into %d contiguous slices, repeated for %.1f s (%d MiB)"
+                      % (sample, sample * 16, threads, tsecs, tdone // MiB)}
 
     if rank == 0:
         out = {
