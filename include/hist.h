@@ -191,6 +191,26 @@ typedef struct hist_stream hist_stream;
  * the moving window's chunk histograms) and initialises it; synchronous (the
  * device is synchronized), so call it outside stream capture. */
 int hist_stream_create(const hist_config* cfg, hist_stream** out);
+
+/* A device-memory allocator of the caller's (a framework's caching
+ * allocator, a pool).  alloc returns at least `bytes` bytes of device memory
+ * on the current device, 256-byte aligned, or null when it has none; free
+ * takes back a block with the size it was asked for.  Both are called only
+ * from the host calls of the stream that uses them (create, attach_staging,
+ * destroy), on the caller's thread. */
+typedef struct hist_allocator {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* ctx; /* passed to both */
+} hist_allocator;
+
+/* hist_stream_create with the stream's device memory -- its state and any
+ * staging buffers -- taken from `alloc` instead of cudaMalloc (alloc null:
+ * hist_stream_create).  The allocator must stay valid until the stream is
+ * destroyed.  HIST_ENOMEM when alloc returns null, HIST_EINVAL when it
+ * returns a block that is not 256-byte aligned (the block is given back) or
+ * when only one of alloc and free is set. */
+int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocator* alloc, hist_stream** out);
 /* Waits for the stream's work, frees its device state. */
 int hist_stream_destroy(hist_stream* st);
 

@@ -163,16 +163,49 @@ def change_to_host(res: torch.Tensor) -> tuple[int, int, int]:
     return int(r.dist_ppm), int(r.flag), int(r.in_range)
 
 
+class TorchAllocator:
+    """Device memory for a stream from PyTorch's caching allocator
+    (``torch.cuda.caching_allocator_alloc`` on the current device), passed
+    to the library as a ``hist_allocator``.  Keep it alive as long as the
+    streams that use it (``Stream`` holds a reference)."""
+
+    def __init__(self, device: Optional[int] = None):
+        self.device = torch.cuda.current_device() if device is None else device
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(nbytes, self.device)
+            except Exception:  # out of memory: the library returns HIST_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc = _abi.AllocFn(_alloc)
+        self._free = _abi.FreeFn(_free)
+        self.struct = _abi.Allocator(self._alloc, self._free, None)
+
+
 class Stream:
-    """Chunked stream with device-resident adaptive state (Sec. III.B / III.C)."""
+    """Chunked stream with device-resident adaptive state (Sec. III.B / III.C).
+    ``allocator``: None (cudaMalloc), a ``TorchAllocator``, or "torch" for a
+    new ``TorchAllocator`` on the current device."""
 
     def __init__(self, budget: int = BUDGET_MAX, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO,
-                 grid: int = 0, window: int = 1):
+                 grid: int = 0, window: int = 1, allocator=None):
         cfg = _abi.HistConfig()
         lib().hist_config_init(ctypes.byref(cfg))
         cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid, cfg.window = budget, theta_milli, mode, grid, window
         h = ctypes.c_void_p()
-        _abi.check("hist_stream_create", lib().hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)))
+        if allocator == "torch":
+            allocator = TorchAllocator()
+        self._allocator = allocator
+        if allocator is None:
+            _abi.check("hist_stream_create", lib().hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)))
+        else:
+            _abi.check("hist_stream_create_with_allocator",
+                       lib().hist_stream_create_with_allocator(ctypes.byref(cfg), ctypes.byref(allocator.struct),
+                                                               ctypes.byref(h)))
         self._h = h
         self.budget, self.theta_milli, self.mode, self.window_chunks = budget, theta_milli, mode, window
 

@@ -59,6 +59,15 @@ class DegeneracyResult(ctypes.Structure):
     ]
 
 
+# hist_allocator: void* alloc(size_t bytes, void* ctx); void free(void* ptr, size_t bytes, void* ctx)
+AllocFn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FreeFn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", AllocFn), ("free", FreeFn), ("ctx", ctypes.c_void_p)]
+
+
 class HistConfig(ctypes.Structure):
     _fields_ = [
         ("budget", ctypes.c_uint32),
@@ -168,6 +177,7 @@ SIGNATURES = [
     ("hist_adaptive", _I, [_P, _Z, _P, _P, _P]),
     ("hist_config_init", None, [ctypes.POINTER(HistConfig)]),
     ("hist_stream_create", _I, [ctypes.POINTER(HistConfig), ctypes.POINTER(_P)]),
+    ("hist_stream_create_with_allocator", _I, [ctypes.POINTER(HistConfig), ctypes.POINTER(Allocator), ctypes.POINTER(_P)]),
     ("hist_stream_destroy", _I, [_P]),
     ("hist_stream_push", _I, [_P, _P, _Z, _P, _P]),
     ("hist_stream_push_many", _I, [_P, _U32, _P, _P, _P, _P]),

@@ -1199,9 +1199,34 @@ struct hist_stream {
   cudaEvent_t consumed[kMaxStaging];
   cudaStream_t copy_stream;
   unsigned long long host_pushes;
+  // the caller's device allocator (alloc null: cudaMalloc / cudaFree)
+  hist_allocator alloc;
 };
 
 namespace {
+
+// Device memory of a stream: from the caller's allocator if it gave one.
+int dev_alloc(hist_stream* st, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!st->alloc.alloc) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    return e == cudaSuccess ? HIST_OK : (e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e));
+  }
+  void* q = st->alloc.alloc(bytes, st->alloc.ctx);
+  if (!q) return HIST_ENOMEM;
+  if ((uintptr_t)q % 256u) {
+    st->alloc.free(q, bytes, st->alloc.ctx);
+    return HIST_EINVAL;
+  }
+  *p = q;
+  return HIST_OK;
+}
+
+void dev_free(hist_stream* st, void* p, size_t bytes) {
+  if (!p) return;
+  if (st->alloc.alloc) st->alloc.free(p, bytes, st->alloc.ctx);
+  else cudaFree(p);
+}
 
 int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, const size_t* ns, uint32_t* const* outs,
                  cudaStream_t s) {
@@ -1334,7 +1359,7 @@ int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem, bool 
 
 void release_staging(hist_stream* st) {
   for (uint32_t i = 0; i < kMaxStaging; ++i) {
-    if (st->staging[i]) cudaFree(st->staging[i]);
+    dev_free(st, st->staging[i], st->max_chunk);
     if (st->copied[i]) cudaEventDestroy(st->copied[i]);
     if (st->consumed[i]) cudaEventDestroy(st->consumed[i]);
     st->staging[i] = nullptr;
@@ -1361,11 +1386,17 @@ void hist_config_init(hist_config* c) {
 }
 
 int hist_stream_create(const hist_config* cfg, hist_stream** out) {
+  return hist_stream_create_with_allocator(cfg, nullptr, out);
+}
+
+int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocator* alloc, hist_stream** out) {
   if (!out || !config_ok(cfg)) return HIST_EINVAL;
   *out = nullptr;
+  if (alloc && (!alloc->alloc) != (!alloc->free)) return HIST_EINVAL;
   hist_stream* st = (hist_stream*)calloc(1, sizeof(hist_stream));
   if (!st) return HIST_ENOMEM;
   st->cfg = *cfg;
+  if (alloc) st->alloc = *alloc;
   st->sms = sm_count();
   // modes whose chunk layouts never depend on the previous chunk's histogram
   // the flat kernel when no chunk's layout depends on its predecessor's
@@ -1385,19 +1416,19 @@ int hist_stream_create(const hist_config* cfg, hist_stream** out) {
     return rc;
   }
   st->grid = grid_for(cfg, st->sms, fn, smem, st->flat || st->autok);
-  cudaError_t e = cudaMalloc((void**)&st->d, sizeof(StreamDev));
-  if (e != cudaSuccess) {
+  rc = dev_alloc(st, (void**)&st->d, sizeof(StreamDev));
+  if (rc) {
     free(st);
-    return e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e);
+    return rc;
   }
-  e = cudaMemset(st->d, 0, sizeof(StreamDev));
+  cudaError_t e = cudaMemset(st->d, 0, sizeof(StreamDev));
   if (e == cudaSuccess) {
     init_kernel<<<1, 256>>>(st->d, cfg->budget);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
-    cudaFree(st->d);
+    dev_free(st, st->d, sizeof(StreamDev));
     free(st);
     return cuda_fail(e);
   }
@@ -1409,7 +1440,7 @@ int hist_stream_destroy(hist_stream* st) {
   if (!st) return HIST_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();
   release_staging(st);
-  cudaFree(st->d);
+  dev_free(st, st->d, sizeof(StreamDev));
   free(st);
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
@@ -1433,18 +1464,19 @@ int hist_stream_attach_staging(hist_stream* st, size_t max_chunk, uint32_t depth
   if (!st || max_chunk == 0 || max_chunk >= ((size_t)1 << 32) || depth < 2 || depth > kMaxStaging)
     return HIST_EINVAL;
   if (st->depth) return HIST_ESTATE;
+  st->max_chunk = max_chunk;  // the staging buffers' size, also when they are freed
+  int rc = HIST_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking);
-  for (uint32_t i = 0; e == cudaSuccess && i < depth; ++i) {
-    e = cudaMalloc((void**)&st->staging[i], max_chunk);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->copied[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->consumed[i], cudaEventDisableTiming);
+  for (uint32_t i = 0; e == cudaSuccess && rc == HIST_OK && i < depth; ++i) {
+    rc = dev_alloc(st, (void**)&st->staging[i], max_chunk);
+    if (rc == HIST_OK) e = cudaEventCreateWithFlags(&st->copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess && rc == HIST_OK) e = cudaEventCreateWithFlags(&st->consumed[i], cudaEventDisableTiming);
   }
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || rc != HIST_OK) {
     release_staging(st);
-    return e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e);
+    return rc != HIST_OK ? rc : (e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e));
   }
   st->depth = depth;
-  st->max_chunk = max_chunk;
   st->host_pushes = 0;
   return HIST_OK;
 }

@@ -145,7 +145,24 @@ _STRUCTS = {
     "hist_completion": "Completion",
     "hist_request": "Request",
     "hist_change_result": "ChangeResult",
+    "hist_allocator": "Allocator",
 }
+
+
+def test_allocator_argument_errors(lib):
+    """Host-side checks of hist_stream_create_with_allocator, before any
+    device call: a missing output, or only one of alloc and free."""
+    cfg = _abi.HistConfig()
+    lib.hist_config_init(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    half = _abi.Allocator()
+    half.alloc = _abi.AllocFn(lambda n, ctx: None)
+    assert lib.hist_stream_create_with_allocator(ctypes.byref(cfg), ctypes.byref(half), ctypes.byref(h)) == _abi.EINVAL
+    half2 = _abi.Allocator()
+    half2.free = _abi.FreeFn(lambda p, n, ctx: None)
+    assert lib.hist_stream_create_with_allocator(ctypes.byref(cfg), ctypes.byref(half2), ctypes.byref(h)) == _abi.EINVAL
+    assert lib.hist_stream_create_with_allocator(ctypes.byref(cfg), None, None) == _abi.EINVAL
+    assert h.value is None
 
 
 def test_binding_structs_match_the_header(tmp_path):

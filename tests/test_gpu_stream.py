@@ -283,6 +283,105 @@ def test_auto_recounts_chunks_whose_sample_misled(window):
     st2.close()
 
 
+@pytest.mark.parametrize("depth,budget,mode", [(2, 8192, hl.MODE_ADAPTIVE), (3, 8192, hl.MODE_AUTO),
+                                               (4, 960, hl.MODE_AUTO), (2, 8192, hl.MODE_PLAIN)])
+def test_host_fed_stream(depth, budget, mode):
+    """Chunks pushed from pinned host memory through `depth` staging buffers
+    (copies on the stream's own copy stream, overlapped with the kernels):
+    every chunk's output and the stream's state equal the oracle's.  Chunk
+    sizes are ragged (empty, a few bytes, up to the staging size), and every
+    host chunk is overwritten right after its push once the stream has
+    passed it, as the contract allows."""
+    sizes = [(0, 1, 17, 4 << 20, 123457, 64 * 1024, 4 << 20, 999)[c % 8] + (c if c % 8 != 3 else 0)
+             for c in range(19)]
+    sizes = [min(n, 4 << 20) for n in sizes]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 3, SEED + 9)
+    ref = oracle.StreamOracle(budget, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    st = hl.Stream(budget=budget, mode=mode)
+    with pytest.raises(hl.HistError) as e:
+        st.push_host(0, 0)
+    assert e.value.code == hl._abi.ESTATE
+    st.attach_staging(4 << 20, depth)
+    hbuf = torch.empty(4 << 20, dtype=torch.uint8, pin_memory=True)
+    with pytest.raises(hl.HistError):
+        st.push_host(hbuf.data_ptr(), (4 << 20) + 1)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    cur = torch.cuda.current_stream()
+    for i, ch in enumerate(chunks):
+        hbuf[:ch.size].copy_(torch.from_numpy(ch))
+        st.push_host(hbuf.data_ptr(), ch.size, outs[i].data_ptr())
+        cur.synchronize()  # the stream has passed the push: the host chunk may be reused
+    _check_state(st.state(), ref, recs[-1])
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for i, r in enumerate(recs):
+        assert np.array_equal(got[i], r.hist), i
+    st.close()
+
+
+class _CountingTorchAllocator:
+    """A hist_allocator over PyTorch's caching allocator that records every
+    block it hands out (pointer -> size) and every mismatch on free."""
+
+    def __init__(self):
+        self.live, self.bad = {}, []
+
+        def _alloc(n, ctx):
+            p = torch.cuda.caching_allocator_alloc(n)
+            self.live[p] = n
+            return p
+
+        def _free(p, n, ctx):
+            if self.live.pop(p, None) != n:
+                self.bad.append((p, n))
+            torch.cuda.caching_allocator_delete(p)
+
+        self._a, self._f = hl._abi.AllocFn(_alloc), hl._abi.FreeFn(_free)
+        self.struct = hl._abi.Allocator(self._a, self._f, None)
+
+
+def test_stream_memory_from_the_torch_allocator():
+    """A stream whose state and staging buffers come from PyTorch's caching
+    allocator (hist_stream_create_with_allocator): the blocks are asked for
+    at create and attach_staging, every one is given back with its size at
+    destroy, and results equal the oracle's; an allocator with no memory
+    gives HIST_ENOMEM."""
+    chunks = _phase_chunks(9, lambda c: 300_000 + 7 * c, 2, SEED + 10)
+    ref = oracle.StreamOracle(8192)
+    recs = [ref.push(ch) for ch in chunks]
+    al = _CountingTorchAllocator()
+    st = hl.Stream(budget=8192, allocator=al)
+    assert len(al.live) == 1 and min(al.live.values()) >= 1 << 20  # the ~1.9 MiB state
+    assert all(p % 256 == 0 for p in al.live)
+    st.attach_staging(1 << 20, 2)
+    assert len(al.live) == 3 and sorted(al.live.values())[:2] == [1 << 20, 1 << 20]
+    for ch in chunks[:4]:
+        st.push(dev(ch))
+    hbuf = torch.empty(1 << 20, dtype=torch.uint8, pin_memory=True)
+    for ch in chunks[4:]:
+        hbuf[:ch.size].copy_(torch.from_numpy(ch))
+        st.push_host(hbuf.data_ptr(), ch.size)
+        torch.cuda.current_stream().synchronize()
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
+    assert al.live == {} and al.bad == []
+    # the binding's own TorchAllocator
+    st = hl.Stream(budget=8192, allocator="torch")
+    for ch in chunks:
+        st.push(dev(ch))
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
+
+    empty = hl._abi.Allocator(hl._abi.AllocFn(lambda n, ctx: None), hl._abi.FreeFn(lambda p, n, ctx: None), None)
+
+    class NoMemory:
+        struct = empty
+
+    with pytest.raises(hl.HistError) as e:
+        hl.Stream(allocator=NoMemory())
+    assert e.value.code == hl._abi.ENOMEM
+
+
 def test_stream_checkpoint_resume():
     chunks = _phase_chunks(10, lambda c: 200_000 + c, 3, SEED + 6)
     ref = oracle.StreamOracle(960)
