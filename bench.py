@@ -646,6 +646,10 @@ def run_native(args):
         extras.update(batch_extras(torch, hl, synth, hbm, steps=max(3, min(args.steps, 10))))
         extras["serving"] = serving_extras(torch, np, hl, synth, hbm)
         extras["ablation_table1"] = ablation_extras(torch, hl, synth, hbm)
+        # a read-only kernel's ceiling on this GPU: stage 1 reads every 16-byte
+        # vector once and writes 1 KiB per CTA (the copy peak reads and writes)
+        abl = extras["ablation_table1"]
+        extras["read_only_kernel_gbs"] = max(abl[k][0] for k in abl if k.endswith("_gbs"))
         extras["table2"] = table2_extras(torch, hl, synth)
         # one-shot kernels on the whole 1 GiB at once (no stream)
         full = hl.pattern_from_host([32 * b for b in range(256)], [5] * 256, 8192, 8192)
