@@ -416,8 +416,9 @@ int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  *   poll    writes one hist_completion per request that has finished since
  *           the last poll -- a request's epilogue on the GPU writes its
  *           completion word in pinned host memory once the request's output
- *           and its stream's state are written, so a request completes
- *           without waiting for the rest of its batch -- and releases the
+ *           is written (the stream's state is updated right after, before
+ *           the batch retires), so a request completes without waiting for
+ *           the rest of its batch -- and releases the
  *           batch slots whose completion event has fired (with them, their
  *           streams and their bytes of the budget); then it admits the next
  *           batch if one of max_inflight batch slots is free: in FIFO order,

@@ -15,12 +15,12 @@
 // its stream's layout and add it into the request's accumulator; the CTA
 // that completes a request (a done-bytes counter) computes its degeneracy
 // and next pattern and updates the stream's state.  A request counted whole
-// by one CTA skips the accumulator.  When a request's epilogue is done it
-// writes the batch's sequence number into the request's completion word in
-// pinned host memory, so the host sees each request complete without waiting
-// for the rest of its batch; the slot itself (its scratch, the streams it
-// holds and its bytes of the budget) is released when the slot's event shows
-// the whole batch done.
+// by one CTA skips the accumulator.  Once a request's output is written, its
+// epilogue writes the batch's sequence number into the request's completion
+// word in pinned host memory (and then updates the stream's state), so the
+// host sees each request complete without waiting for the rest of its batch;
+// the slot itself (its scratch, the streams it holds and its bytes of the
+// budget) is released when the slot's event shows the whole batch done.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -168,18 +168,27 @@ __device__ void srv_cost_prefix(const SrvReq* req, uint32_t count, const SrvStre
 }
 
 // Request r (q) is complete and cs.hist holds its histogram: write its
-// output, advance its stream's state, then publish the request's completion
-// word.  All threads of the CTA call.
+// output and publish the request's completion word, then advance its
+// stream's state.  The state can follow the completion: the stream's next
+// request is admitted only once this batch has retired.  All threads of the
+// CTA call.
 __device__ __noinline__ void srv_epilogue(const SrvCommon& a, uint32_t r, const SrvReq& q, uint32_t ctl,
                                           CtaShared& cs, EpiShared& es) {
   SrvStream* st = a.streams + q.stream;
   const uint32_t kernel = srv_kernel_for(a.mode, ctl & 1u), cur = (ctl >> 2) & 1u;
   __syncthreads();  // cs.hist is written
+  if (threadIdx.x < HIST_BINS && q.out) q.out[threadIdx.x] = cs.hist[threadIdx.x];
+  // the output precedes the completion word (the barrier orders the CTA's
+  // writes before thread 0's system-scope fence and release store)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.done + r), "r"(a.seq) : "memory");
+  }
   const hist_degeneracy_result d = block_epilogue(cs.hist, q.n, a.budget, a.theta, cs.pat, es);
   __syncthreads();
   if (threadIdx.x < HIST_BINS) {
     const uint32_t h = cs.hist[threadIdx.x];
-    if (q.out) q.out[threadIdx.x] = h;
     if (h) atomicAdd(&st->totals[threadIdx.x], (unsigned long long)h);
     st->last_hist[threadIdx.x] = h;
   }
@@ -191,13 +200,7 @@ __device__ __noinline__ void srv_epilogue(const SrvCommon& a, uint32_t r, const 
     st->last_kernel = kernel;
     st->chunks += 1;
   }
-  // every write above precedes the completion word (the barrier orders the
-  // CTA's writes before thread 0's system-scope fence and release store)
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence_system();
-    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.done + r), "r"(a.seq) : "memory");
-  }
 }
 
 // The slot table of a stream's pattern that is not a uniform shift (all
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     count_call(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut);
     flush_table(path, lk, table, cs.pat, lut, cs);
     count_edges(base, sp, cs);
-    zero_table(table);
+    if (r + 1 < a.count && pre[r + 1] < hi) zero_table(table);  // the CTA has another piece
     __syncthreads();
     if (b0 == 0 && e0 == q.n) {
       // the whole request
@@ -343,6 +346,7 @@ struct BatchSlot {
   std::vector<PendingReq> reqs;
   std::vector<uint8_t> reported;  // the request's completion has been returned
   uint32_t n_reported = 0;
+  uint32_t polls = 0;  // polls of the running batch
   uint64_t admit_ns = 0;
   uint64_t bytes = 0;
 };
@@ -385,13 +389,18 @@ uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
   for (uint32_t k = 0; k < s->cfg.max_inflight; ++k) {
     BatchSlot& f = s->slot[k];
     if (!f.busy) continue;
-    const cudaError_t q = f.waited ? cudaSuccess : cudaEventQuery(f.done);
+    const uint32_t count = (uint32_t)f.reqs.size();
+    // the event is asked (a driver call) once every request has reported,
+    // and every 32nd poll before that, so that a failed batch is still seen;
+    // the completion words themselves are plain reads of host memory
+    cudaError_t q = cudaErrorNotReady;
+    if (f.waited) q = cudaSuccess;
+    else if (f.n_reported == count || (++f.polls & 31u) == 0) q = cudaEventQuery(f.done);
     if (q != cudaSuccess && q != cudaErrorNotReady) {
       *err = cuda_fail(q);
       return n;
     }
     const bool all = q == cudaSuccess;
-    const uint32_t count = (uint32_t)f.reqs.size();
     for (uint32_t i = 0; i < count && f.n_reported < count && (!out || n < cap); ++i) {
       if (f.reported[i]) continue;
       // the acquire pairs with the epilogue's release: the request's output
@@ -463,6 +472,7 @@ int admit(hist_server* s) {
   f->seq = s->seq;
   f->reported.assign(count, 0);
   f->n_reported = 0;
+  f->polls = 0;
   SrvArgs<kSrvMaxBatch>* a = s->args;
   a->c.streams = s->d_streams;
   a->c.slot = f->d_slot;
