@@ -60,6 +60,7 @@ struct StreamDev {
   uint32_t racc[kChunkRing][HIST_BINS];        // by flat chunk number mod kChunkRing
   unsigned long long rdone[kChunkRing];
   uint32_t rpred[kChunkRing];                  // AUTO flat batches: a chunk's predicted switch
+  hist_pattern ppat[kChunkRing];               // below the full budget: the layout a chunk is counted with
   uint32_t rflag[kChunkRing];                  // AUTO flat batches: a chunk's switch
   uint32_t lredo_n[kLaunchRing];               // AUTO flat batches: chunks counted with the wrong kernel
   uint32_t lk0[kLaunchRing];                   // AUTO flat batches: the stream's switch before the launch
@@ -462,12 +463,15 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 
 // ------------------------------------------------------------ flat batches --
 //
-// For the modes in which a chunk's kernel and layout do not depend on the
-// previous chunk's histogram -- the plain mode (the plain kernel uses no
-// pattern) and the adaptive mode at the full budget (the pattern rule then
-// gives the full table after every non-empty chunk and the default pattern
-// after an empty one) -- the chunks of a batch need not be counted one after
-// the other.  batch_flat_kernel splits the batch's chunks, placed end to end,
+// A chunk's counts do not depend on the kernel or the layout that count it,
+// so the chunks of a batch need not be counted one after the other.  Where
+// the layout does not depend on the previous chunk's histogram -- the plain
+// mode (the plain kernel uses no pattern) and the adaptive mode at the full
+// budget (the pattern rule then gives the full table after every non-empty
+// chunk and the default pattern after an empty one) -- it is known before
+// the launch; elsewhere predict_kernel derives each chunk's kernel and layout
+// from a sample of the previous chunk, and the epilogues record the exact
+// switch and pattern.  batch_flat_kernel splits the batch's chunks, placed end to end,
 // into one contiguous range per CTA by a cost model (a chunk costs its bytes
 // plus kFlatChunkCost), so a CTA counts one or two pieces of chunks and
 // reduces its table only where its range crosses a chunk boundary.  A CTA
@@ -487,7 +491,7 @@ static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
 // pre[j] = sum over chunks before j of (n + kFlatChunkCost); pre[count] = total.
 // The kernel a flat launch runs chunk j with: the mode's, or in AUTO mode
 // the predicted switch of chunk j-1 (chunk 0: the stream's switch, exact, as
-// auto_predict_kernel copied it before the launch; the launch rewrites the
+// predict_kernel copied it before the launch; the launch rewrites the
 // stream's switch at its end).
 __device__ __forceinline__ uint32_t flat_kernel_of(const BatchArgs& a, uint32_t j) {
   if (a.mode == HIST_MODE_PLAIN) return HIST_FLAG_PLAIN;
@@ -533,10 +537,18 @@ __device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre, uint32_
 // Layout of chunk j (uniform over the CTA): the plain tables, the full table,
 // or -- for chunk 0 (the stream's current pattern) and after an empty chunk
 // (the default pattern) -- the pattern in cs.pat with its slot table.
+__device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pattern* src) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
+}
 __device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j, uint32_t* lut, CtaShared& cs,
                                                  EpiShared& es) {
   __syncthreads();
-  if (j == 0) {
+  if (a.budget < HIST_BUDGET_MAX) {
+    // the pattern predict_kernel derived for the chunk (chunk 0: the stream's)
+    copy_pattern_cg(&cs.pat, &a.st->ppat[(a.first_chunk + j) % kChunkRing]);
+  } else if (j == 0) {
     pdl_wait();  // the previous launch writes the stream's pattern
     copy_pattern(&cs.pat, &a.st->pattern);
   } else {
@@ -558,7 +570,7 @@ __device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool
     lk = 0;
     return;
   }
-  if (j > 0 ? a.c[j - 1].n > 0 : a.chunk0_full != 0) {
+  if (a.budget == HIST_BUDGET_MAX && (j > 0 ? a.c[j - 1].n > 0 : a.chunk0_full != 0)) {
     path = PATH_SHIFT;
     lk = 5;
     return;
@@ -568,11 +580,6 @@ __device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool
   lk = cs.lk;
 }
 
-__device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pattern* src) {
-  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
-  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
-}
 
 // Chunk j is complete and cs.hist holds its histogram: its switch, pattern,
 // output and totals; `check` says when chunk j+1 was counted with the full
@@ -608,7 +615,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
   const uint32_t rs = (uint32_t)((a.first_chunk + j) % kChunkRing);
   if (check == kCheckPredicted && t == 0) st->rflag[rs] = flag;
   if (a.window > 1 && t < HIST_BINS) st->whist[rs][t] = cs.hist[t];
-  if (j + 1 < a.count &&
+  if (j + 1 < a.count && a.budget == HIST_BUDGET_MAX &&
       (check == kCheckAlways || (check == kCheckPredicted && __ldcg(&st->rpred[rs]) == HIST_FLAG_ADAPTIVE))) {
     // chunk j+1 was counted with the layout the rule gives after n pixels
     saturated_pattern(n, a.budget, cs, es);
@@ -847,14 +854,14 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   flat_flush(a, table, lut, fs, true);
 }
 
-// AUTO mode at the full budget with a window of one chunk.  Chunk j's
-// kernel is chunk j-1's switch, and the layout that kernel then uses is
-// fixed (the full table after a non-empty chunk: R3 saturates at the full
-// budget; an empty chunk always switches to the plain kernel).  Since a
-// chunk's histogram does not depend on the kernel that counts it, the one-bit
-// dependency is broken by prediction:
-//   1. auto_predict_kernel takes each chunk's switch from a 4096-pixel sample
-//      (every pixel of a smaller chunk);
+// AUTO mode.  Chunk j's kernel is chunk j-1's switch (at the full budget
+// the adaptive kernel's layout is then fixed: the full table after a
+// non-empty chunk, since R3 saturates there; an empty chunk always switches
+// to the plain kernel).  Since a chunk's histogram does not depend on the
+// kernel that counts it, the one-bit dependency is broken by prediction:
+//   1. predict_kernel takes each chunk's switch from a 4096-pixel sample
+//      (every pixel of a smaller chunk), and below the full budget the
+//      layout too;
 //   2. batch_flat_kernel counts every chunk, all at once, with the kernel the
 //      predictions give it (chunk 0: the stream's switch, exact); each
 //      chunk's epilogue records its exact switch, and the last one lists the
@@ -866,9 +873,19 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
 
 constexpr uint32_t kSampleVecs = HIST_BINS;  // 16-byte vectors per sample: 4096 pixels
 
-__global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_constant__ BatchArgs a) {
+// Before a flat launch of an AUTO stream, or of any adaptive stream below the
+// full budget: CTA j samples chunk j (256 evenly spaced 16-byte vectors,
+// 4096 pixels; a smaller chunk whole) and predicts from the sample what the
+// chunk's own histogram gives -- its switch (AUTO) and, below the full
+// budget, the binning pattern the rule derives from it, which becomes the
+// layout chunk j+1 is counted with.  Chunk 0 is counted with the stream's
+// pattern and kernel (exact).  A chunk's counts do not depend on its
+// layout, so a prediction that differs from the exact pattern only costs
+// speed; the epilogues still record the exact patterns and switches.
+__global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ uint32_t h[HIST_BINS];
   __shared__ uint32_t wm[HIST_BINS / 32];
+  __shared__ EpiShared es;
   const int t = threadIdx.x;
   const ChunkDesc d = a.c[blockIdx.x];
   h[t] = 0;
@@ -893,7 +910,7 @@ __global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_co
     sampled = d.n;
   }
   __syncthreads();
-  if (a.window > 1) {
+  if (a.window > 1 && a.mode == HIST_MODE_AUTO) {
     // the window's prediction needs every sample (window_predict_kernel)
     const uint32_t slot = (uint32_t)((a.first_chunk + blockIdx.x) % kChunkRing);
     a.st->wsamp[slot][t] = h[t];
@@ -902,16 +919,28 @@ __global__ void __launch_bounds__(HIST_BINS) auto_predict_kernel(const __grid_co
       a.st->wn[slot] = d.n;
     }
   }
-  const uint32_t m = __reduce_max_sync(0xffffffffu, h[t]);
-  if ((t & 31) == 0) wm[t >> 5] = m;
-  __syncthreads();
-  if (t == 0) {
-    uint32_t mx = 0;
+  if (a.mode == HIST_MODE_AUTO) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, h[t]);
+    if ((t & 31) == 0) wm[t >> 5] = m;
+    __syncthreads();
+    if (t == 0) {
+      uint32_t mx = 0;
 #pragma unroll
-    for (int i = 0; i < HIST_BINS / 32; ++i) mx = wm[i] > mx ? wm[i] : mx;
-    a.st->rpred[(a.first_chunk + blockIdx.x) % kChunkRing] =
-        reaches_theta(mx, sampled, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-    if (blockIdx.x == 0) a.st->lk0[a.launch % kLaunchRing] = a.st->flag;  // chunk 0's kernel
+      for (int i = 0; i < HIST_BINS / 32; ++i) mx = wm[i] > mx ? wm[i] : mx;
+      a.st->rpred[(a.first_chunk + blockIdx.x) % kChunkRing] =
+          reaches_theta(mx, sampled, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+      if (blockIdx.x == 0) a.st->lk0[a.launch % kLaunchRing] = a.st->flag;  // chunk 0's kernel
+    }
+  }
+  if (a.budget < HIST_BUDGET_MAX) {
+    StreamDev* st = a.st;
+    if (blockIdx.x == 0) copy_pattern(&st->ppat[a.first_chunk % kChunkRing], &st->pattern);
+    if (blockIdx.x + 1 < a.count) {
+      // the rule on the sample (proportions: its total is the sampled pixels;
+      // an empty chunk gives the default pattern)
+      hist_pattern& next = st->ppat[(a.first_chunk + blockIdx.x + 1) % kChunkRing];
+      block_epilogue(h, sampled, a.budget, a.theta, next, es);
+    }
   }
 }
 
@@ -1072,13 +1101,20 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
     const ChunkDesc d = a.c[j];
     const uint32_t slot = (uint32_t)((a.first_chunk + j) % kChunkRing);
     const uint32_t kern = st->rflag[(a.first_chunk + j - 1) % kChunkRing];
-    // the adaptive kernel: the full table after a non-empty chunk, the
-    // default pattern after an empty one (with a window of more than one
-    // chunk the switch can choose it there)
+    // the adaptive kernel: at the full budget the full table after a
+    // non-empty chunk, the default pattern after an empty one (with a window
+    // of more than one chunk the switch can choose it there); below it, the
+    // layout predict_kernel derived for the chunk
     int path = kern == HIST_FLAG_ADAPTIVE ? PATH_SHIFT : PATH_PLAIN;
     int lk = kern == HIST_FLAG_ADAPTIVE ? 5 : 0;
-    if (kern == HIST_FLAG_ADAPTIVE && a.c[j - 1].n == 0) {
-      saturated_pattern(0, a.budget, cs, es);
+    if (kern == HIST_FLAG_ADAPTIVE && (a.budget < HIST_BUDGET_MAX || a.c[j - 1].n == 0)) {
+      __syncthreads();
+      if (a.budget < HIST_BUDGET_MAX) {
+        copy_pattern_cg(&cs.pat, &st->ppat[slot]);
+        __syncthreads();
+      } else {
+        saturated_pattern(0, a.budget, cs, es);
+      }
       classify_pattern(cs.pat, lut, cs);
       path = cs.path;
       lk = cs.lk;
@@ -1178,7 +1214,8 @@ struct hist_stream {
   int grid;
   unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
   bool flat;   // batches run batch_flat_kernel
-  bool autok;  // AUTO at the full budget, window 1: predict, flat launch, recount
+  bool autok;  // AUTO: predict, flat launch, recount
+  bool predict;  // the layouts come from predict_kernel (adaptive kernel below the full budget)
   bool flat_full;  // the stream's pattern is the full table (known on the host)
   unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
   unsigned long long flat_chunks;    // chunks of those launches
@@ -1261,7 +1298,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   if (st->autok) {
     // predictions, the flat launch with the predicted kernels, (the window,)
     // the recount
-    e = cudaLaunchKernel((const void*)auto_predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
+    e = cudaLaunchKernel((const void*)predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess && windowed)
       e = cudaLaunchKernel((const void*)window_predict_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
@@ -1272,10 +1309,13 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)auto_redo_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
                            kSmemBytes, s);
-  } else if (st->flat && windowed) {
-    e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
-                         kFlatSmemBytes, s);
+  } else if (st->flat && (windowed || st->predict)) {
+    e = cudaSuccess;
+    if (st->predict) e = cudaLaunchKernel((const void*)predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
+      e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+                           kFlatSmemBytes, s);
+    if (e == cudaSuccess && windowed)
       e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
   } else if (st->flat) {
     // may start while the previous launch on `s` finishes (see batch_flat_kernel)
@@ -1300,12 +1340,13 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   if (st->autok) {
     st->flat_launches += 1;
     st->flat_chunks += count;
-    st->flat_full = ns[count - 1] > 0;  // the pattern after a non-empty chunk is the full table
+    // at the full budget the pattern after a non-empty chunk is the full table
+    st->flat_full = st->cfg.budget == HIST_BUDGET_MAX && ns[count - 1] > 0;
   } else if (st->flat) {
     st->flat_launches += 1;
     st->flat_chunks += count;
     // in the adaptive mode the pattern after a non-empty chunk is the full table
-    st->flat_full = st->cfg.mode == HIST_MODE_ADAPTIVE && ns[count - 1] > 0;
+    st->flat_full = st->cfg.mode == HIST_MODE_ADAPTIVE && st->cfg.budget == HIST_BUDGET_MAX && ns[count - 1] > 0;
   } else {
     const uint32_t last = count - 1;
     st->pending = true;
@@ -1402,9 +1443,11 @@ int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocat
   // the flat kernel when no chunk's layout depends on its predecessor's
   // pattern: the plain mode, or the full budget (AUTO adds predictions and a
   // recount; a window of more than one chunk adds the window kernels)
-  const bool flatable = cfg->mode == HIST_MODE_PLAIN || cfg->budget == HIST_BUDGET_MAX;
+  const bool flatable = true;
   st->flat = flatable && cfg->mode != HIST_MODE_AUTO;
   st->autok = flatable && cfg->mode == HIST_MODE_AUTO;
+  // below the full budget the adaptive kernel's layout is predicted
+  st->predict = cfg->budget < HIST_BUDGET_MAX && cfg->mode != HIST_MODE_PLAIN;
   const bool flat_kernel = st->flat || st->autok;
   const void* fn = flat_kernel ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
   static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_redo[kMaxDevices];
