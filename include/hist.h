@@ -151,15 +151,19 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  * from chunk i's histogram (a moving window of one chunk).  The first chunk
  * runs the plain kernel with default_pattern(budget).
  *
- * A batch of pushed chunks runs in one cooperative launch.  In AUTO mode, and
- * in ADAPTIVE mode below the full budget, chunk i+1's kernel or layout
- * depends on chunk i's histogram, so the CTAs wait for it between chunks.
- * In PLAIN mode (no pattern used) and in ADAPTIVE mode at HIST_BUDGET_MAX
- * (the rule then gives the full table after every non-empty chunk and the
- * default pattern after an empty one) the layouts are known in advance: the
- * chunks are counted back to back and each one's switch and pattern are
- * computed from its histogram afterwards, and checked against the layout
- * that was used (status bit 8 otherwise). */
+ * The chunks of a push are counted back to back by one launch, and each
+ * chunk's exact switch and pattern are computed from its histogram in its
+ * epilogue.  A chunk's counts do not depend on the kernel or the layout that
+ * count it.  Where those depend on the previous chunk's histogram -- the
+ * switch in AUTO mode, the pattern of the adaptive kernel below
+ * HIST_BUDGET_MAX -- a launch before the count predicts them from a
+ * 4096-pixel sample of the previous chunk; in AUTO mode a chunk whose
+ * predicted kernel is not the one the switch chose is counted again with
+ * that kernel (hist_stream_state.recounted), while a predicted layout that
+ * differs from the exact pattern only costs speed.  At HIST_BUDGET_MAX the
+ * layouts are known in advance (the rule gives the full table after every
+ * non-empty chunk and the default pattern after an empty one) and are
+ * checked against the exact patterns (status bit 8 otherwise). */
 #define HIST_MODE_AUTO 0u     /* kernel chosen by the degeneracy switch */
 #define HIST_MODE_PLAIN 1u    /* always the plain kernel (pattern still refreshed) */
 #define HIST_MODE_ADAPTIVE 2u /* always the adaptive kernel */
@@ -177,7 +181,7 @@ typedef struct hist_config {
   uint32_t budget;      /* sub-bin table slots, HIST_BUDGET_MIN..MAX (default MAX) */
   uint32_t theta_milli; /* critical degeneracy per mille, 0..1000 (default 450) */
   uint32_t mode;        /* HIST_MODE_* (default AUTO) */
-  uint32_t grid;        /* CTAs per chunk launch; 0 = the kernel's default */
+  uint32_t grid;        /* CTAs of a push's counting launch; 0 = every CTA that can be resident */
   uint32_t window;      /* chunks in the moving window, 1..HIST_WINDOW_MAX (default 1) */
   uint32_t reserved[3]; /* zero */
 } hist_config;
@@ -217,11 +221,8 @@ int hist_stream_destroy(hist_stream* st);
 /* Push one chunk (d_chunk, n pixels, n < 2^32).  d_chunk_out: optional
  * uint32_t[256] that receives the chunk's histogram, or null.  The chunk's
  * results (d_chunk_out, the totals, the next pattern and switch) are
- * complete once the push's own work on `s` is (streams counted in one launch
- * per push: the plain mode, every mode at HIST_BUDGET_MAX) or else once the
- * next push on the stream or hist_stream_flush is, in order on `s`: there
- * the epilogue of chunk i runs at the head of chunk i+1's kernel.  The
- * caller keeps d_chunk and d_chunk_out alive until then.
+ * complete once the push's own work on `s` is; the caller keeps d_chunk and
+ * d_chunk_out alive until then.
  * Consecutive calls on one stream object must use the same `s`. */
 int hist_stream_push(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t* d_chunk_out,
                      hist_cuda_stream s);
@@ -229,7 +230,8 @@ int hist_stream_push(hist_stream* st, const uint8_t* d_chunk, size_t n, uint32_t
  * outputs) or hold null entries. */
 int hist_stream_push_many(hist_stream* st, uint32_t count, const uint8_t* const* d_chunks,
                           const size_t* sizes, uint32_t* const* d_chunk_outs, hist_cuda_stream s);
-/* Complete the last pushed chunk's epilogue (no-op if none is pending). */
+/* Kept for callers written against a deferred last epilogue: every push now
+ * completes its own chunks, so this only checks its argument. */
 int hist_stream_flush(hist_stream* st, hist_cuda_stream s);
 /* Flush, then copy the running totals (uint64_t[256]) to d_totals. */
 int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s);
@@ -250,19 +252,15 @@ int hist_stream_attach_staging(hist_stream* st, size_t max_chunk, uint32_t depth
 int hist_stream_push_host(hist_stream* st, const uint8_t* h_chunk, size_t n, uint32_t* d_chunk_out,
                           hist_cuda_stream s);
 
-/* Tracing: the kernels record %globaltimer (ns) at eight phase boundaries of
- * every chunk -- start, previous histogram complete, pattern ready, chunk
- * counted by warp 0, counted by all warps, table reduced, partial sums
- * published, end -- for three CTAs (the first, middle and last) into
- * d_trace, a uint64_t array laid out [chunk][3][8] for
- * capacity_chunks chunks counted from this call; later chunks are not
- * recorded.  Streams that count all of a batch's chunks in one launch (the
- * plain mode at any budget, every mode at HIST_BUDGET_MAX) give each CTA a
- * contiguous range of the chunks placed end to end: a traced CTA records
- * phases 0, 5 and 7 (start of its first piece of the chunk, table reduced,
- * end) of the chunks its range touches and leaves the other entries
- * unchanged.  d_trace null turns tracing off.  The caller keeps d_trace
- * alive while tracing is on. */
+/* Tracing: the counting launch records %globaltimer (ns) for three CTAs
+ * (the first, middle and last) into d_trace, a uint64_t array laid out
+ * [chunk][3][8] for capacity_chunks chunks counted from this call; later
+ * chunks are not recorded.  Each CTA counts a contiguous range of the
+ * push's chunks placed end to end; a traced CTA records, for the chunks its
+ * range touches, phase 0 (start of its piece of the chunk), 5 (its table
+ * reduced) and 7 (end: its piece published, or the chunk's epilogue done),
+ * and leaves the other entries unchanged.  d_trace null turns tracing off.
+ * The caller keeps d_trace alive while tracing is on. */
 int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chunks);
 
 /* Stream state, for inspection and for checkpoint / resume. */

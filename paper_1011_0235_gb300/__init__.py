@@ -236,8 +236,8 @@ class Stream:
         O = (ctypes.c_void_p * n)(*outs) if outs is not None else None
         _abi.check("hist_stream_push_many", lib().hist_stream_push_many(self._h, n, P, Z, O, _stream_ptr(stream)))
 
-    TRACE_PHASES = ("start", "hist_ready", "pattern_ready", "counted_warp0", "counted_all", "reduced",
-                    "published", "end")
+    # eight slots per chunk and CTA; the counting launch fills 0, 5 and 7
+    TRACE_PHASES = ("start", "unused1", "unused2", "unused3", "unused4", "reduced", "unused6", "end")
 
     def trace(self, capacity_chunks: int) -> torch.Tensor:
         """Start tracing into a new [capacity, 3, 8] int64 device tensor (ns)."""

@@ -1,28 +1,14 @@
 // hist_stream.cu -- the chunked stream of Sec. III.B with the kernel switch of
 // Sec. III.C, all on the device.
 //
-// A stream whose chunk kernels and layouts depend on the previous chunk's
-// histogram (the AUTO mode, and the adaptive mode below the full budget)
-// runs each batch of chunks in one cooperative launch of batch_synced_kernel
-// with one 1024-thread CTA per SM.  For each chunk every CTA
-//   1. waits until the previous chunk's histogram is complete: each CTA adds
-//      its per-bin sums into 4 global replicas, then (after a fence) one
-//      arrival and its pixel count into one 64-bit counter; the chunk is
-//      complete when every CTA has arrived and the pixels equal the chunk's
-//      size (the arrivals matter: a CTA with no pixels must also be past its
-//      earlier steps).  One thread per CTA polls the counter (bounded), then
-//      the CTA reads the replicas once;
-//   2. derives this chunk's switch and binning pattern from that histogram
-//      (every CTA computes the same values); every CTA folds a slice of the
-//      previous chunk into the stream state (totals, last histogram, output);
-//   3. counts its slice of the chunk with the chosen kernel, the next
-//      chunk's slice streaming into L2 meanwhile;
-//   4. adds its per-bin sums into the chunk's replicas.
-// The last chunk of a batch stays pending: its epilogue runs at the head of
-// the next batch or in the finish kernel (hist_stream_flush).
-//
-// The other streams (plain mode; adaptive mode at the full budget) run
-// batch_flat_kernel, which needs no waits (see the comment above it).
+// Every batch of chunks a stream is given (hist_stream_push / push_many) is
+// counted by one launch of batch_flat_kernel, which needs no device-wide
+// waits: a chunk's counts do not depend on the kernel or the layout that
+// count it, so where those depend on the previous chunk's histogram (AUTO
+// mode; the adaptive kernel below the full budget) predict_kernel derives
+// them beforehand from a sample of the previous chunk, and the chunks'
+// epilogues record the exact switches and patterns (see the comments above
+// the kernels).
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -38,7 +24,6 @@ using namespace histlib;
 
 namespace {
 
-constexpr int kStreamReplicas = 4;   // global partial histograms per chunk
 constexpr uint32_t kMaxBatch = 128;  // chunks per launch
 constexpr uint32_t kChunkRing = 4 * kMaxBatch;  // flat scratch: chunk accumulators
 constexpr uint32_t kLaunchRing = 8;             // flat scratch: per-launch records
@@ -48,10 +33,6 @@ constexpr uint32_t kStatusPattern = 8;     // device status: a layout differed f
 
 // Device-resident stream state.
 struct StreamDev {
-  uint32_t rep[3][kStreamReplicas][HIST_BINS];  // chunk partials, by chunk index mod 3
-  // CTAs that published into rep[i] (high 32 bits) and their pixels (low 32
-  // bits), one 128-byte line each
-  unsigned long long cnt[3][16];
   // flat batches.  Launches of one stream overlap, so their scratch is in
   // rings: flat chunk g (counted from the stream's first flat chunk) sums
   // into slot g mod kChunkRing, which returns to zero in the chunk's
@@ -74,10 +55,6 @@ struct StreamDev {
   uint32_t wn[kChunkRing];                     // chunk g's size
   unsigned long long wmw[HIST_BINS];
   uint32_t lredo[kLaunchRing][kMaxBatch];
-  // moving window (synced batches, window > 1): the window histogram after
-  // chunk c in mw[c mod 2], chunk c's histogram in wring[c mod (W + 1)]
-  unsigned long long mw[2][HIST_BINS];
-  uint32_t wring[HIST_WINDOW_MAX + 1][HIST_BINS];
   unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
   hist_pattern lpat[kLaunchRing][2];
   uint32_t lflag[kLaunchRing];
@@ -91,7 +68,6 @@ struct StreamDev {
   uint32_t last_kernel;       // kernel the last completed chunk ran
   uint32_t status;            // 0, or kStatusTimeout
   uint32_t recounted;         // AUTO flat batches: chunks recounted after a misprediction
-  uint32_t abort;             // set by a CTA whose wait ran out
 };
 
 struct ChunkDesc {
@@ -104,11 +80,6 @@ struct ChunkDesc {
 struct BatchArgs {
   StreamDev* st;
   uint32_t count;
-  uint32_t has_prev;   // the chunk before this batch is pending: its epilogue runs here
-  uint32_t* prev_out;
-  uint32_t prev_n;
-  uint32_t prev_buf;
-  uint32_t first_buf;  // synced: replica buffer of this batch's first chunk; flat: scratch set
   uint32_t budget;
   uint32_t theta;
   uint32_t mode;
@@ -118,16 +89,15 @@ struct BatchArgs {
   uint32_t chunk0_full;             // flat: the stream's pattern is known to be the full table
   unsigned long long first_chunk;   // flat: number of this batch's first chunk among the stream's flat chunks
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
-  unsigned long long chunk_index;   // synced: index of this batch's first chunk in the stream
   uint32_t window;                  // chunks in the moving window
   uint32_t pad3;
   ChunkDesc c[kMaxBatch];
 };
 
 // Phase timestamps (%globaltimer, ns) of chunk j by CTA slot k (0: the first
-// CTA, 1: the middle one, 2: the last one).
-// start, histogram ready, pattern ready, counted (warp 0), counted (all warps),
-// table reduced, published, end
+// CTA, 1: the middle one, 2: the last one), eight slots per chunk and CTA, of
+// which the flat launch records phase 0 (start of the CTA's piece of the
+// chunk), 5 (table reduced) and 7 (end).
 constexpr int kTracePhases = 8;
 constexpr int kTraceCtas = 3;
 
@@ -137,112 +107,16 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ uint32_t kernel_for(uint32_t mode, uint32_t flag) {
-  return mode == HIST_MODE_AUTO ? flag : (mode == HIST_MODE_PLAIN ? HIST_FLAG_PLAIN : HIST_FLAG_ADAPTIVE);
-}
-
 __device__ __forceinline__ void copy_pattern(hist_pattern* dst, const hist_pattern* src) {
   const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-// Counter value of a complete chunk: `ctas` arrivals and n pixels.
-__device__ __forceinline__ unsigned long long complete_count(uint32_t ctas, uint32_t n) {
-  return ((unsigned long long)ctas << 32) | n;
-}
-
-// Wait until counter `cnt` reaches `target`, then sum the replicas `rep` into
-// cs.hist.  All threads call.  Returns false if the wait ran out or another
-// CTA aborted (the stream status is set).
-__device__ bool poll_gather(StreamDev* st, const uint32_t* rep, const unsigned long long* cnt,
-                            unsigned long long target, uint32_t* part, CtaShared& cs, uint32_t* table_to_zero) {
-  const int t = threadIdx.x;
-  if (table_to_zero && t >= 32) {
-    // the other warps clear the counting table while warp 0 waits
-    uint4* t4 = reinterpret_cast<uint4*>(table_to_zero);
-    for (int i = t - 32; i < kTableWords / 4; i += kThreads - 32) t4[i] = make_uint4(0, 0, 0, 0);
-  }
-  if (t == 0) {
-    uint32_t state = 0;
-    for (uint32_t it = 0;; ++it) {
-      if (ld_acquire(cnt) == target) {
-        state = 1;
-        break;
-      }
-      if (it >= kPollLimit) {
-        atomicExch(&st->abort, 1u);
-        atomicExch(&st->status, kStatusTimeout);
-        break;
-      }
-      if ((it & 63) == 63 && ld_relaxed(&st->abort)) break;
-      __nanosleep(32);
-    }
-    cs.kernel = state;
-  }
-  __syncthreads();
-  if (cs.kernel != 1u) return false;
-  __threadfence();
-  const int b = t & 255, q = t >> 8;  // 1024 threads: one word of the 4 x 256 replicas each
-  part[t] = (q < kStreamReplicas) ? __ldcg(rep + q * HIST_BINS + b) : 0u;
-  __syncthreads();
-  if (t < HIST_BINS) {
-    uint32_t h = 0;
-    for (int r = 0; r < kStreamReplicas; ++r) h += part[r * HIST_BINS + t];
-    cs.hist[t] = h;
-  }
-  __syncthreads();
-  return true;
-}
-
-// Fold the chunk whose histogram is in cs.hist into the stream state.  The
-// work is split over the CTAs: CTA k writes the bins and pattern words whose
-// index is k modulo the CTA count (every CTA holds the same histogram and
-// pattern); CTA 0 writes the scalar fields.  No barrier inside.
-__device__ void write_epilogue(StreamDev* st, uint32_t* out, uint32_t mode, uint32_t flag, const CtaShared& cs,
-                               uint32_t k, uint32_t ctas) {
-  const uint32_t t = threadIdx.x;
-  const uint32_t bin = k + t * ctas;
-  if (bin < HIST_BINS) {
-    const uint32_t h = cs.hist[bin];
-    st->totals[bin] += h;
-    st->last_hist[bin] = h;
-    if (out) out[bin] = h;
-  }
-  constexpr uint32_t words = sizeof(hist_pattern) / 4;
-  const uint32_t wd = k + (t - 256) * ctas;  // threads 256.. copy pattern words
-  if (t >= 256 && wd < words) {
-    uint32_t* cur = reinterpret_cast<uint32_t*>(&st->pattern);
-    uint32_t* last = reinterpret_cast<uint32_t*>(&st->last_pattern);
-    last[wd] = cur[wd];
-    cur[wd] = reinterpret_cast<const uint32_t*>(&cs.pat)[wd];
-  }
-  if (k == 0 && t == 1023) {
-    st->last_kernel = kernel_for(mode, st->flag);
-    st->flag = flag;
-    st->chunks += 1;
-  }
-}
-
-// Switch and pattern for the next chunk from cs.hist (total known), into
-// cs.flag / cs.pat.  All threads call.
-__device__ void epilogue(uint32_t total, uint32_t budget, uint32_t theta, CtaShared& cs, EpiShared& es) {
-  const hist_degeneracy_result r = block_epilogue(cs.hist, total, budget, theta, cs.pat, es);
-  if (threadIdx.x == 0) cs.flag = r.flag;
-  __syncthreads();
 }
 
 struct Geo {
@@ -262,179 +136,6 @@ __device__ __forceinline__ Geo chunk_geo(const ChunkDesc& d) {
   return g;
 }
 
-// Bulk prefetch of this CTA's slice of chunk d into L2 (thread 0).
-__device__ __forceinline__ void prefetch_slice(const ChunkDesc& d) {
-  if (threadIdx.x != 0) return;
-  const Geo g = chunk_geo(d);
-  const uint8_t* p = reinterpret_cast<const uint8_t*>(g.body + g.begin);
-  size_t bytes = (size_t)(g.end - g.begin) * 16;
-  while (bytes) {
-    const uint32_t c = bytes > (1u << 20) ? (1u << 20) : (uint32_t)bytes;
-    prefetch_l2(p, c);
-    p += c;
-    bytes -= c;
-  }
-}
-
-__device__ __forceinline__ void count_geo(int path, int lk, const Geo& g, uint32_t* table, const uint32_t* lut) {
-  count_dispatch(path, lk, g.body, g.begin, g.end, table, lut);
-}
-
-// Set the CTA's layout for a chunk run by `kernel` with pattern cs.pat.
-__device__ __forceinline__ void set_layout(uint32_t kernel, uint32_t* lut, CtaShared& cs) {
-  if (kernel == HIST_FLAG_ADAPTIVE) {
-    classify_pattern(cs.pat, lut, cs);
-  } else {
-    if (threadIdx.x == 0) {
-      cs.path = PATH_PLAIN;
-      cs.lk = 0;
-    }
-    __syncthreads();
-  }
-}
-
-// Reduce the table, add the chunk's edge bytes (CTA 0) and add the per-bin sums
-// into `rep`.  Returns this CTA's pixel count to warp 0.  With `fence`, each
-// adding thread makes its writes visible before the closing barrier.
-__device__ __forceinline__ uint32_t publish_partials(CtaShared& cs, const ChunkDesc& d, uint32_t* table,
-                                                     uint32_t* lut, uint32_t* rep, bool fence) {
-  flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
-  if (blockIdx.x == 0) {
-    count_edges(d.in, split_bytes(d.in, d.n), cs);
-    __syncthreads();
-  }
-  if (threadIdx.x < HIST_BINS) {
-    if (cs.res[threadIdx.x]) atomicAdd(rep + threadIdx.x, cs.res[threadIdx.x]);
-    if (fence) __threadfence();
-  }
-  uint32_t c = 0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < HIST_BINS; i += 32) c += cs.res[i];
-    c = (uint32_t)warp_sum(c);
-  }
-  __syncthreads();
-  return c;
-}
-
-// Moving window (window > 1): chunk c's histogram is in cs.hist.  The
-// window histogram after chunk c is the one after chunk c-1 plus chunk c
-// minus chunk c-W (missing chunks count as empty); it replaces the switch
-// in cs.flag.  Every CTA computes it; CTA k of `ctas` stores the bins whose
-// index is k modulo `ctas` (window histogram by the parity of c, chunk
-// histogram in ring slot c mod (W + 1), so the slot read here, (c - W) mod
-// (W + 1), is never the one written).  A CTA's stores precede its next
-// publication, which every later reader waits for.  All threads call.
-__device__ __noinline__ void window_switch(StreamDev* st, unsigned long long c, uint32_t W, uint32_t theta,
-                                           uint32_t k, uint32_t ctas, CtaShared& cs) {
-  unsigned long long* red = cs.red;  // 16 of its words
-  const int t = threadIdx.x;
-  unsigned long long v = 0, mx = 0, tot = 0;
-  if (t < HIST_BINS) {
-    const unsigned long long prev = c >= 1 ? __ldcg(&st->mw[(c - 1) & 1][t]) : 0ull;
-    const unsigned long long old = c >= W ? (unsigned long long)__ldcg(&st->wring[(c - W) % (W + 1)][t]) : 0ull;
-    const uint32_t h = cs.hist[t];
-    v = prev + h - old;
-    if ((uint32_t)t % ctas == k) {
-      st->mw[c & 1][t] = v;
-      st->wring[c % (W + 1)][t] = h;
-    }
-    mx = v;
-    tot = v;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = m2 > mx ? m2 : mx;
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((t & 31) == 0) {
-      red[t >> 5] = mx;
-      red[8 + (t >> 5)] = tot;
-    }
-  }
-  __syncthreads();
-  if (t == 0) {
-    unsigned long long m = 0, s = 0;
-    for (int i = 0; i < 8; ++i) {
-      m = red[i] > m ? red[i] : m;
-      s += red[8 + i];
-    }
-    cs.flag = reaches_theta(m, s, theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-  }
-  __syncthreads();
-}
-
-// Synchronised batch: chunk j+1's kernel and pattern come from chunk j's
-// histogram, so every CTA waits for it (see the file comment).
-__global__ void __launch_bounds__(kThreads, 1) batch_synced_kernel(const __grid_constant__ BatchArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* table = smem;
-  uint32_t* lut = smem + kTableWords;
-  __shared__ CtaShared cs;
-  __shared__ EpiShared es;
-  StreamDev* st = a.st;
-  const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
-  auto mark = [&](uint32_t j, int phase) {
-    if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
-      a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
-  };
-
-  prefetch_slice(a.c[0]);
-  zero_table(table);
-  __syncthreads();
-
-  for (uint32_t j = 0; j < a.count; ++j) {
-    const uint32_t buf = (a.first_buf + j) % 3;
-    mark(j, 0);
-    // 1. switch and pattern for chunk j from chunk j-1
-    const bool fold = j > 0 || a.has_prev;  // chunk j-1 is folded into the state in this iteration
-    uint32_t* pout = j == 0 ? a.prev_out : a.c[j - 1].out;
-    if (!fold) {
-      copy_pattern(&cs.pat, &st->pattern);
-      if (threadIdx.x == 0) cs.flag = st->flag;
-      __syncthreads();
-      mark(j, 1);
-    } else {
-      const uint32_t pbuf = j == 0 ? a.prev_buf : (a.first_buf + j - 1) % 3;
-      const uint32_t pn = j == 0 ? a.prev_n : a.c[j - 1].n;
-      if (!poll_gather(st, &st->rep[pbuf][0][0], &st->cnt[pbuf][0], complete_count(gridDim.x, pn), lut, cs,
-                       j == 0 ? nullptr : table))
-        return;
-      mark(j, 1);
-      epilogue(pn, a.budget, a.theta, cs, es);
-      if (a.window > 1) window_switch(st, a.chunk_index + j - 1, a.window, a.theta, blockIdx.x, gridDim.x, cs);
-    }
-    mark(j, 2);
-    {
-      // chunk j+1's buffer, a slice per CTA; its last readers gathered chunk
-      // j-2 before adding chunk j-1, which every CTA has now seen complete
-      uint32_t* nb = &st->rep[(buf + 1) % 3][0][0];
-      const uint32_t i = blockIdx.x + threadIdx.x * gridDim.x;
-      if (i < kStreamReplicas * HIST_BINS) nb[i] = 0;
-      if (blockIdx.x == 0 && threadIdx.x == 0) st->cnt[(buf + 1) % 3][0] = 0;
-    }
-    // 2. layout for the chosen kernel; the next chunk streams into L2 meanwhile
-    set_layout(kernel_for(a.mode, cs.flag), lut, cs);
-    if (j + 1 < a.count) prefetch_slice(a.c[j + 1]);
-    // 3. count this CTA's slice (from L2)
-    count_geo(cs.path, cs.lk, chunk_geo(a.c[j]), table, lut);
-    mark(j, 3);
-    __syncthreads();
-    mark(j, 4);
-    // 4. per-bin sums into the replicas, then the pixel count
-    const uint32_t c = publish_partials(cs, a.c[j], table, lut, &st->rep[buf][blockIdx.x % kStreamReplicas][0], true);
-    mark(j, 5);
-    if (threadIdx.x == 0) red_release_add(&st->cnt[buf][0], complete_count(1, c));
-    mark(j, 6);
-    // fold chunk j-1 into the state, off the path the other CTAs wait on
-    if (fold) write_epilogue(st, pout, a.mode, cs.flag, cs, blockIdx.x, gridDim.x);
-    mark(j, 7);
-  }
-}
-
-// Layout the adaptive kernel uses at the full budget after a chunk of n
-// pixels: binning_pattern() of a non-empty histogram is then the full table
-// (the floor reaches 32: 256 x 32 = HIST_BUDGET_MAX), of an empty one the
-// default pattern.
 __device__ void saturated_pattern(uint32_t prev_n, uint32_t budget, CtaShared& cs, EpiShared& es) {
   if (prev_n) {
     if (threadIdx.x < HIST_BINS) {
@@ -1150,44 +851,27 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
 }
 
 // Epilogue of the last pushed chunk (one CTA of 1024 threads).
-__global__ void __launch_bounds__(kThreads) finish_kernel(StreamDev* st, uint32_t buf, uint32_t n, uint32_t ctas,
-                                                          uint32_t* out, uint32_t budget, uint32_t theta, uint32_t mode,
-                                                          unsigned long long chunk, uint32_t window) {
-  __shared__ uint32_t part[kThreads];
-  __shared__ CtaShared cs;
-  __shared__ EpiShared es;
-  if (!poll_gather(st, &st->rep[buf][0][0], &st->cnt[buf][0], complete_count(ctas, n), part, cs, nullptr)) return;
-  epilogue(n, budget, theta, cs, es);
-  if (window > 1) window_switch(st, chunk, window, theta, 0, 1, cs);
-  write_epilogue(st, out, mode, cs.flag, cs, 0, 1);
-}
-
-// The moving-window histogram after chunk `last` (none: zeros).
-// The moving-window histogram after chunk `last` (none: zeros): the last
-// chunk's histogram for a window of one; else the flat path's window
-// histogram, or the synced path's by the parity of the chunk.
-__device__ __forceinline__ unsigned long long window_bin(const StreamDev* st, unsigned long long last, uint32_t window,
-                                                         bool any, bool flat, int b) {
+// The moving-window histogram after the last chunk (none: zeros): the last
+// chunk's histogram for a window of one, else the window kept by the flat
+// launches.
+__device__ __forceinline__ unsigned long long window_bin(const StreamDev* st, uint32_t window, bool any, int b) {
   if (!any) return 0ull;
-  if (window == 1) return st->last_hist[b];
-  return flat ? st->wmw[b] : st->mw[last & 1][b];
+  return window == 1 ? (unsigned long long)st->last_hist[b] : st->wmw[b];
 }
 
-__global__ void window_copy_kernel(const StreamDev* st, unsigned long long last, uint32_t window, bool any, bool flat,
-                                   unsigned long long* out) {
+__global__ void window_copy_kernel(const StreamDev* st, uint32_t window, bool any, unsigned long long* out) {
   const int b = threadIdx.x;
   if (b >= HIST_BINS) return;
-  out[b] = window_bin(st, last, window, any, flat, b);
+  out[b] = window_bin(st, window, any, b);
 }
 
 // Change detection between the stream's totals and its moving-window
-// histogram after chunk `last` (256 threads).
-__global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDev* st, unsigned long long last,
-                                                                  uint32_t window, bool any, bool flat,
+// histogram after the last chunk (256 threads).
+__global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDev* st, uint32_t window, bool any,
                                                                   uint32_t tau_milli, hist_change_result* res) {
   __shared__ ChangeShared sh;
   const int b = threadIdx.x;
-  const unsigned long long m = window_bin(st, last, window, any, flat, b);
+  const unsigned long long m = window_bin(st, window, any, b);
   const hist_change_result r = change_eval(st->totals[b], m, tau_milli, sh);
   if (b == 0) *res = r;
 }
@@ -1212,7 +896,7 @@ struct hist_stream {
   StreamDev* d;
   int sms;
   int grid;
-  unsigned long long chunks_launched;  // chunk index -> replica buffer (index mod 3)
+  unsigned long long chunks_launched;  // chunks pushed
   bool flat;   // batches run batch_flat_kernel
   bool autok;  // AUTO: predict, flat launch, recount
   bool predict;  // the layouts come from predict_kernel (adaptive kernel below the full budget)
@@ -1220,10 +904,6 @@ struct hist_stream {
   unsigned long long flat_launches;  // flat launches so far (scratch ring positions)
   unsigned long long flat_chunks;    // chunks of those launches
   unsigned long long resume_chunk;   // first chunk after the last set_state
-  bool pending;
-  uint32_t* pending_out;
-  uint32_t pending_n;
-  uint32_t pending_buf;
   // tracing (optional)
   unsigned long long* trace;
   uint32_t trace_cap;
@@ -1271,14 +951,8 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   if (!a) return HIST_ENOMEM;
   a->st = st->d;
   a->count = count;
-  a->has_prev = st->pending ? 1u : 0u;
-  a->prev_out = st->pending_out;
-  a->prev_n = st->pending_n;
-  a->prev_buf = st->pending_buf;
-  a->first_buf = (uint32_t)(st->chunks_launched % 3);
   a->chunk0_full = st->flat_full ? 1u : 0u;
   a->first_chunk = st->flat_chunks;
-  a->chunk_index = st->chunks_launched;
   a->window = st->cfg.window;
   a->launch = st->flat_launches + 1;
   a->budget = st->cfg.budget;
@@ -1330,30 +1004,14 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     lc.attrs = at;
     lc.numAttrs = 1;
     e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel, params);
-  } else {
-    // the synced kernel's CTAs wait on one another: all must be resident
-    e = cudaLaunchCooperativeKernel((const void*)batch_synced_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
-                                    kSmemBytes, s);
   }
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (st->autok) {
-    st->flat_launches += 1;
-    st->flat_chunks += count;
-    // at the full budget the pattern after a non-empty chunk is the full table
-    st->flat_full = st->cfg.budget == HIST_BUDGET_MAX && ns[count - 1] > 0;
-  } else if (st->flat) {
-    st->flat_launches += 1;
-    st->flat_chunks += count;
-    // in the adaptive mode the pattern after a non-empty chunk is the full table
-    st->flat_full = st->cfg.mode == HIST_MODE_ADAPTIVE && st->cfg.budget == HIST_BUDGET_MAX && ns[count - 1] > 0;
-  } else {
-    const uint32_t last = count - 1;
-    st->pending = true;
-    st->pending_out = outs ? outs[last] : nullptr;
-    st->pending_n = (uint32_t)ns[last];
-    st->pending_buf = (uint32_t)((st->chunks_launched + last) % 3);
-  }
+  st->flat_launches += 1;
+  st->flat_chunks += count;
+  // at the full budget the pattern after a non-empty chunk is the full table
+  // (the adaptive and AUTO modes; the plain mode never reads it)
+  st->flat_full = st->cfg.mode != HIST_MODE_PLAIN && st->cfg.budget == HIST_BUDGET_MAX && ns[count - 1] > 0;
   st->chunks_launched += count;
   if (st->trace) st->trace_next += count;
   return HIST_OK;
@@ -1369,32 +1027,18 @@ int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, cons
   return HIST_OK;
 }
 
-int do_flush(hist_stream* st, cudaStream_t s) {
-  if (!st->pending) return HIST_OK;
-  finish_kernel<<<1, kThreads, 0, s>>>(st->d, st->pending_buf, st->pending_n, (uint32_t)st->grid, st->pending_out,
-                                       st->cfg.budget, st->cfg.theta_milli, st->cfg.mode, st->chunks_launched - 1,
-                                       st->cfg.window);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e);
-  st->pending = false;
-  st->pending_out = nullptr;
-  return HIST_OK;
-}
-
 bool config_ok(const hist_config* c) {
   return c && c->budget >= HIST_BUDGET_MIN && c->budget <= HIST_BUDGET_MAX && c->theta_milli <= 1000 &&
          c->mode <= HIST_MODE_ADAPTIVE && c->window >= 1 && c->window <= HIST_WINDOW_MAX;
 }
 
-int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem, bool flat) {
-  // at most the CTAs that can be resident at once: a cooperative launch needs
-  // them all; the synced kernel defaults to one CTA per SM (one table
-  // reduction per SM per chunk), the flat one to every resident CTA
+int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
+  // every CTA that can be resident at once, or fewer if the caller asks
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int cap = per_sm * sms;
-  const int g = cfg->grid ? (int)cfg->grid : (flat ? cap : sms);
+  const int g = cfg->grid ? (int)cfg->grid : cap;
   return g > cap ? cap : g;
 }
 
@@ -1439,26 +1083,21 @@ int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocat
   st->cfg = *cfg;
   if (alloc) st->alloc = *alloc;
   st->sms = sm_count();
-  // modes whose chunk layouts never depend on the previous chunk's histogram
-  // the flat kernel when no chunk's layout depends on its predecessor's
-  // pattern: the plain mode, or the full budget (AUTO adds predictions and a
-  // recount; a window of more than one chunk adds the window kernels)
-  const bool flatable = true;
-  st->flat = flatable && cfg->mode != HIST_MODE_AUTO;
-  st->autok = flatable && cfg->mode == HIST_MODE_AUTO;
-  // below the full budget the adaptive kernel's layout is predicted
+  // AUTO adds the predicted switches and a recount; below the full budget
+  // the adaptive kernel's layouts are predicted too; a window of more than
+  // one chunk adds the window kernels
+  st->flat = cfg->mode != HIST_MODE_AUTO;
+  st->autok = cfg->mode == HIST_MODE_AUTO;
   st->predict = cfg->budget < HIST_BUDGET_MAX && cfg->mode != HIST_MODE_PLAIN;
-  const bool flat_kernel = st->flat || st->autok;
-  const void* fn = flat_kernel ? (const void*)batch_flat_kernel : (const void*)batch_synced_kernel;
-  static int attr_sync[kMaxDevices], attr_flat[kMaxDevices], attr_redo[kMaxDevices];
-  const size_t smem = flat_kernel ? kFlatSmemBytes : kSmemBytes;
-  int rc = ensure_smem_attr_bytes(fn, flat_kernel ? attr_flat : attr_sync, smem);
+  const void* fn = (const void*)batch_flat_kernel;
+  static int attr_flat[kMaxDevices], attr_redo[kMaxDevices];
+  int rc = ensure_smem_attr_bytes(fn, attr_flat, kFlatSmemBytes);
   if (rc == HIST_OK && st->autok) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel, attr_redo, kSmemBytes);
   if (rc) {
     free(st);
     return rc;
   }
-  st->grid = grid_for(cfg, st->sms, fn, smem, st->flat || st->autok);
+  st->grid = grid_for(cfg, st->sms, fn, kFlatSmemBytes);
   rc = dev_alloc(st, (void**)&st->d, sizeof(StreamDev));
   if (rc) {
     free(st);
@@ -1555,14 +1194,12 @@ int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chun
 }
 
 int hist_stream_flush(hist_stream* st, hist_cuda_stream s) {
-  if (!st) return HIST_EINVAL;
-  return do_flush(st, (cudaStream_t)s);
+  (void)s;  // every push completes its chunks' epilogues in its own launches
+  return st ? HIST_OK : HIST_EINVAL;
 }
 
 int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s) {
   if (!st || !d_totals) return HIST_EINVAL;
-  int rc = do_flush(st, (cudaStream_t)s);
-  if (rc) return rc;
   const void* src = reinterpret_cast<const char*>(st->d) + offsetof(StreamDev, totals);
   cudaError_t e = cudaMemcpyAsync(d_totals, src, HIST_BINS * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
                                   (cudaStream_t)s);
@@ -1571,11 +1208,8 @@ int hist_stream_totals(hist_stream* st, uint64_t* d_totals, hist_cuda_stream s) 
 
 int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s) {
   if (!st || !d_window) return HIST_EINVAL;
-  int rc = do_flush(st, (cudaStream_t)s);
-  if (rc) return rc;
   const bool any = st->chunks_launched > st->resume_chunk;
-  window_copy_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
-                                                            st->flat || st->autok,
+  window_copy_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->cfg.window, any,
                                                             reinterpret_cast<unsigned long long*>(d_window));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
@@ -1583,19 +1217,14 @@ int hist_stream_window(hist_stream* st, uint64_t* d_window, hist_cuda_stream s) 
 
 int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* d_res, hist_cuda_stream s) {
   if (!st || !d_res || tau_milli > 1000) return HIST_EINVAL;
-  int rc = do_flush(st, (cudaStream_t)s);
-  if (rc) return rc;
   const bool any = st->chunks_launched > st->resume_chunk;
-  stream_change_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->chunks_launched - 1, st->cfg.window, any,
-                                                             st->flat || st->autok, tau_milli, d_res);
+  stream_change_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st->d, st->cfg.window, any, tau_milli, d_res);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 
 int hist_stream_get_state(hist_stream* st, hist_stream_state* h, hist_cuda_stream s) {
   if (!st || !h) return HIST_EINVAL;
-  int rc = do_flush(st, (cudaStream_t)s);
-  if (rc) return rc;
   StreamDev* tmp = (StreamDev*)malloc(sizeof(StreamDev));
   if (!tmp) return HIST_ENOMEM;
   cudaError_t e = cudaMemcpyAsync(tmp, st->d, sizeof(StreamDev), cudaMemcpyDeviceToHost, (cudaStream_t)s);
@@ -1623,8 +1252,6 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h, hist_cuda
   if (hist_pattern_check(&h->pattern) != HIST_OK || hist_pattern_check(&h->last_pattern) != HIST_OK ||
       h->pattern.budget != st->cfg.budget || h->flag > HIST_FLAG_ADAPTIVE)
     return HIST_EINVAL;
-  int rc = do_flush(st, (cudaStream_t)s);
-  if (rc) return rc;
   StreamDev* tmp = (StreamDev*)calloc(1, sizeof(StreamDev));
   if (!tmp) return HIST_ENOMEM;
   memcpy(tmp->totals, h->totals, sizeof(tmp->totals));

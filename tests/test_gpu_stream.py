@@ -241,8 +241,8 @@ def _misleading_chunk(n, value, sampled_law_seed):
     return x
 
 
-@pytest.mark.parametrize("window", [1, 2])
-def test_auto_recounts_chunks_whose_sample_misled(window):
+@pytest.mark.parametrize("window,budget", [(1, 8192), (2, 8192), (1, 960), (2, 2048)])
+def test_auto_recounts_chunks_whose_sample_misled(window, budget):
     # chunks alternate: a misleading degenerate chunk (exact switch ADAPTIVE,
     # sample PLAIN), then flat uniform chunks.  Every chunk whose exact
     # switch (over its window) chose the adaptive kernel was predicted plain,
@@ -255,11 +255,11 @@ def test_auto_recounts_chunks_whose_sample_misled(window):
             chunks.append(_misleading_chunk(n, 40 + c, c))
         else:
             chunks.append(synth.host(n, synth.uniform(), SEED + 60, c * n))
-    ref = oracle.StreamOracle(8192, window=window)
+    ref = oracle.StreamOracle(budget, window=window)
     recs = [ref.push(ch) for ch in chunks]
     bd = dev(np.concatenate(chunks))
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
-    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO, window=window)
+    st = hl.Stream(budget=budget, mode=hl.MODE_AUTO, window=window)
     st.push_many([bd.data_ptr() + c * n for c in range(len(chunks))], [n] * len(chunks),
                  [outs[c].data_ptr() for c in range(len(chunks))])
     s = st.state()
@@ -274,13 +274,58 @@ def test_auto_recounts_chunks_whose_sample_misled(window):
     assert s.recounted == expect
     assert np.array_equal(u64(st.window()), ref.mw)
     # ordinary data: the samples agree with the chunks
-    st2 = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
+    st2 = hl.Stream(budget=budget, mode=hl.MODE_AUTO)
     phase = _phase_chunks(16, lambda c: 1 << 20, 4, SEED + 61)
     bp = dev(np.concatenate(phase))
     st2.push_many([bp.data_ptr() + c * (1 << 20) for c in range(16)], [1 << 20] * 16)
     assert st2.state().recounted == 0
     st.close()
     st2.close()
+
+
+@pytest.mark.parametrize("budget,mode", [(8192, hl.MODE_ADAPTIVE), (960, hl.MODE_AUTO), (8192, hl.MODE_PLAIN)])
+def test_stream_trace(budget, mode):
+    """hist_stream_trace: the three traced CTAs (the first, middle and last of
+    the counting launch) each record phases 0, 5 and 7, in order, for the
+    contiguous run of chunks their range touches -- the first CTA's starts
+    at chunk 0, the last CTA's ends at the last chunk; other entries stay
+    zero; chunks beyond the capacity are not recorded; results are the same
+    with tracing on."""
+    chunks = _phase_chunks(10, lambda c: (3 << 20) + 4096 * c, 3, SEED + 12)
+    ref = oracle.StreamOracle(budget, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    bd = dev(np.concatenate(chunks))
+    offs = np.concatenate([[0], np.cumsum([c.size for c in chunks])])
+    ptrs, sizes = [bd.data_ptr() + int(o) for o in offs[:-1]], [c.size for c in chunks]
+    st = hl.Stream(budget=budget, mode=mode)
+    cap = len(chunks)
+    tr = st.trace(cap)
+    st.push_many(ptrs, sizes)
+    _check_state(st.state(), ref, recs[-1])
+    t = tr.cpu().numpy().view(np.uint64).reshape(cap, 3, 8)
+    seen = {k: [j for j in range(cap) if t[j, k, 0] != 0] for k in range(3)}
+    assert seen[0] and seen[0][0] == 0
+    assert seen[2] and seen[2][-1] == cap - 1
+    assert seen[1] and 0 < seen[1][0] and seen[1][-1] < cap - 1
+    for k, js in seen.items():
+        assert js == list(range(js[0], js[-1] + 1)), (k, js)
+        for j in js:
+            r = t[j, k]
+            assert 0 < r[0] <= r[5] <= r[7], (j, k, r)
+            assert r[1] == r[2] == r[3] == r[4] == r[6] == 0
+    for j in range(cap):
+        for k in range(3):
+            if j not in seen[k]:
+                assert not t[j, k].any()
+    st.trace_off()
+    st.close()
+    # a trace smaller than the push: the chunks past it are not recorded
+    st = hl.Stream(budget=budget, mode=mode)
+    small = st.trace(3)
+    st.push_many(ptrs, sizes)
+    _check_state(st.state(), ref, recs[-1])
+    assert small.shape == (3, 3, 8) and small[0, 0, 0].item() != 0
+    st.close()
 
 
 @pytest.mark.parametrize("depth,budget,mode", [(2, 8192, hl.MODE_ADAPTIVE), (3, 8192, hl.MODE_AUTO),
