@@ -659,6 +659,30 @@ def run_native(args):
         e4 = time_steps(torch, lambda: hl.hist_plain(x, o), 2, 10)
         extras["oneshot_plain_gbs"] = round(nbytes * 10 / e4 / 1e9, 2)
         st_pl.close()
+        # the same stream below the full table (the paper's 960 slots and
+        # between): layouts predicted from samples; beside it, one
+        # hist_adaptive call over the same bytes with the rule's pattern
+        sb = {"budgets": [960, 2048, 4096]}
+        hx1 = hl.hist_plain(x, hl.empty_hist())
+        for name, mode in (("adaptive", hl.MODE_ADAPTIVE), ("auto", hl.MODE_AUTO)):
+            row = []
+            for b in sb["budgets"]:
+                s3 = hl.Stream(budget=b, mode=mode)
+
+                def st3(s3=s3):
+                    s3.push_many(ptrs, sizes)
+                    s3.flush()
+                e5 = time_steps(torch, st3, 2, 10)
+                row.append(round(nbytes * 10 / e5 / 1e9, 2))
+                s3.close()
+            sb["%s_stream_gbs" % name] = row
+        row = []
+        for b in sb["budgets"]:
+            pb = hl.binning_pattern(hx1.clone(), b)
+            e6 = time_steps(torch, lambda: hl.hist_adaptive(x, pb, o), 2, 10)
+            row.append(round(nbytes * 10 / e6 / 1e9, 2))
+        sb["oneshot_adaptive_gbs"] = row
+        extras["stream_budgets"] = sb
 
     # end to end: host buffers through hist_stream_push_host, H2D inside the timed region
     e2e = None
