@@ -47,10 +47,12 @@ def parse():
     ap.add_argument("--chunks", type=int, default=64, help="chunks of 16 MiB per step (64 = 1 GiB)")
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
-    ap.add_argument("--profile-part", default=None, choices=["serving", "batch", "ablation", "table2", "auto"],
+    ap.add_argument("--profile-part", default=None,
+                    choices=["serving", "batch", "ablation", "table2", "auto", "budget960"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
                          "(4000 requests), the 4096-image batch, 256 MiB cases of Table 1 and Table 2, "
-                         "or the degenerate workload through an AUTO stream")
+                         "the degenerate workload through an AUTO stream, or the N(128, 8) stream at "
+                         "960 slots")
     return ap.parse_args()
 
 
@@ -542,6 +544,14 @@ def run_part(args):
         ptrs = [xdg.data_ptr() + c * CHUNK for c in range(64)]
         el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
         out = {"auto_gbs": round(64 * CHUNK * 2 / el / 1e9, 1), "recounted": st.state().recounted}
+    elif args.profile_part == "budget960":
+        # the headline's N(128, 8) stream with the paper's 960-slot table:
+        # predict_kernel, then the counting launch; 3 pushes of 64 chunks
+        x = gen_workload_device(torch, synth, 64, synth.SEED_BASE + 2, lambda c: synth.normal(128, 8))
+        st = hl.Stream(budget=960, mode=hl.MODE_ADAPTIVE)
+        ptrs = [x.data_ptr() + c * CHUNK for c in range(64)]
+        el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
+        out = {"adaptive_960_gbs": round(64 * CHUNK * 2 / el / 1e9, 1), "status": st.state().status}
     else:
         out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=False)
     print(json.dumps({"profile_part": args.profile_part, "result": out}))
