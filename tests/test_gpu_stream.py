@@ -96,8 +96,9 @@ def test_stream_batched_matches_step_by_step_and_outputs():
     st.close()
 
 
-@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
-def test_back_to_back_batches(mode):
+@pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 8192), (hl.MODE_PLAIN, 8192), (hl.MODE_AUTO, 8192),
+                                         (hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 960)])
+def test_back_to_back_batches(mode, budget):
     """Many small push_many calls in a row on one stream, with empty and
     ragged chunks and a checkpoint in the middle: launches of the flat path
     overlap their predecessors, so every chunk's output, the totals and the
@@ -105,7 +106,7 @@ def test_back_to_back_batches(mode):
     rng = np.random.default_rng(11 + mode)
     sizes = [int(x) for x in rng.choice([0, 1, 15, 4096, 65_536, 300_001, 1 << 20], size=160)]
     chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 5, SEED + 20 + mode)
-    ref = oracle.StreamOracle(8192, mode=mode)
+    ref = oracle.StreamOracle(budget, mode=mode)
     recs = [ref.push(ch) for ch in chunks]
     offs, pos = [], 0
     for c, ch in enumerate(chunks):
@@ -117,7 +118,7 @@ def test_back_to_back_batches(mode):
         buf[o:o + ch.size] = ch
     bd = dev(buf)
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
-    st = hl.Stream(budget=8192, mode=mode)
+    st = hl.Stream(budget=budget, mode=mode)
     i = 0
     calls = 0
     while i < len(chunks):
@@ -128,10 +129,32 @@ def test_back_to_back_batches(mode):
         i += len(idx)
         calls += 1
         if calls % 17 == 0:
-            ref_i = oracle.StreamOracle(8192, mode=mode)
+            ref_i = oracle.StreamOracle(budget, mode=mode)
             for ch in chunks[:i]:
                 rec_i = ref_i.push(ch)
             _check_state(st.state(), ref_i, rec_i)
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
+
+
+@pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 8192), (hl.MODE_PLAIN, 8192)])
+def test_one_push_of_600_chunks(mode, budget):
+    """One push_many of 600 chunks: five counting launches of at most 128
+    chunks, whose chunk numbers wrap the 512-slot scratch rings; every
+    chunk's output and the final state equal the oracle's."""
+    rng = np.random.default_rng(600 + mode)
+    sizes = [int(x) for x in rng.choice([0, 33, 4096, 50_000], size=600)]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 7, SEED + 70 + mode)
+    ref = oracle.StreamOracle(budget, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=budget, mode=mode)
+    st.push_many([bd.data_ptr() + int(o) for o in offs[:-1]], sizes, [outs[j].data_ptr() for j in range(600)])
     got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
     for j, r in enumerate(recs):
         assert np.array_equal(got[j], r.hist), j
