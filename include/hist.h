@@ -345,18 +345,19 @@ int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uin
  *   d_status      optional uint32_t: 0, or 4 if a bounded device wait ran out.
  * d_chunks / sizes are host arrays of `count` device pointers and sizes; each
  * size is below 2^32, and count is 1..HIST_NOALLOC_MAX_CHUNKS (more ->
- * HIST_EINVAL).  cfg->grid is ignored; cfg->window must be 1 (HIST_EINVAL
- * otherwise).
+ * HIST_EINVAL).  cfg->grid is ignored; cfg->window is honoured as by
+ * hist_stream_create.
  *
- * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * -- the partial sums of three chunks in flight and their counters, about
- * 12.5 KiB -- is one fixed device array in the library, held by every GPU
- * that loads the library until the process exits, and cleared at the start of
- * every call.  The first call on a device looks up that array's device
- * address and sets the kernel up; make that first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * (on different streams, or from several threads) race and give wrong
- * results; run them in order on one stream. */
+ * It allocates no device memory (no cudaMalloc, cudaFree or other device
+ * allocator): it runs the same launches as hist_stream_push_many on a stream
+ * state -- about 1.9 MiB -- that is one fixed device array in the library,
+ * held by every GPU that loads the library until the process exits, and
+ * cleared and initialised on `s` at the start of every call.  The first call
+ * on a device looks up that array's device address and sets the kernels up;
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (on different streams, or from
+ * several threads) race and give wrong results; run them in order on one
+ * stream. */
 #define HIST_NOALLOC_MAX_CHUNKS 128u
 int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes, uint32_t count,
                             const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals,

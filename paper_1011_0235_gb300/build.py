@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhist.so")
 
-SOURCES = ["hist_core.cu", "hist_stream.cu", "hist_batch.cu", "hist_noalloc.cu", "hist_server.cu", "hist_ablation.cu"]
+SOURCES = ["hist_core.cu", "hist_stream.cu", "hist_batch.cu", "hist_server.cu", "hist_ablation.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -11,6 +11,7 @@
 // the kernels).
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <mutex>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -876,6 +877,17 @@ __global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDe
   if (b == 0) *res = r;
 }
 
+// The stream state of hist_stream_run_noalloc: one fixed array of the
+// library, so that the call allocates no device memory.
+__device__ StreamDev g_noalloc_state;
+
+// The totals and status of a no-alloc run, to the caller's buffers.
+__global__ void noalloc_out_kernel(const StreamDev* st, unsigned long long* totals, uint32_t* status) {
+  const int b = threadIdx.x;
+  if (b < HIST_BINS) totals[b] = st->totals[b];
+  if (b == 0 && status) *status = st->status;
+}
+
 __global__ void init_kernel(StreamDev* st, uint32_t budget) {
   __shared__ CtaShared cs;
   __shared__ uint32_t zero[HIST_BINS];
@@ -1040,6 +1052,31 @@ int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
   const int cap = per_sm * sms;
   const int g = cfg->grid ? (int)cfg->grid : cap;
   return g > cap ? cap : g;
+}
+
+// Once per device, with that device current: the no-alloc state's device
+// address and the counting kernels' shared-memory opt-in (none of it
+// allocates).
+int noalloc_setup(void** state) {
+  static std::mutex mu;
+  static void* ptr[kMaxDevices];
+  static int attr_flat[kMaxDevices], attr_redo[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxDevices) return HIST_EINVAL;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_state);
+    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    int rc = ensure_smem_attr_bytes((const void*)batch_flat_kernel, attr_flat, kFlatSmemBytes);
+    if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel, attr_redo, kSmemBytes);
+    if (rc) return rc;
+    ptr[dev] = p;
+  }
+  *state = ptr[dev];
+  return HIST_OK;
 }
 
 void release_staging(hist_stream* st) {
@@ -1268,6 +1305,43 @@ int hist_stream_set_state(hist_stream* st, const hist_stream_state* h, hist_cuda
   st->flat_launches = 0;   // the rings restart with the zeroed scratch
   st->flat_chunks = 0;
   st->resume_chunk = st->chunks_launched;  // and so does the moving window
+  return e == cudaSuccess ? HIST_OK : cuda_fail(e);
+}
+
+int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes, uint32_t count,
+                            const hist_config* cfg, uint32_t* d_chunk_outs, uint64_t* d_totals, uint32_t* d_status,
+                            hist_cuda_stream s) {
+  if (!cfg || !d_totals || count == 0 || count > HIST_NOALLOC_MAX_CHUNKS || !d_chunks || !sizes) return HIST_EINVAL;
+  hist_config c = *cfg;
+  c.grid = 0;  // ignored: the counting launch takes every resident CTA
+  if (!config_ok(&c)) return HIST_EINVAL;
+  for (uint32_t i = 0; i < count; ++i)
+    if ((!d_chunks[i] && sizes[i]) || sizes[i] >= ((size_t)1 << 32)) return HIST_EINVAL;
+  void* state = nullptr;
+  int rc = noalloc_setup(&state);
+  if (rc) return rc;
+  // a fresh stream on the fixed state: the same launches as hist_stream_push_many
+  hist_stream st;
+  memset(&st, 0, sizeof(st));
+  st.cfg = c;
+  st.d = static_cast<StreamDev*>(state);
+  st.sms = sm_count();
+  st.flat = c.mode != HIST_MODE_AUTO;
+  st.autok = c.mode == HIST_MODE_AUTO;
+  st.predict = c.budget < HIST_BUDGET_MAX && c.mode != HIST_MODE_PLAIN;
+  st.grid = grid_for(&c, st.sms, (const void*)batch_flat_kernel, kFlatSmemBytes);
+  uint32_t* outs[HIST_NOALLOC_MAX_CHUNKS];
+  for (uint32_t i = 0; i < count; ++i) outs[i] = d_chunk_outs ? d_chunk_outs + (size_t)i * HIST_BINS : nullptr;
+  cudaError_t e = cudaMemsetAsync(state, 0, sizeof(StreamDev), (cudaStream_t)s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  init_kernel<<<1, 256, 0, (cudaStream_t)s>>>(st.d, c.budget);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  rc = push_chunks(&st, count, d_chunks, sizes, outs, (cudaStream_t)s);
+  if (rc) return rc;
+  noalloc_out_kernel<<<1, HIST_BINS, 0, (cudaStream_t)s>>>(st.d, reinterpret_cast<unsigned long long*>(d_totals),
+                                                           d_status);
+  e = cudaGetLastError();
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
 

@@ -44,15 +44,16 @@ def _chunks():
     return sizes, offs, torch.from_numpy(buf).cuda()
 
 
-def _config(lib, abi, budget, mode):
+def _config(lib, abi, budget, mode, window=1):
     cfg = abi.HistConfig()
     lib.hist_config_init(ctypes.byref(cfg))
-    cfg.budget, cfg.mode = budget, mode
+    cfg.budget, cfg.mode, cfg.window = budget, mode, window
     return cfg
 
 
-@pytest.mark.parametrize("budget,mode", [(8192, 0), (960, 0), (8192, 2), (2048, 2), (8192, 1)])
-def test_noalloc_matches_stream_api(cuda_ok, budget, mode):
+@pytest.mark.parametrize("budget,mode,window", [(8192, 0, 1), (960, 0, 1), (8192, 2, 1), (2048, 2, 1), (8192, 1, 1),
+                                                (8192, 0, 4), (960, 2, 3)])
+def test_noalloc_matches_stream_api(cuda_ok, budget, mode, window):
     from paper_1011_0235_gb300 import _abi, build
 
     build.build()
@@ -65,7 +66,7 @@ def test_noalloc_matches_stream_api(cuda_ok, budget, mode):
     stream = torch.cuda.current_stream().cuda_stream
 
     # the allocating stream API
-    cfg = _config(lib, _abi, budget, mode)
+    cfg = _config(lib, _abi, budget, mode, window)
     h = ctypes.c_void_p()
     assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
     ref_outs = torch.full((count, 256), -1, dtype=torch.int32, device="cuda")
@@ -110,3 +111,49 @@ def test_noalloc_rejects_sizes_beyond_the_maximum(cuda_ok):
     Z1 = (ctypes.c_size_t * 1)(1 << 32)
     assert lib.hist_stream_run_noalloc(P1, Z1, 1, ctypes.byref(cfg), None, tot.data_ptr(), None, s) == _abi.EINVAL
     assert lib.hist_stream_run_noalloc(P1, Z1, 0, ctypes.byref(cfg), None, tot.data_ptr(), None, s) == _abi.EINVAL
+
+
+def test_noalloc_inside_a_cuda_graph_capture(cuda_ok):
+    """The call the entry point exists for: captured into a CUDA graph (no
+    allocation may happen while capturing) and replayed twice; every replay
+    gives the allocating stream API's results."""
+    from paper_1011_0235_gb300 import _abi, build
+
+    build.build()
+    lib = _abi.load()
+    sizes, offs, dbuf = _chunks()
+    count = len(sizes)
+    P = (ctypes.c_void_p * count)(*[dbuf.data_ptr() + o for o in offs])
+    Z = (ctypes.c_size_t * count)(*sizes)
+    cfg = _config(lib, _abi, 8192, 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p()
+    assert lib.hist_stream_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    ref_outs = torch.full((count, 256), -1, dtype=torch.int32, device="cuda")
+    O = (ctypes.c_void_p * count)(*[ref_outs[i].data_ptr() for i in range(count)])
+    assert lib.hist_stream_push_many(h, count, P, Z, O, stream) == 0
+    ref_tot = torch.empty(256, dtype=torch.int64, device="cuda")
+    assert lib.hist_stream_totals(h, ref_tot.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert lib.hist_stream_destroy(h) == 0
+
+    outs = torch.full((count, 256), -1, dtype=torch.int32, device="cuda")
+    tot = torch.full((256,), -1, dtype=torch.int64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    # the first call on the device sets the entry point up: before capturing
+    assert lib.hist_stream_run_noalloc(P, Z, count, ctypes.byref(cfg), outs.data_ptr(), tot.data_ptr(),
+                                       status.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = lib.hist_stream_run_noalloc(P, Z, count, ctypes.byref(cfg), outs.data_ptr(), tot.data_ptr(),
+                                         status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    for _ in range(2):
+        outs.fill_(-1)
+        tot.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(outs, ref_outs)
+        assert torch.equal(tot, ref_tot)
