@@ -343,14 +343,15 @@ def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
             "adaptive_8192": hl.pattern_from_host(*full)}
     sink = torch.empty(lib.hist_ablation_grid(n) * 256, dtype=torch.int32, device="cuda")
     out = torch.empty(256, dtype=torch.int32, device="cuda")
-    res = {"bytes": n, "stages": ["read+write", "+init", "+pattern", "+atomics", "+reduce"]}
+    res = {"bytes": n, "stages": ["read+write", "+init", "+pattern", "+atomics", "+reduce",
+                                  "complete, warp-aggregated increments"]}
     for law_name, law in (("uniform", synth.uniform()), ("normal_sigma8", synth.normal(128, 8))):
         x = torch.empty(n, dtype=torch.uint8, device="cuda")
         synth.device_fill(x.data_ptr(), n, law, synth.SEED_BASE + 13, 0, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         for name, pd in pats.items():
             row = []
-            for stage in range(1, 6):
+            for stage in range(1, 7):
                 def step(stage=stage, pd=pd):
                     _abi.check("hist_ablation", lib.hist_ablation(
                         x.data_ptr(), n, pd.data_ptr() if pd is not None else None, stage,

@@ -394,8 +394,10 @@ int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* 
  *   3  + read the binning pattern and compute every pixel's sub-bin address;
  *   4  + the shared-memory increments;
  *   5  + sum the sub-bins per bin and write the histogram (= hist_adaptive,
- *        or hist_plain without a pattern).
- * Stage 5 overwrites d_out (uint32_t[256]); stages 1-4 write
+ *        or hist_plain without a pattern);
+ *   6  stage 5 with warp-aggregated increments (the lanes holding one value
+ *        elect a leader, which adds the group's size).
+ * Stages 5 and 6 overwrite d_out (uint32_t[256]); stages 1-4 write
  * hist_ablation_grid(n) x 256 words of scratch to d_sink, contents
  * unspecified.  n < 2^32; HIST_EINVAL for a bad stage or a missing buffer. */
 int hist_ablation_grid(size_t n);

@@ -15,7 +15,11 @@
 //            folding the addresses into the register instead of counting;
 //   stage 4: + the shared-memory increments (the full counting);
 //   stage 5: + reduce the table per bin and add it into the histogram: the
-//            complete kernel (hist_plain / hist_adaptive).
+//            complete kernel (hist_plain / hist_adaptive);
+//   stage 6: stage 5 with warp-aggregated increments: the lanes holding the
+//            same value elect one (__match_any_sync over the active lanes),
+//            which adds the group's size -- the classic remedy for
+//            same-address conflicts, measured against the plain increments.
 // Without a pattern the variants are those of the per-warp (plain) kernel.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,6 +41,12 @@ __device__ __forceinline__ void ablate_word(uint32_t w, uint32_t base, uint32_t 
     const uint32_t v = (w >> (8 * k)) & 0xffu;
     if (STAGE <= 2) {
       acc += v;
+    } else if (STAGE == 6) {
+      const uint32_t m = __match_any_sync(__activemask(), v);
+      if ((uint32_t)(__ffs(m) - 1) == (threadIdx.x & 31u)) {
+        const uint32_t a = PATH == PATH_LUT ? table + (shared_ld(lutb + (v << 7)) << 2) : base + (v << (LK + 2));
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"((uint32_t)__popc(m)) : "memory");
+      }
     } else {
       const uint32_t a = PATH == PATH_LUT ? table + (shared_ld(lutb + (v << 7)) << 2) : base + (v << (LK + 2));
       if (STAGE == 3) acc ^= a;
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const size_t end = begin + per < sp.nvec ? begin + per : sp.nvec;
   uint32_t acc = 0;
   ablate_dispatch<STAGE>(cs.path, cs.lk, body, begin, end, table, lut, acc);
-  if (STAGE == 5) {
+  if (STAGE >= 5) {
     flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
     if (blockIdx.x == 0) {
       count_edges(in, sp, cs);
@@ -148,7 +158,8 @@ const void* ablation_fn(uint32_t stage) {
     case 2: return (const void*)ablation_kernel<2>;
     case 3: return (const void*)ablation_kernel<3>;
     case 4: return (const void*)ablation_kernel<4>;
-    default: return (const void*)ablation_kernel<5>;
+    case 5: return (const void*)ablation_kernel<5>;
+    default: return (const void*)ablation_kernel<6>;
   }
 }
 
@@ -165,15 +176,15 @@ int hist_ablation_grid(size_t n) {
 
 int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t stage, uint32_t* d_out,
                   uint32_t* d_sink, hist_cuda_stream s) {
-  if ((!d_in && n) || n >= ((size_t)1 << 32) || stage < 1 || stage > 5) return HIST_EINVAL;
-  if (stage == 5 && !d_out) return HIST_EINVAL;
+  if ((!d_in && n) || n >= ((size_t)1 << 32) || stage < 1 || stage > 6) return HIST_EINVAL;
+  if (stage >= 5 && !d_out) return HIST_EINVAL;
   if (stage < 5 && !d_sink) return HIST_EINVAL;
-  static int attr_done[5][kMaxDevices];
+  static int attr_done[6][kMaxDevices];
   const void* fn = ablation_fn(stage);
   int rc = ensure_smem_attr_bytes(fn, attr_done[stage - 1], kSmemBytes);
   if (rc) return rc;
   cudaError_t e = cudaSuccess;
-  if (stage == 5) e = cudaMemsetAsync(d_out, 0, HIST_BINS * sizeof(uint32_t), (cudaStream_t)s);
+  if (stage >= 5) e = cudaMemsetAsync(d_out, 0, HIST_BINS * sizeof(uint32_t), (cudaStream_t)s);
   if (e != cudaSuccess) return cuda_fail(e);
   const int grid = hist_ablation_grid(n);
   void* args[] = {(void*)&d_in, (void*)&n, (void*)&d_pat, (void*)&d_out, (void*)&d_sink};

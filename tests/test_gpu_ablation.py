@@ -1,5 +1,6 @@
-"""The Table 1 kernel variants: stage 5 is the complete kernel and must give
-the exact histogram for every layout; stages 1-4 must run and write their
+"""The Table 1 kernel variants: stage 5 is the complete kernel and stage 6
+the complete kernel with warp-aggregated increments, and both must give the
+exact histogram for every layout; stages 1-4 must run and write their
 scratch result on the same inputs (their values are unspecified)."""
 import numpy as np
 import pytest
@@ -45,9 +46,12 @@ def test_ablation_stages(name, n, off):
     s = torch.cuda.current_stream().cuda_stream
     for stage in (1, 2, 3, 4):
         assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, stage, None, sink.data_ptr(), s) == 0
-    assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, 5, out.data_ptr(), None, s) == 0
-    torch.cuda.synchronize()
-    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.hist_u32(x))
+    ref = oracle.hist_u32(x)
+    for stage in (5, 6):
+        out.fill_(-1)
+        assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, stage, out.data_ptr(), None, s) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref), stage
 
 
 def test_ablation_argument_errors():
@@ -56,6 +60,7 @@ def test_ablation_argument_errors():
     out = torch.zeros(256, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     assert lib.hist_ablation(x.data_ptr(), 64, None, 0, out.data_ptr(), out.data_ptr(), s) == -1
-    assert lib.hist_ablation(x.data_ptr(), 64, None, 6, out.data_ptr(), out.data_ptr(), s) == -1
+    assert lib.hist_ablation(x.data_ptr(), 64, None, 7, out.data_ptr(), out.data_ptr(), s) == -1
+    assert lib.hist_ablation(x.data_ptr(), 64, None, 6, None, None, s) == -1
     assert lib.hist_ablation(x.data_ptr(), 64, None, 5, None, None, s) == -1
     assert lib.hist_ablation(x.data_ptr(), 64, None, 2, None, None, s) == -1
