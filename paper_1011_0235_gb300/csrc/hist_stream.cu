@@ -1003,8 +1003,9 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
                            kFlatSmemBytes, s);
     if (e == cudaSuccess && windowed)
       e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
-  } else if (st->flat) {
-    // may start while the previous launch on `s` finishes (see batch_flat_kernel)
+  } else {
+    // PLAIN or ADAPTIVE at the full budget, window 1: one launch, which may
+    // start while the previous launch on `s` finishes (see batch_flat_kernel)
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)st->grid);
     lc.blockDim = dim3(kThreads);
