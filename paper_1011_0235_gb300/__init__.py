@@ -45,6 +45,27 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
     return None if t is None else t.data_ptr()
 
 
+def _dev_buf(t: torch.Tensor, nbytes: int, what: str, elem: Optional[int] = None) -> torch.Tensor:
+    """A device buffer the library reads or writes: a contiguous CUDA tensor
+    of at least `nbytes` bytes (and `elem`-byte elements if given).  The
+    kernels take raw addresses, so a host tensor or a short buffer is caught
+    here instead of on the GPU."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if elem is not None and t.element_size() != elem:
+        raise TypeError("%s must have %d-byte elements" % (what, elem))
+    if t.numel() * t.element_size() < nbytes:
+        raise ValueError("%s must hold at least %d bytes" % (what, nbytes))
+    return t
+
+
+def _out_ptr(t: Optional[torch.Tensor], what: str = "out") -> Optional[int]:
+    """Address of an optional uint32[256] output (4-byte elements)."""
+    return None if t is None else _dev_buf(t, 4 * BINS, what, 4).data_ptr()
+
+
 def empty_hist(device=None, dtype=torch.int32) -> torch.Tensor:
     """A 256-entry device buffer for a u32 histogram (torch has no uint32 ops; the
     bits are read as int32 / converted by ``as_u32``)."""
@@ -69,7 +90,7 @@ def as_u64(h: torch.Tensor):
 def hist_plain(x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Per-warp kernel (NVHist).  Returns a 256-entry int32 tensor holding u32 counts."""
     x = _dev_u8(x)
-    out = empty_hist(x.device) if out is None else out
+    out = empty_hist(x.device) if out is None else _dev_buf(out, 4 * BINS, "out", 4)
     _abi.check("hist_plain", lib().hist_plain(x.data_ptr(), x.numel(), out.data_ptr(), _stream_ptr(stream)))
     return out
 
@@ -79,7 +100,7 @@ def hist_adaptive(x: torch.Tensor, pattern: torch.Tensor, out: Optional[torch.Te
     """Adaptive sub-binned kernel (AHist) with a device pattern buffer (776 bytes)."""
     x = _dev_u8(x)
     _check_pattern_buf(pattern)
-    out = empty_hist(x.device) if out is None else out
+    out = empty_hist(x.device) if out is None else _dev_buf(out, 4 * BINS, "out", 4)
     _abi.check("hist_adaptive", lib().hist_adaptive(x.data_ptr(), x.numel(), pattern.data_ptr(), out.data_ptr(),
                                                     _stream_ptr(stream)))
     return out
@@ -96,6 +117,7 @@ def empty_pattern(device=None) -> torch.Tensor:
 
 def binning_pattern(prev_hist: torch.Tensor, budget: int, out: Optional[torch.Tensor] = None,
                     stream=None) -> torch.Tensor:
+    _dev_buf(prev_hist, 4 * BINS, "prev_hist", 4)
     out = empty_pattern(prev_hist.device) if out is None else out
     _check_pattern_buf(out)
     _abi.check("binning_pattern", lib().binning_pattern(prev_hist.data_ptr(), budget, out.data_ptr(),
@@ -130,6 +152,9 @@ def pattern_to_host(p: torch.Tensor) -> HistPattern:
 def degeneracy(hist: torch.Tensor, theta_milli: int = THETA_MILLI_DEFAULT, stream=None) -> torch.Tensor:
     """Degeneracy of a u32 (int32-typed) or u64 (int64-typed) histogram: a 24-byte
     device buffer holding {u64 max, u64 total, u32 maxbin, u32 flag}."""
+    if not isinstance(hist, torch.Tensor) or hist.element_size() not in (4, 8):
+        raise TypeError("hist must be an int32 (u32 counts) or int64 (u64 counts) tensor")
+    _dev_buf(hist, hist.element_size() * BINS, "hist")
     res = torch.empty(24, dtype=torch.uint8, device=hist.device)
     if hist.element_size() == 4:
         rc = lib().degeneracy(hist.data_ptr(), theta_milli, res.data_ptr(), _stream_ptr(stream))
@@ -150,6 +175,8 @@ def change(acc: torch.Tensor, window: torch.Tensor, tau_milli: int = _abi.HIST_C
            stream=None) -> torch.Tensor:
     """Change detection between two uint64[256] histograms (int64 device
     tensors): a device tensor holding one hist_change_result."""
+    _dev_buf(acc, 8 * BINS, "acc", 8)
+    _dev_buf(window, 8 * BINS, "window", 8)
     out = torch.zeros(2, dtype=torch.int64, device="cuda")
     _abi.check("hist_change", lib().hist_change(acc.data_ptr(), window.data_ptr(), tau_milli, out.data_ptr(),
                                                 _stream_ptr(stream)))
@@ -222,8 +249,8 @@ class Stream:
 
     def push(self, chunk: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> None:
         chunk = _dev_u8(chunk)
-        _abi.check("hist_stream_push", lib().hist_stream_push(self._h, chunk.data_ptr(), chunk.numel(), _ptr(out),
-                                                              _stream_ptr(stream)))
+        _abi.check("hist_stream_push", lib().hist_stream_push(self._h, chunk.data_ptr(), chunk.numel(),
+                                                              _out_ptr(out), _stream_ptr(stream)))
 
     def push_ptr(self, ptr: int, n: int, out_ptr: Optional[int] = None, stream=None) -> None:
         _abi.check("hist_stream_push", lib().hist_stream_push(self._h, ptr, n, out_ptr, _stream_ptr(stream)))
@@ -260,13 +287,13 @@ class Stream:
         _abi.check("hist_stream_flush", lib().hist_stream_flush(self._h, _stream_ptr(stream)))
 
     def totals(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
+        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else _dev_buf(out, 8 * BINS, "out", 8)
         _abi.check("hist_stream_totals", lib().hist_stream_totals(self._h, out.data_ptr(), _stream_ptr(stream)))
         return out
 
     def window(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """The moving-window histogram after the last pushed chunk (uint64 in an int64 tensor)."""
-        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else out
+        out = torch.empty(BINS, dtype=torch.int64, device="cuda") if out is None else _dev_buf(out, 8 * BINS, "out", 8)
         _abi.check("hist_stream_window", lib().hist_stream_window(self._h, out.data_ptr(), _stream_ptr(stream)))
         return out
 
@@ -324,7 +351,7 @@ class Server:
 
     def submit(self, stream_id: int, x: torch.Tensor, out: Optional[torch.Tensor] = None, tag: int = 0) -> None:
         x = _dev_u8(x)
-        self.submit_ptr(stream_id, x.data_ptr(), x.numel(), _ptr(out), tag)
+        self.submit_ptr(stream_id, x.data_ptr(), x.numel(), _out_ptr(out), tag)
 
     def submit_ptr(self, stream_id: int, ptr: int, n: int, out_ptr: Optional[int] = None, tag: int = 0) -> None:
         _abi.check("hist_server_submit", lib().hist_server_submit(self._h, stream_id, ptr, n, out_ptr, tag))

@@ -181,3 +181,17 @@ def test_argument_errors_gpu():
         hl.degeneracy(torch.zeros(256, dtype=torch.int32, device="cuda"), 1001)
     with pytest.raises(TypeError):
         hl.hist_plain(x.to(torch.int32))
+    # buffers the binding refuses before the library sees them
+    short = torch.empty(100, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        hl.hist_plain(x, out=short)
+    with pytest.raises(ValueError):
+        hl.binning_pattern(short, 8192)
+    with pytest.raises(TypeError):
+        hl.change(torch.zeros(256, dtype=torch.int32, device="cuda"), torch.zeros(256, dtype=torch.int64, device="cuda"))
+    st = hl.Stream()
+    with pytest.raises(ValueError):
+        st.push(x, out=short)
+    with pytest.raises(TypeError):
+        st.totals(torch.zeros(256, dtype=torch.int32, device="cuda"))
+    st.close()
