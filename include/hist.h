@@ -275,13 +275,14 @@ typedef struct hist_stream_state {
   uint32_t status;              /* 0, or device-side error bits: 4 = a bounded wait
                                    ran out, 8 = a chunk's layout differed from the
                                    pattern rule (never expected) */
-  uint32_t recounted;           /* AUTO streams at the full budget: chunks counted a
-                                   second time because their kernel was predicted
-                                   from a sample that misjudged the chunk before */
+  uint32_t recounted;           /* AUTO streams: chunks counted a second time
+                                   because their kernel was predicted from a
+                                   sample that misjudged the chunk before */
   uint32_t reserved[6];
 } hist_stream_state;
 
-/* Flush, copy the state to the host and synchronize `s`. */
+/* Copy the state to the host (after the stream's work on `s`) and
+ * synchronize `s`. */
 int hist_stream_get_state(hist_stream* st, hist_stream_state* h_state, hist_cuda_stream s);
 /* Replace the stream's state (resume from a checkpoint); synchronizes `s`.
  * HIST_EINVAL if the state's patterns are invalid for this stream's budget. */

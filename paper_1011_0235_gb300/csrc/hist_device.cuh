@@ -27,7 +27,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTableWords = HIST_BUDGET_MAX;    // 8192 u32 slots (32 KiB)
 constexpr int kLutWords = HIST_BINS * 32;       // one u32 slot index per (value, lane)
 constexpr size_t kSmemBytes = (size_t)(kTableWords + kLutWords) * 4;  // 64 KiB dynamic
-constexpr int kReplicas = 16;                   // global partial-histogram replicas
 
 enum Path : int { PATH_PLAIN = 0, PATH_SHIFT = 1, PATH_LUT = 2 };
 
@@ -190,7 +189,7 @@ __device__ __forceinline__ void zero_table(uint32_t* table) {
   for (int i = threadIdx.x; i < kTableWords / 4; i += kThreads) t4[i] = make_uint4(0, 0, 0, 0);
 }
 
-// Reduce the table to per-bin sums in cs.res (all threads call; ends synced).
+// Reduce the table to per-bin sums in cs.res (all threads call; ends with a barrier).
 // `part` is 1024 words of free shared memory.
 static __device__ void flush_table(int path, int lk, const uint32_t* table, const hist_pattern& pat,
                             uint32_t* part, CtaShared& cs) {
