@@ -263,6 +263,16 @@ int hist_stream_push_host(hist_stream* st, const uint8_t* h_chunk, size_t n, uin
  * The caller keeps d_trace alive while tracing is on. */
 int hist_stream_trace(hist_stream* st, uint64_t* d_trace, uint32_t capacity_chunks);
 
+/* Test hook for the failure path of the one device wait: before a counting
+ * launch adds into its scratch rings, its CTAs wait (bounded) until the
+ * launch that last used those ring slots has finished.  This call makes the
+ * stream's next launch wait for `launches` (1..1024) launches that never
+ * run, so that wait runs out -- after a few seconds -- and the launch
+ * completes with status bit 4 set in the stream state (its counts stay
+ * exact: no other launch uses the rings).  Later launches do not wait.
+ * HIST_EINVAL for a null stream or a count out of range. */
+int hist_stream_test_hold_ring(hist_stream* st, uint32_t launches);
+
 /* Stream state, for inspection and for checkpoint / resume. */
 typedef struct hist_stream_state {
   uint64_t totals[HIST_BINS];   /* sum of all chunk histograms */

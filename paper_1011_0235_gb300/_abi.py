@@ -178,6 +178,7 @@ SIGNATURES = [
     ("hist_config_init", None, [ctypes.POINTER(HistConfig)]),
     ("hist_stream_create", _I, [ctypes.POINTER(HistConfig), ctypes.POINTER(_P)]),
     ("hist_stream_create_with_allocator", _I, [ctypes.POINTER(HistConfig), ctypes.POINTER(Allocator), ctypes.POINTER(_P)]),
+    ("hist_stream_test_hold_ring", _I, [_P, _U32]),
     ("hist_stream_destroy", _I, [_P]),
     ("hist_stream_push", _I, [_P, _P, _Z, _P, _P]),
     ("hist_stream_push_many", _I, [_P, _U32, _P, _P, _P, _P]),

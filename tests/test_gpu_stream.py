@@ -1,5 +1,7 @@
 """GPU parity of the chunked stream (Sec. III.B / III.C) against the oracle's
 StreamOracle: per-chunk histograms, kernel choices, patterns, totals; bit-exact."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -448,6 +450,36 @@ def test_stream_memory_from_the_torch_allocator():
     with pytest.raises(hl.HistError) as e:
         hl.Stream(allocator=NoMemory())
     assert e.value.code == hl._abi.ENOMEM
+
+
+@pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 8192), (hl.MODE_AUTO, 960)])
+def test_ring_wait_runs_out_and_reports_status(mode, budget):
+    """The one device wait's failure path, without a fault: the test hook
+    makes the next launch wait for launches that never run; the bounded
+    wait runs out, the launch completes with status bit 4 and exact counts,
+    and the stream (and the GPU) go on working."""
+    chunks = _phase_chunks(12, lambda c: (1 << 20) + 4096 * c, 3, SEED + 80)
+    ref = oracle.StreamOracle(budget, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    bd = dev(np.concatenate(chunks))
+    offs = np.concatenate([[0], np.cumsum([c.size for c in chunks])])
+    ptrs, sizes = [bd.data_ptr() + int(o) for o in offs[:-1]], [c.size for c in chunks]
+    st = hl.Stream(budget=budget, mode=mode)
+    st.push_many(ptrs[:4], sizes[:4])
+    assert st.state().status == 0
+    assert hl.lib().hist_stream_test_hold_ring(st._h, 16) == 0
+    t0 = time.monotonic()
+    st.push_many(ptrs[4:8], sizes[4:8])
+    s = st.state()
+    held = time.monotonic() - t0
+    assert s.status & 4, s.status
+    assert held > 0.5  # the wait ran to its limit
+    st.push_many(ptrs[8:], sizes[8:])  # later launches do not wait
+    s = st.state()
+    assert np.array_equal(np.array(s.totals, np.uint64), ref.totals)
+    assert bytes(s.pattern) == ref.pattern.to_bytes() and s.flag == ref.flag and s.chunks == ref.chunks
+    assert hl.lib().hist_stream_test_hold_ring(st._h, 0) == hl._abi.EINVAL
+    st.close()
 
 
 def test_stream_checkpoint_resume():
