@@ -243,6 +243,29 @@ def test_replay_poisson_schedule(pool16):
     srv.close()
 
 
+def test_replay_times_out_on_the_host(pool16):
+    """The host loop's own bound: a schedule whose arrivals run to 2 s,
+    replayed with a 100 ms limit, returns HIST_ETIMEDOUT after about 100 ms;
+    the requests already submitted then drain normally."""
+    reqs = workloads.serving_schedule(50, 100, streams=16, region=4 << 20, size_lo=4 << 10, size_hi=64 << 10,
+                                      seed=SEED + 50)
+    assert reqs[-1].arrival_ns > 500_000_000
+    srv = hl.Server(streams=16)
+    R = (_abi.Request * len(reqs))()
+    for i, r in enumerate(reqs):
+        R[i].arrival_ns, R[i].stream, R[i].d_in, R[i].n = r.arrival_ns, r.stream, pool16.ptr(r), r.n
+        R[i].d_out, R[i].tag = None, i
+    t0 = time.monotonic()
+    with pytest.raises(hl.HistError) as e:
+        srv.replay(R, timeout_ms=100)
+    assert e.value.code == _abi.ETIMEDOUT
+    assert time.monotonic() - t0 < 5
+    srv.drain(timeout_ms=60000)
+    st = srv.stats()
+    assert st.queued == 0 and st.inflight_bytes == 0 and st.completed == st.submitted
+    srv.close()
+
+
 def test_full_batches_of_many_small_requests():
     streams, region = 1024, 64 << 10
     pool = Pool(streams, region)
