@@ -32,7 +32,7 @@ CHUNK = 16 * MiB
 METRIC = "input GB/s (% of HBM peak), adaptive vs plain kernel; p50/p99 request latency"
 UNIT = "GB/s"
 CPU_SAMPLE_SECONDS = 10.0
-STREAM_MAX_BATCH = 128  # chunks per launch of the stream kernels
+STREAM_MAX_BATCH = 1024  # chunks per launch of the stream kernels
 SERVE_RATES = (2000, 5000, 10000, 20000, 50000)  # requests per second
 SERVE_SECONDS = 0.5  # of arrivals per rate
 CPU_THREADS_SECONDS = 3.0  # of the threaded oracle count
@@ -701,6 +701,23 @@ def run_native(args):
             row.append(round(nbytes * 10 / e6 / 1e9, 2))
         sb["oneshot_adaptive_gbs"] = row
         extras["stream_budgets"] = sb
+        # the same 1 GiB pushed as smaller chunks (one push_many per GiB):
+        # the fixed cost per launch and per chunk against the bytes
+        cs = {"chunk_kib": [16384, 1024, 256, 64]}
+        for name, mode in (("adaptive", hl.MODE_ADAPTIVE), ("auto", hl.MODE_AUTO)):
+            row = []
+            for kib in cs["chunk_kib"]:
+                k = nbytes // (kib << 10)
+                cp = [x.data_ptr() + i * (kib << 10) for i in range(k)]
+                s4 = hl.Stream(budget=8192, mode=mode)
+
+                def st4(s4=s4, cp=cp, k=k, kib=kib):
+                    s4.push_many(cp, [kib << 10] * k)
+                e7 = time_steps(torch, st4, 2, 5)
+                row.append(round(nbytes * 5 / e7 / 1e9, 2))
+                s4.close()
+            cs["%s_stream_gbs" % name] = row
+        extras["stream_chunk_sizes"] = cs
 
     # end to end: host buffers through hist_stream_push_host, H2D inside the timed region
     e2e = None

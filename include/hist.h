@@ -151,7 +151,8 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  * from chunk i's histogram (a moving window of one chunk).  The first chunk
  * runs the plain kernel with default_pattern(budget).
  *
- * The chunks of a push are counted back to back by one launch, and each
+ * The chunks of a push are counted back to back by one launch (one per
+ * 1024 chunks), and each
  * chunk's exact switch and pattern are computed from its histogram in its
  * epilogue.  A chunk's counts do not depend on the kernel or the layout that
  * count it.  Where those depend on the previous chunk's histogram -- the
@@ -190,7 +191,7 @@ void hist_config_init(hist_config* cfg);
 
 typedef struct hist_stream hist_stream;
 
-/* Allocates the stream's device state (about 1.9 MiB, cudaMalloc on the
+/* Allocates the stream's device state (about 15 MiB, cudaMalloc on the
  * current device: the state, the scratch rings of the one-launch paths and
  * the moving window's chunk histograms) and initialises it; synchronous (the
  * device is synchronized), so call it outside stream capture. */
@@ -361,7 +362,7 @@ int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uin
  *
  * It allocates no device memory (no cudaMalloc, cudaFree or other device
  * allocator): it runs the same launches as hist_stream_push_many on a stream
- * state -- about 1.9 MiB -- that is one fixed device array in the library,
+ * state -- about 15 MiB -- that is one fixed device array in the library,
  * held by every GPU that loads the library until the process exits, and
  * cleared and initialised on `s` at the start of every call.  The first call
  * on a device looks up that array's device address and sets the kernels up;

@@ -25,7 +25,8 @@ using namespace histlib;
 
 namespace {
 
-constexpr uint32_t kMaxBatch = 128;  // chunks per launch
+constexpr uint32_t kMaxBatch = 1024;   // chunks per launch
+constexpr uint32_t kSmallBatch = 128;  // chunks per launch of the smaller parameter block
 constexpr uint32_t kChunkRing = 4 * kMaxBatch;  // flat scratch: chunk accumulators
 constexpr uint32_t kLaunchRing = 8;             // flat scratch: per-launch records
 constexpr uint32_t kPollLimit = 1u << 22;  // bounded wait: about a second
@@ -48,7 +49,7 @@ struct StreamDev {
   uint32_t lk0[kLaunchRing];                   // AUTO flat batches: the stream's switch before the launch
   // flat batches with a window of more than one chunk: every chunk's
   // histogram (by chunk number mod kChunkRing: a window of up to 256 chunks
-  // plus a batch of 128 fit), its sample histogram and sample size (AUTO),
+  // plus a batch of 1024 fit), its sample histogram and sample size (AUTO),
   // and the window histogram after the last chunk of the last launch
   uint32_t whist[kChunkRing][HIST_BINS];
   uint32_t wsamp[kChunkRing][HIST_BINS];
@@ -78,7 +79,12 @@ struct ChunkDesc {
   uint32_t pad;
 };
 
+// The launch parameters: the header and the chunk table.  Two capacities,
+// so that a launch of a few chunks does not carry (and the driver does not
+// copy) a 24 KiB table; the kernels are instantiated for both.
+template <uint32_t CAP>
 struct BatchArgs {
+  static constexpr uint32_t kCap = CAP;
   StreamDev* st;
   uint32_t count;
   uint32_t budget;
@@ -92,8 +98,10 @@ struct BatchArgs {
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
   uint32_t window;                  // chunks in the moving window
   uint32_t pad3;
-  ChunkDesc c[kMaxBatch];
+  ChunkDesc c[CAP];
 };
+using SmallArgs = BatchArgs<kSmallBatch>;
+using LargeArgs = BatchArgs<kMaxBatch>;
 
 // Phase timestamps (%globaltimer, ns) of chunk j by CTA slot k (0: the first
 // CTA, 1: the middle one, 2: the last one), eight slots per chunk and CTA, of
@@ -187,7 +195,10 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 
 constexpr unsigned long long kFlatChunkCost = 64ull << 10;  // cost of a chunk beyond its bytes
 // dynamic shared memory: table, slot table, chunk cost prefix (u64 per chunk + 1)
-constexpr size_t kFlatSmemBytes = (size_t)(kTableWords + kLutWords) * 4 + (size_t)(kMaxBatch + 1) * 8;
+template <class A>
+constexpr size_t flat_smem_bytes() {
+  return (size_t)(kTableWords + kLutWords) * 4 + (size_t)(A::kCap + 1) * 8;
+}
 static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
 
 // pre[j] = sum over chunks before j of (n + kFlatChunkCost); pre[count] = total.
@@ -195,7 +206,8 @@ static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
 // the predicted switch of chunk j-1 (chunk 0: the stream's switch, exact, as
 // predict_kernel copied it before the launch; the launch rewrites the
 // stream's switch at its end).
-__device__ __forceinline__ uint32_t flat_kernel_of(const BatchArgs& a, uint32_t j) {
+template <class A>
+__device__ __forceinline__ uint32_t flat_kernel_of(const A& a, uint32_t j) {
   if (a.mode == HIST_MODE_PLAIN) return HIST_FLAG_PLAIN;
   if (a.mode == HIST_MODE_ADAPTIVE) return HIST_FLAG_ADAPTIVE;
   return j == 0 ? a.st->lk0[a.launch % kLaunchRing] : a.st->rpred[(a.first_chunk + j - 1) % kChunkRing];
@@ -208,9 +220,10 @@ __device__ __forceinline__ uint32_t flat_kernel_of(const BatchArgs& a, uint32_t 
 // constant cache: the distinct addresses of one warp's load are served one
 // after another (4 us per launch when thread t read chunk t's size), so each
 // warp reads its chunks' sizes with a warp-uniform index into shared memory.
-__device__ void flat_prefix(const BatchArgs& a, unsigned long long* pre, uint32_t* wt) {
+template <class A>
+__device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt) {
   __shared__ unsigned long long wsum[kWarps];
-  __shared__ uint32_t sz[kMaxBatch];
+  __shared__ uint32_t sz[A::kCap];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (uint32_t j = (uint32_t)w; j < a.count; j += kWarps) {
     const uint32_t n = a.c[j].n;
@@ -244,7 +257,8 @@ __device__ __forceinline__ void copy_pattern_cg(hist_pattern* dst, const hist_pa
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
   for (int i = threadIdx.x; i < (int)(sizeof(hist_pattern) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
 }
-__device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j, uint32_t* lut, CtaShared& cs,
+template <class A>
+__device__ __noinline__ void flat_layout_general(const A& a, uint32_t j, uint32_t* lut, CtaShared& cs,
                                                  EpiShared& es) {
   __syncthreads();
   if (a.budget < HIST_BUDGET_MAX) {
@@ -260,12 +274,15 @@ __device__ __noinline__ void flat_layout_general(const BatchArgs& a, uint32_t j,
   classify_pattern(cs.pat, lut, cs);
 }
 
-__device__ __forceinline__ uint32_t flat_check(const BatchArgs& a);
-__device__ __forceinline__ uint32_t flat_last_kernel(const BatchArgs& a) {
+template <class A>
+__device__ __forceinline__ uint32_t flat_check(const A& a);
+template <class A>
+__device__ __forceinline__ uint32_t flat_last_kernel(const A& a) {
   return a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;  // AUTO: set by the last epilogue
 }
 
-__device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool adaptive, uint32_t* lut,
+template <class A>
+__device__ __forceinline__ void flat_layout(const A& a, uint32_t j, bool adaptive, uint32_t* lut,
                                             CtaShared& cs, EpiShared& es, int& path, int& lk) {
   if (!adaptive) {
     path = PATH_PLAIN;
@@ -295,10 +312,12 @@ __device__ __forceinline__ void flat_layout(const BatchArgs& a, uint32_t j, bool
 // predicted kernel was not the one the switch chose (for a recount) and
 // sets the last kernel itself.
 constexpr uint32_t kCheckNever = 0, kCheckAlways = 1, kCheckPredicted = 3;
-__device__ __forceinline__ uint32_t flat_check(const BatchArgs& a) {
+template <class A>
+__device__ __forceinline__ uint32_t flat_check(const A& a) {
   return a.mode == HIST_MODE_PLAIN ? kCheckNever : (a.mode == HIST_MODE_ADAPTIVE ? kCheckAlways : kCheckPredicted);
 }
-__device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint32_t check, uint32_t last_kernel,
+template <class A>
+__device__ __noinline__ void flat_epilogue(const A& a, uint32_t j, uint32_t check, uint32_t last_kernel,
                                            hist_pattern& next, CtaShared& cs, EpiShared& es) {
   StreamDev* st = a.st;
   const int t = threadIdx.x;
@@ -366,6 +385,7 @@ __device__ __noinline__ void flat_epilogue(const BatchArgs& a, uint32_t j, uint3
 }
 
 // CTA-wide state of batch_flat_kernel (shared memory).
+template <uint32_t CAP>
 struct FlatShared {
   CtaShared cs;
   EpiShared es;
@@ -377,10 +397,11 @@ struct FlatShared {
   int last;
   int released;  // this CTA has waited for the previous launch
   int ring_ok;   // the chunk ring slots of this launch are free
-  uint32_t wt[kMaxBatch];  // cost weight of each chunk (flat_prefix)
+  uint32_t wt[CAP];  // cost weight of each chunk (flat_prefix)
 };
 
-__device__ __forceinline__ void flat_mark(const BatchArgs& a, uint32_t j, int phase) {
+template <class A>
+__device__ __forceinline__ void flat_mark(const A& a, uint32_t j, int phase) {
   const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
   if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
     a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
@@ -394,13 +415,15 @@ __device__ __forceinline__ void flat_mark(const BatchArgs& a, uint32_t j, int ph
 // first adds into a chunk ring slot, the last user of the slot -- a launch
 // at least kChunkRing / kMaxBatch - 1 launches back -- must have written
 // its state (flat_ring_ready, a bounded wait).  All threads call both.
-__device__ __forceinline__ void flat_release(FlatShared& fs) {
+template <class F>
+__device__ __forceinline__ void flat_release(F& fs) {
   if (!fs.released) pdl_wait();
   __syncthreads();
   if (threadIdx.x == 0) fs.released = 1;
 }
 
-__device__ __noinline__ void flat_ring_ready(const BatchArgs& a, FlatShared& fs) {
+template <class A>
+__device__ __noinline__ void flat_ring_ready(const A& a, FlatShared<A::kCap>& fs) {
   // fs.ring_ok is read between the first two barriers and written after the
   // second, so every thread takes the same branch
   __syncthreads();
@@ -425,7 +448,8 @@ __device__ __noinline__ void flat_ring_ready(const BatchArgs& a, FlatShared& fs)
 // chunk, straight into the chunk's epilogue.  The CTA whose bytes complete
 // the chunk runs the epilogue.  The CTA's last flush leaves the table as it
 // is.  All threads call.
-__device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uint32_t* lut, FlatShared& fs,
+template <class A>
+__device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* lut, FlatShared<A::kCap>& fs,
                                         bool last_flush = false) {
   __syncthreads();
   const int j = fs.cur;
@@ -476,8 +500,9 @@ __device__ __noinline__ void flat_flush(const BatchArgs& a, uint32_t* table, uin
 
 // Count bytes [b0, e0) of chunk j (not empty) into the table, reducing the
 // table first if it holds another chunk.  All threads call.
-__device__ __forceinline__ void flat_piece(const BatchArgs& a, uint32_t j, uint32_t b0, uint32_t e0,
-                                           uint32_t* table, uint32_t* lut, FlatShared& fs) {
+template <class A>
+__device__ __forceinline__ void flat_piece(const A& a, uint32_t j, uint32_t b0, uint32_t e0,
+                                           uint32_t* table, uint32_t* lut, FlatShared<A::kCap>& fs) {
   if (fs.cur != (int)j) {
     flat_flush(a, table, lut, fs);
     flat_mark(a, j, 0);
@@ -502,9 +527,10 @@ __device__ __forceinline__ void flat_piece(const BatchArgs& a, uint32_t j, uint3
 // Count the cost range [x0, x1) of the batch.  Chunk j's byte b sits at
 // cost pre[j] + b wt[j]; a range takes the bytes whose cost position it
 // holds.  All threads call.
-__device__ void flat_range(const BatchArgs& a, const unsigned long long* pre, const uint32_t* wt,
+template <class A>
+__device__ void flat_range(const A& a, const unsigned long long* pre, const uint32_t* wt,
                            unsigned long long x0, unsigned long long x1, uint32_t* table, uint32_t* lut,
-                           FlatShared& fs) {
+                           FlatShared<A::kCap>& fs) {
   uint32_t j = 0, jh = a.count;
   while (j + 1 < jh) {
     const uint32_t mid = (j + jh) >> 1;
@@ -533,12 +559,13 @@ __device__ void flat_range(const BatchArgs& a, const unsigned long long* pre, co
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_constant__ BatchArgs a) {
+template <class A>
+__global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_constant__ A a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
   unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
-  __shared__ FlatShared fs;
+  __shared__ FlatShared<A::kCap> fs;
   const int t = threadIdx.x;
 
   pdl_launch_dependents();
@@ -584,7 +611,8 @@ constexpr uint32_t kSampleVecs = HIST_BINS;  // 16-byte vectors per sample: 4096
 // pattern and kernel (exact).  A chunk's counts do not depend on its
 // layout, so a prediction that differs from the exact pattern only costs
 // speed; the epilogues still record the exact patterns and switches.
-__global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constant__ BatchArgs a) {
+template <class A>
+__global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constant__ A a) {
   __shared__ uint32_t h[HIST_BINS];
   __shared__ uint32_t wm[HIST_BINS / 32];
   __shared__ EpiShared es;
@@ -650,7 +678,7 @@ __global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constan
 // chunk g is the one after chunk g-1 plus chunk g minus chunk g-W, so one
 // CTA runs through the batch's chunks in order, bin b in thread b; per chunk
 // each warp reduces its 32 bins' maximum and sum without a barrier, and the
-// switches come after the loop.  Chunks are numbered from the stream's first
+// switches of each group of eight chunks follow the group.  Chunks are numbered from the stream's first
 // flat chunk (a resumed stream restarts at 0), and a chunk before number 0
 // counts as empty.
 
@@ -665,8 +693,9 @@ __device__ __forceinline__ float window_est(const StreamDev* st, unsigned long l
   return sn ? (float)__ldcg(&st->wsamp[slot][b]) * ((float)__ldcg(&st->wn[slot]) / (float)sn) : 0.0f;
 }
 
-__global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_constant__ BatchArgs a) {
-  __shared__ float smax[kMaxBatch][HIST_BINS / 32], ssum[kMaxBatch][HIST_BINS / 32];
+template <class A>
+__global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_constant__ A a) {
+  __shared__ float smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];  // one group of eight chunks
   const StreamDev* st = a.st;
   const int b = threadIdx.x, w = b >> 5, lane = b & 31;
   const unsigned long long W = a.window, g0 = a.first_chunk;
@@ -699,28 +728,32 @@ __global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_
         sm += __shfl_xor_sync(0xffffffffu, sm, o);
       }
       if (lane == 0) {
-        smax[j0 + k][w] = m;
-        ssum[j0 + k][w] = sm;
+        smax[k][w] = m;
+        ssum[k][w] = sm;
       }
     }
-  }
-  __syncthreads();
-  for (uint32_t j = b; j < a.count; j += HIST_BINS) {
-    float m = 0.0f, sm = 0.0f;
-    for (int i = 0; i < HIST_BINS / 32; ++i) {
-      m = fmaxf(m, smax[j][i]);
-      sm += ssum[j][i];
+    // the group's switches (thread k: chunk j0 + k), then the next group
+    __syncthreads();
+    if (b < 8 && j0 + b < a.count) {
+      float m = 0.0f, sm = 0.0f;
+      for (int i = 0; i < HIST_BINS / 32; ++i) {
+        m = fmaxf(m, smax[b][i]);
+        sm += ssum[b][i];
+      }
+      a.st->rpred[(g0 + j0 + b) % kChunkRing] =
+          (sm > 0.0f && m * 1000.0f >= sm * (float)a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
     }
-    a.st->rpred[(g0 + j) % kChunkRing] =
-        (sm > 0.0f && m * 1000.0f >= sm * (float)a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    __syncthreads();
   }
 }
 
 // Exact window switches after the flat launch; the stream's switch and last
 // kernel; in AUTO mode the list of chunks whose predicted kernel was not the
 // one their predecessor's window switch chose.
-__global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_constant__ BatchArgs a) {
-  __shared__ unsigned long long smax[kMaxBatch][HIST_BINS / 32], ssum[kMaxBatch][HIST_BINS / 32];
+template <class A>
+__global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_constant__ A a) {
+  // one group of eight chunks
+  __shared__ unsigned long long smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];
   StreamDev* st = a.st;
   const int b = threadIdx.x, w = b >> 5, lane = b & 31;
   const unsigned long long W = a.window, g0 = a.first_chunk;
@@ -747,21 +780,23 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
         sm += __shfl_xor_sync(0xffffffffu, sm, o);
       }
       if (lane == 0) {
-        smax[j0 + k][w] = m;
-        ssum[j0 + k][w] = sm;
+        smax[k][w] = m;
+        ssum[k][w] = sm;
       }
     }
+    // the group's switches (thread k: chunk j0 + k), then the next group
+    __syncthreads();
+    if (b < 8 && j0 + b < a.count) {
+      unsigned long long m = 0, sm = 0;
+      for (int i = 0; i < HIST_BINS / 32; ++i) {
+        m = smax[b][i] > m ? smax[b][i] : m;
+        sm += ssum[b][i];
+      }
+      st->rflag[(g0 + j0 + b) % kChunkRing] = reaches_theta(m, sm, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+    }
+    __syncthreads();
   }
   st->wmw[b] = v;
-  __syncthreads();
-  for (uint32_t j = b; j < a.count; j += HIST_BINS) {
-    unsigned long long m = 0, sm = 0;
-    for (int i = 0; i < HIST_BINS / 32; ++i) {
-      m = smax[j][i] > m ? smax[j][i] : m;
-      sm += ssum[j][i];
-    }
-    st->rflag[(g0 + j) % kChunkRing] = reaches_theta(m, sm, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-  }
   __threadfence();
   __syncthreads();
   if (b == 0) {
@@ -785,7 +820,8 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_constant__ BatchArgs a) {
+template <class A>
+__global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_constant__ A a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table of a default-pattern layout, then scratch of the reduction
@@ -957,9 +993,10 @@ void dev_free(hist_stream* st, void* p, size_t bytes) {
   else cudaFree(p);
 }
 
+template <class A>
 int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, const size_t* ns, uint32_t* const* outs,
                  cudaStream_t s) {
-  BatchArgs* a = (BatchArgs*)calloc(1, sizeof(BatchArgs));
+  A* a = (A*)calloc(1, sizeof(A));
   if (!a) return HIST_ENOMEM;
   a->st = st->d;
   a->count = count;
@@ -984,39 +1021,39 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   if (st->autok) {
     // predictions, the flat launch with the predicted kernels, (the window,)
     // the recount
-    e = cudaLaunchKernel((const void*)predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
+    e = cudaLaunchKernel((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess && windowed)
-      e = cudaLaunchKernel((const void*)window_predict_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = cudaLaunchKernel((const void*)window_predict_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
-                           kFlatSmemBytes, s);
+      e = cudaLaunchKernel((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                           flat_smem_bytes<A>(), s);
     if (e == cudaSuccess && windowed)
-      e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)auto_redo_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
+      e = cudaLaunchKernel((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
                            kSmemBytes, s);
   } else if (st->flat && (windowed || st->predict)) {
     e = cudaSuccess;
-    if (st->predict) e = cudaLaunchKernel((const void*)predict_kernel, dim3(count), dim3(HIST_BINS), params, 0, s);
+    if (st->predict) e = cudaLaunchKernel((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)batch_flat_kernel, dim3((unsigned)st->grid), dim3(kThreads), params,
-                           kFlatSmemBytes, s);
+      e = cudaLaunchKernel((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                           flat_smem_bytes<A>(), s);
     if (e == cudaSuccess && windowed)
-      e = cudaLaunchKernel((const void*)window_flat_kernel, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
   } else {
     // PLAIN or ADAPTIVE at the full budget, window 1: one launch, which may
     // start while the previous launch on `s` finishes (see batch_flat_kernel)
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)st->grid);
     lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = kFlatSmemBytes;
+    lc.dynamicSmemBytes = flat_smem_bytes<A>();
     lc.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel, params);
+    e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel<A>, params);
   }
   free(a);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1034,7 +1071,8 @@ int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, cons
                 cudaStream_t s) {
   for (uint32_t i = 0; i < count; i += kMaxBatch) {
     const uint32_t c = count - i < kMaxBatch ? count - i : kMaxBatch;
-    int rc = launch_batch(st, c, ins + i, ns + i, outs ? outs + i : nullptr, s);
+    int rc = c <= kSmallBatch ? launch_batch<SmallArgs>(st, c, ins + i, ns + i, outs ? outs + i : nullptr, s)
+                              : launch_batch<LargeArgs>(st, c, ins + i, ns + i, outs ? outs + i : nullptr, s);
     if (rc) return rc;
   }
   return HIST_OK;
@@ -1055,13 +1093,31 @@ int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {
   return g > cap ? cap : g;
 }
 
+// The counting kernels' shared-memory opt-in, once per (kernel, device).
+int flat_kernels_setup() {
+  static std::mutex mu;
+  static int attr[4][kMaxDevices];
+  std::lock_guard<std::mutex> lock(mu);
+  int rc = ensure_smem_attr_bytes((const void*)batch_flat_kernel<SmallArgs>, attr[0], flat_smem_bytes<SmallArgs>());
+  if (rc == HIST_OK)
+    rc = ensure_smem_attr_bytes((const void*)batch_flat_kernel<LargeArgs>, attr[1], flat_smem_bytes<LargeArgs>());
+  if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel<SmallArgs>, attr[2], kSmemBytes);
+  if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel<LargeArgs>, attr[3], kSmemBytes);
+  return rc;
+}
+
+// The grid of the counting launches (the larger variant's occupancy: the
+// smaller one needs less shared memory).
+int flat_grid(const hist_config* cfg, int sms) {
+  return grid_for(cfg, sms, (const void*)batch_flat_kernel<LargeArgs>, flat_smem_bytes<LargeArgs>());
+}
+
 // Once per device, with that device current: the no-alloc state's device
 // address and the counting kernels' shared-memory opt-in (none of it
 // allocates).
 int noalloc_setup(void** state) {
   static std::mutex mu;
   static void* ptr[kMaxDevices];
-  static int attr_flat[kMaxDevices], attr_redo[kMaxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1071,8 +1127,7 @@ int noalloc_setup(void** state) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_state);
     if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-    int rc = ensure_smem_attr_bytes((const void*)batch_flat_kernel, attr_flat, kFlatSmemBytes);
-    if (rc == HIST_OK) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel, attr_redo, kSmemBytes);
+    const int rc = flat_kernels_setup();
     if (rc) return rc;
     ptr[dev] = p;
   }
@@ -1127,15 +1182,12 @@ int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocat
   st->flat = cfg->mode != HIST_MODE_AUTO;
   st->autok = cfg->mode == HIST_MODE_AUTO;
   st->predict = cfg->budget < HIST_BUDGET_MAX && cfg->mode != HIST_MODE_PLAIN;
-  const void* fn = (const void*)batch_flat_kernel;
-  static int attr_flat[kMaxDevices], attr_redo[kMaxDevices];
-  int rc = ensure_smem_attr_bytes(fn, attr_flat, kFlatSmemBytes);
-  if (rc == HIST_OK && st->autok) rc = ensure_smem_attr_bytes((const void*)auto_redo_kernel, attr_redo, kSmemBytes);
+  int rc = flat_kernels_setup();
   if (rc) {
     free(st);
     return rc;
   }
-  st->grid = grid_for(cfg, st->sms, fn, kFlatSmemBytes);
+  st->grid = flat_grid(cfg, st->sms);
   rc = dev_alloc(st, (void**)&st->d, sizeof(StreamDev));
   if (rc) {
     free(st);
@@ -1338,7 +1390,7 @@ int hist_stream_run_noalloc(const uint8_t* const* d_chunks, const size_t* sizes,
   st.flat = c.mode != HIST_MODE_AUTO;
   st.autok = c.mode == HIST_MODE_AUTO;
   st.predict = c.budget < HIST_BUDGET_MAX && c.mode != HIST_MODE_PLAIN;
-  st.grid = grid_for(&c, st.sms, (const void*)batch_flat_kernel, kFlatSmemBytes);
+  st.grid = flat_grid(&c, st.sms);
   uint32_t* outs[HIST_NOALLOC_MAX_CHUNKS];
   for (uint32_t i = 0; i < count; ++i) outs[i] = d_chunk_outs ? d_chunk_outs + (size_t)i * HIST_BINS : nullptr;
   cudaError_t e = cudaMemsetAsync(state, 0, sizeof(StreamDev), (cudaStream_t)s);

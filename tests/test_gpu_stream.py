@@ -143,12 +143,13 @@ def test_back_to_back_batches(mode, budget):
 
 
 @pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 8192), (hl.MODE_PLAIN, 8192)])
-def test_one_push_of_600_chunks(mode, budget):
-    """One push_many of 600 chunks: five counting launches of at most 128
-    chunks, whose chunk numbers wrap the 512-slot scratch rings; every
+def test_one_push_wrapping_the_rings(mode, budget):
+    """One push_many of 4500 chunks: five counting launches of at most 1024
+    chunks, whose chunk numbers wrap the 4096-slot scratch rings; every
     chunk's output and the final state equal the oracle's."""
+    n = 4500
     rng = np.random.default_rng(600 + mode)
-    sizes = [int(x) for x in rng.choice([0, 33, 4096, 50_000], size=600)]
+    sizes = [int(x) for x in rng.choice([0, 33, 4096, 50_000], size=n)]
     chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 7, SEED + 70 + mode)
     ref = oracle.StreamOracle(budget, mode=mode)
     recs = [ref.push(ch) for ch in chunks]
@@ -156,7 +157,7 @@ def test_one_push_of_600_chunks(mode, budget):
     bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
     st = hl.Stream(budget=budget, mode=mode)
-    st.push_many([bd.data_ptr() + int(o) for o in offs[:-1]], sizes, [outs[j].data_ptr() for j in range(600)])
+    st.push_many([bd.data_ptr() + int(o) for o in offs[:-1]], sizes, [outs[j].data_ptr() for j in range(n)])
     got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
     for j, r in enumerate(recs):
         assert np.array_equal(got[j], r.hist), j
@@ -421,7 +422,7 @@ def test_stream_memory_from_the_torch_allocator():
     recs = [ref.push(ch) for ch in chunks]
     al = _CountingTorchAllocator()
     st = hl.Stream(budget=8192, allocator=al)
-    assert len(al.live) == 1 and min(al.live.values()) >= 1 << 20  # the ~1.9 MiB state
+    assert len(al.live) == 1 and min(al.live.values()) >= 1 << 20  # the ~15 MiB state
     assert all(p % 256 == 0 for p in al.live)
     st.attach_staging(1 << 20, 2)
     assert len(al.live) == 3 and sorted(al.live.values())[:2] == [1 << 20, 1 << 20]
