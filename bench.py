@@ -593,8 +593,9 @@ def run_native(args):
     thr = synth.normal(128, 8)
     seed = synth.SEED_BASE + 2
     x = gen_workload_device(torch, synth, chunks, seed, lambda c: thr, first_chunk=rank * chunks)
-    ptrs = [x.data_ptr() + c * CHUNK for c in range(chunks)]
-    sizes = [CHUNK] * chunks
+    # chunk tables as arrays, passed to the library without conversion
+    ptrs = np.array([x.data_ptr() + c * CHUNK for c in range(chunks)], dtype=np.uint64)
+    sizes = np.full(chunks, CHUNK, dtype=np.uint64)
 
     def stream_step(st):
         def step():
@@ -708,15 +709,23 @@ def run_native(args):
             row = []
             for kib in cs["chunk_kib"]:
                 k = nbytes // (kib << 10)
-                cp = [x.data_ptr() + i * (kib << 10) for i in range(k)]
+                cp = x.data_ptr() + np.arange(k, dtype=np.uint64) * np.uint64(kib << 10)
+                cz = np.full(k, kib << 10, dtype=np.uint64)
                 s4 = hl.Stream(budget=8192, mode=mode)
 
-                def st4(s4=s4, cp=cp, k=k, kib=kib):
-                    s4.push_many(cp, [kib << 10] * k)
+                def st4(s4=s4, cp=cp, cz=cz):
+                    s4.push_many(cp, cz)
                 e7 = time_steps(torch, st4, 2, 5)
                 row.append(round(nbytes * 5 / e7 / 1e9, 2))
                 s4.close()
             cs["%s_stream_gbs" % name] = row
+            # the fixed cost: one launch of 1024 chunks of 16 bytes
+            tp = x.data_ptr() + np.arange(1024, dtype=np.uint64) * np.uint64(4096)
+            tz = np.full(1024, 16, dtype=np.uint64)
+            s5 = hl.Stream(budget=8192, mode=mode)
+            e8 = time_steps(torch, lambda: s5.push_many(tp, tz), 3, 20)
+            cs.setdefault("launch_us_1024x16B", {})[name] = round(e8 / 20 * 1e6, 1)
+            s5.close()
         extras["stream_chunk_sizes"] = cs
 
     # end to end: host buffers through hist_stream_push_host, H2D inside the timed region

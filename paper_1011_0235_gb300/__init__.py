@@ -213,6 +213,26 @@ class TorchAllocator:
         self.struct = _abi.Allocator(self._alloc, self._free, None)
 
 
+
+def _u64_array(seq, n: int, name: str):
+    """The address of n 8-byte integers for a C array argument, and the
+    object that owns them (kept alive for the call)."""
+    if isinstance(seq, torch.Tensor):
+        if seq.device.type != "cpu":
+            raise ValueError(f"{name}: a CPU tensor or a sequence of ints")
+        seq = seq.numpy()
+    if hasattr(seq, "__array_interface__"):
+        import numpy as np
+
+        a = np.asarray(seq)
+        if a.ndim != 1 or a.shape[0] != n or a.dtype.kind not in "iu" or a.dtype.itemsize != 8:
+            raise ValueError(f"{name}: a 1-D array of {n} 8-byte integers")
+        if not a.flags.c_contiguous:
+            a = np.ascontiguousarray(a)
+        return a.ctypes.data, a
+    a = (ctypes.c_uint64 * n)(*[0 if v is None else v for v in seq])
+    return ctypes.addressof(a), a
+
 class Stream:
     """Chunked stream with device-resident adaptive state (Sec. III.B / III.C).
     ``allocator``: None (cudaMalloc), a ``TorchAllocator``, or "torch" for a
@@ -255,12 +275,17 @@ class Stream:
     def push_ptr(self, ptr: int, n: int, out_ptr: Optional[int] = None, stream=None) -> None:
         _abi.check("hist_stream_push", lib().hist_stream_push(self._h, ptr, n, out_ptr, _stream_ptr(stream)))
 
-    def push_many(self, ptrs: Sequence[int], sizes: Sequence[int], outs: Optional[Sequence[Optional[int]]] = None,
-                  stream=None) -> None:
+    def push_many(self, ptrs, sizes, outs=None, stream=None) -> None:
+        """Push len(ptrs) chunks: device addresses, byte counts and optional
+        output addresses, as sequences of ints or as 1-D arrays of 8-byte
+        integers (numpy, or torch on the CPU), which are passed to the
+        library as they are -- building the C arrays from Python ints costs
+        about 0.3 us per chunk on the host, more than a small chunk costs on
+        the device."""
         n = len(ptrs)
-        P = (ctypes.c_void_p * n)(*ptrs)
-        Z = (ctypes.c_size_t * n)(*sizes)
-        O = (ctypes.c_void_p * n)(*outs) if outs is not None else None
+        P, keep_p = _u64_array(ptrs, n, "ptrs")
+        Z, keep_z = _u64_array(sizes, n, "sizes")
+        O, keep_o = _u64_array(outs, n, "outs") if outs is not None else (None, None)
         _abi.check("hist_stream_push_many", lib().hist_stream_push_many(self._h, n, P, Z, O, _stream_ptr(stream)))
 
     # eight slots per chunk and CTA; the counting launch fills 0, 5 and 7

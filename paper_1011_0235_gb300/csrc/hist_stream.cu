@@ -300,6 +300,41 @@ __device__ __forceinline__ void flat_layout(const A& a, uint32_t j, bool adaptiv
 }
 
 
+// AUTO flat launches: the chunks to count again.  Chunk i ran the kernel
+// chunk i-1's predicted switch chose and had to run the one its exact switch
+// chose (chunk 0: the stream's switch, which is exact); the list holds the
+// chunks where the two differ, in order, one thread per chunk (a ballot and
+// a prefix over the warps).  Returns the list's length and, in `kern`, the
+// kernel the last chunk had to run.  All threads call.
+__device__ __noinline__ uint32_t redo_list(StreamDev* st, unsigned long long g0, uint32_t count, uint32_t ls,
+                                           uint32_t& kern) {
+  __shared__ uint32_t wn[kWarps];
+  __shared__ uint32_t base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (int)(blockDim.x >> 5);
+  if (t == 0) base = 0;
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < count; i0 += blockDim.x) {
+    const uint32_t i = i0 + (uint32_t)t;
+    bool redo = false;
+    if (i > 0 && i < count) {
+      const uint32_t prev = (uint32_t)((g0 + i - 1) % kChunkRing);
+      redo = __ldcg(&st->rflag[prev]) != __ldcg(&st->rpred[prev]);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, redo);
+    if (lane == 0) wn[w] = __popc(m);
+    __syncthreads();
+    uint32_t off = base;
+    for (int k = 0; k < w; ++k) off += wn[k];
+    if (redo) st->lredo[ls][off + __popc(m & ((1u << lane) - 1u))] = i;
+    __syncthreads();
+    if (t == 0)
+      for (int k = 0; k < nw; ++k) base += wn[k];
+    __syncthreads();
+  }
+  kern = count > 1 ? __ldcg(&st->rflag[(uint32_t)((g0 + count - 2) % kChunkRing)]) : st->lk0[ls];
+  return base;
+}
+
 // Chunk j is complete and cs.hist holds its histogram: its switch, pattern,
 // output and totals; `check` says when chunk j+1 was counted with the full
 // table that the rule must then give (0: never, 1: always, 2: when chunk j's
@@ -356,19 +391,12 @@ __device__ __noinline__ void flat_epilogue(const A& a, uint32_t j, uint32_t chec
     else copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
     __syncthreads();
     copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
-    if (check == kCheckPredicted && a.window == 1 && t == 0) {
-      // chunk j's kernel had to be chunk j-1's switch (chunk 0: the stream's)
-      const uint32_t before = st->lk0[ls];
-      uint32_t nr = 0, kern = before;
-      for (uint32_t i = 0; i < a.count; ++i) {
-        const uint32_t prev = (uint32_t)((a.first_chunk + i + kChunkRing - 1) % kChunkRing);
-        kern = i == 0 ? before : __ldcg(&st->rflag[prev]);
-        const uint32_t used = i == 0 ? before : __ldcg(&st->rpred[prev]);
-        if (used != kern) st->lredo[ls][nr++] = i;
+    if (check == kCheckPredicted && a.window == 1) {
+      const uint32_t nr = redo_list(st, a.first_chunk, a.count, ls, last_kernel);
+      if (t == 0) {
+        st->lredo_n[ls] = nr;
+        st->recounted += nr;
       }
-      st->lredo_n[ls] = nr;
-      st->recounted += nr;
-      last_kernel = kern;
     }
     if (t == 0) {
       if (a.window == 1) {  // with a window the window kernel sets both
@@ -799,22 +827,17 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
   st->wmw[b] = v;
   __threadfence();
   __syncthreads();
-  if (b == 0) {
-    const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
-    uint32_t kern = a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-    if (a.mode == HIST_MODE_AUTO) {
-      // chunk j's kernel had to be chunk j-1's window switch (chunk 0: the stream's)
-      const uint32_t before = st->lk0[ls];
-      uint32_t nr = 0;
-      for (uint32_t i = 0; i < a.count; ++i) {
-        const uint32_t prev = (uint32_t)((g0 + i + kChunkRing - 1) % kChunkRing);
-        kern = i == 0 ? before : st->rflag[prev];
-        const uint32_t used = i == 0 ? before : st->rpred[prev];
-        if (used != kern) st->lredo[ls][nr++] = i;
-      }
+  const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+  uint32_t kern = a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  if (a.mode == HIST_MODE_AUTO) {
+    // chunk j's kernel had to be chunk j-1's window switch (chunk 0: the stream's)
+    const uint32_t nr = redo_list(st, g0, a.count, ls, kern);
+    if (b == 0) {
       st->lredo_n[ls] = nr;
       st->recounted += nr;
     }
+  }
+  if (b == 0) {
     st->flag = st->rflag[(g0 + a.count - 1) % kChunkRing];
     st->last_kernel = kern;
   }

@@ -35,3 +35,31 @@ def test_buffer_check_helper():
     with pytest.raises(TypeError):
         hl._dev_buf(torch.zeros(256, dtype=torch.int32), 1024, "x", 4)
     assert hl._out_ptr(None) is None
+
+
+def test_chunk_tables_from_lists_and_arrays():
+    # push_many's chunk tables: a list of ints (None for no output) and
+    # 8-byte integer arrays give the same C array; other shapes are refused
+    import ctypes
+
+    import numpy as np
+
+    vals = [0, 1, 1 << 40, (1 << 64) - 1]
+    for seq in (vals, np.array(vals, dtype=np.uint64), torch.tensor(vals[:3], dtype=torch.int64)):
+        n = len(seq)
+        addr, keep = hl._u64_array(seq, n, "x")
+        got = list((ctypes.c_uint64 * n).from_address(addr))
+        assert got == vals[:n]
+    addr, keep = hl._u64_array([None, 5], 2, "outs")
+    assert list((ctypes.c_uint64 * 2).from_address(addr)) == [0, 5]
+    strided = np.arange(8, dtype=np.int64)[::2]
+    addr, keep = hl._u64_array(strided, 4, "x")
+    assert list((ctypes.c_uint64 * 4).from_address(addr)) == [0, 2, 4, 6]
+    with pytest.raises(ValueError):
+        hl._u64_array(np.zeros(4, dtype=np.int32), 4, "x")
+    with pytest.raises(ValueError):
+        hl._u64_array(np.zeros(3, dtype=np.uint64), 4, "x")
+    with pytest.raises(ValueError):
+        hl._u64_array(np.zeros((2, 2), dtype=np.uint64), 2, "x")
+    with pytest.raises(ValueError):
+        hl._u64_array(np.zeros(4, dtype=np.float64), 4, "x")

@@ -157,7 +157,9 @@ def test_one_push_wrapping_the_rings(mode, budget):
     bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
     st = hl.Stream(budget=budget, mode=mode)
-    st.push_many([bd.data_ptr() + int(o) for o in offs[:-1]], sizes, [outs[j].data_ptr() for j in range(n)])
+    # the chunk table as 8-byte integer arrays (passed to the library as they are)
+    st.push_many(np.uint64(bd.data_ptr()) + offs[:-1].astype(np.uint64), np.array(sizes, dtype=np.int64),
+                 torch.tensor([outs[j].data_ptr() for j in range(n)], dtype=torch.int64))
     got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
     for j, r in enumerate(recs):
         assert np.array_equal(got[j], r.hist), j
