@@ -298,6 +298,47 @@ def host_fed_extras(torch, hl, hx, chunks, steps):
         el = time_steps(torch, pipe_step, 2, steps)
         res["staging_depth_%d_gbs" % depth] = round(chunks * CHUNK * steps / el / 1e9, 2)
         st.close()
+    # Figs. 3 and 4: the pipelined time over the sequential time as the
+    # number of chunks grows (4 MiB chunks, 1 .. 256 of them), each step
+    # timed alone (synchronised before and after) so that steps do not overlap
+    c4 = 4 << 20
+    sweep = {"chunk_bytes": c4, "chunks": [k for k in (1, 4, 16, 64, 256) if k * c4 <= hx.numel()],
+             "pipelined_over_sequential": []}
+    d4 = torch.empty(c4, dtype=torch.uint8, device="cuda")
+
+    def alone(step, reps):
+        step()
+        tot = 0.0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    for k in sweep["chunks"]:
+        s1 = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+
+        def seq_k(s1=s1, k=k):
+            for c in range(k):
+                d4.copy_(hx[c * c4:(c + 1) * c4], non_blocking=True)
+                s1.push(d4)
+        t_seq = alone(seq_k, 5)
+        s1.close()
+        s2 = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+        s2.attach_staging(c4, 3)
+
+        def pipe_k(s2=s2, k=k):
+            for c in range(k):
+                s2.push_host(hx.data_ptr() + c * c4, c4)
+        t_pipe = alone(pipe_k, 5)
+        s2.close()
+        sweep["pipelined_over_sequential"].append(round(t_pipe / t_seq, 3))
+    res["chunks_sweep"] = sweep
     return res
 
 
