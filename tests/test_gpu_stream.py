@@ -232,6 +232,34 @@ def test_moving_window_of_256_chunks():
     st.close()
 
 
+@pytest.mark.parametrize("window", [32, 256])
+@pytest.mark.parametrize("mode,budget", [(hl.MODE_AUTO, 8192), (hl.MODE_AUTO, 960), (hl.MODE_ADAPTIVE, 2048),
+                                         (hl.MODE_PLAIN, 8192)])
+def test_moving_window_in_launches_of_1024_chunks(window, mode, budget):
+    """Pushes of 1000 and 1100 chunks (launches of up to 1024 chunks, whose
+    window switches are reduced eight chunks at a time): every chunk's
+    output, the state and the window histogram after each push match the
+    oracle."""
+    chunks = _phase_chunks(2100, lambda c: (0, 17, 4096, 20_000)[(c * 7) % 4], 40, SEED + 80 + window + mode)
+    ref = oracle.StreamOracle(budget, mode=mode, window=window)
+    offs = np.concatenate([[0], np.cumsum([ch.size for ch in chunks])])
+    bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=budget, mode=mode, window=window)
+    for lo, hi in ((0, 1000), (1000, 2100)):
+        ptrs = np.uint64(bd.data_ptr()) + offs[lo:hi].astype(np.uint64)
+        sizes = np.array([chunks[j].size for j in range(lo, hi)], dtype=np.uint64)
+        st.push_many(ptrs, sizes, [outs[j].data_ptr() for j in range(lo, hi)])
+        for j in range(lo, hi):
+            rec = ref.push(chunks[j])
+        _check_state(st.state(), ref, rec)
+        assert np.array_equal(u64(st.window()), ref.mw), hi
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, ch in enumerate(chunks):
+        assert np.array_equal(got[j], oracle.hist_u32(ch)), j
+    st.close()
+
+
 def test_moving_window_restarts_after_resume():
     chunks = _window_chunks(20, 7)
     ref_a = oracle.StreamOracle(8192, window=4)
@@ -267,6 +295,32 @@ def _misleading_chunk(n, value, sampled_law_seed):
         v = k * nvec // 256
         x[16 * v:16 * v + 16] = rng.integers(0, 256, 16)
     return x
+
+
+@pytest.mark.parametrize("window", [1, 2])
+def test_auto_recount_list_of_a_1024_chunk_launch(window):
+    """One AUTO push of 1000 chunks of 64 KiB, every third one misleading
+    (its sample looks flat while it is almost one value): the launch lists
+    its mispredicted chunks with one thread per chunk; the recount total,
+    every output and the state match the oracle."""
+    n = 64 << 10
+    chunks = [_misleading_chunk(n, 40 + c % 200, c) if c % 3 == 0 else
+              synth.host(n, synth.uniform(), SEED + 61, c * n) for c in range(1000)]
+    ref = oracle.StreamOracle(8192, window=window)
+    recs = [ref.push(ch) for ch in chunks]
+    bd = dev(np.concatenate(chunks))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO, window=window)
+    st.push_many(np.uint64(bd.data_ptr()) + np.arange(len(chunks), dtype=np.uint64) * np.uint64(n),
+                 np.full(len(chunks), n, dtype=np.uint64), [outs[c].data_ptr() for c in range(len(chunks))])
+    s = st.state()
+    _check_state(s, ref, recs[-1])
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    expect = sum(1 for r in recs[1:] if r.kernel == oracle.FLAG_ADAPTIVE)
+    assert expect > 300 and s.recounted == expect
+    st.close()
 
 
 @pytest.mark.parametrize("window,budget", [(1, 8192), (2, 8192), (1, 960), (2, 2048)])
