@@ -48,11 +48,11 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
     ap.add_argument("--profile-part", default=None,
-                    choices=["serving", "batch", "ablation", "table2", "auto", "budget960"],
+                    choices=["serving", "batch", "ablation", "table2", "auto", "budget960", "smallchunks"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
                          "(4000 requests), the 4096-image batch, 256 MiB cases of Table 1 and Table 2, "
-                         "the degenerate workload through an AUTO stream, or the N(128, 8) stream at "
-                         "960 slots")
+                         "the degenerate workload through an AUTO stream, the N(128, 8) stream at "
+                         "960 slots, or 256 MiB of it in 64 KiB chunks")
     return ap.parse_args()
 
 
@@ -593,6 +593,15 @@ def run_part(args):
         ptrs = [xdg.data_ptr() + c * CHUNK for c in range(64)]
         el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
         out = {"auto_gbs": round(64 * CHUNK * 2 / el / 1e9, 1), "recounted": st.state().recounted}
+    elif args.profile_part == "smallchunks":
+        # 256 MiB of N(128, 8) in 4096 chunks of 64 KiB through an adaptive
+        # stream: one push_many, four counting launches of 1024 chunks
+        x = gen_workload_device(torch, synth, 16, synth.SEED_BASE + 2, lambda c: synth.normal(128, 8))
+        k, c64 = 4096, 64 << 10
+        st = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+        cp = x.data_ptr() + np.arange(k, dtype=np.uint64) * np.uint64(c64)
+        el = time_steps(torch, lambda: st.push_many(cp, np.full(k, c64, dtype=np.uint64)), 1, 2)
+        out = {"smallchunks_gbs": round(k * c64 * 2 / el / 1e9, 1)}
     elif args.profile_part == "budget960":
         # the headline's N(128, 8) stream with the paper's 960-slot table:
         # predict_kernel, then the counting launch; 3 pushes of 64 chunks
