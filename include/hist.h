@@ -178,13 +178,29 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  * chunk c alone.  W = 1 is the previous chunk. */
 #define HIST_WINDOW_MAX 256u
 
+/* hist_config.flags.
+ * HIST_OVERLAP_PUSHES: the caller promises that the bytes of every chunk it
+ * pushes are complete when the push is called -- written by work the host
+ * has synchronised with (resident data, a synchronised copy or kernel).  A
+ * push's counting launch may then begin reading its chunks while the work
+ * before it on `s` (normally the stream's previous push) is still running,
+ * so consecutive pushes overlap on the device.  Without the flag (default)
+ * the counting launch still starts early and clears its tables, but reads
+ * no chunk byte before the work before it on `s` has completed, so a chunk
+ * written by the kernel just before the push -- even one that lets its
+ * dependents start early -- is read whole.  Only the one-launch paths (PLAIN,
+ * or ADAPTIVE at HIST_BUDGET_MAX, with a window of one chunk) overlap at
+ * all; the others always run after the work before them. */
+#define HIST_OVERLAP_PUSHES 1u
+
 typedef struct hist_config {
   uint32_t budget;      /* sub-bin table slots, HIST_BUDGET_MIN..MAX (default MAX) */
   uint32_t theta_milli; /* critical degeneracy per mille, 0..1000 (default 450) */
   uint32_t mode;        /* HIST_MODE_* (default AUTO) */
   uint32_t grid;        /* CTAs of a push's counting launch; 0 = every CTA that can be resident */
   uint32_t window;      /* chunks in the moving window, 1..HIST_WINDOW_MAX (default 1) */
-  uint32_t reserved[3]; /* zero */
+  uint32_t flags;       /* HIST_OVERLAP_PUSHES or 0 (default 0) */
+  uint32_t reserved[2]; /* zero */
 } hist_config;
 
 void hist_config_init(hist_config* cfg);

@@ -227,22 +227,33 @@ def _u64_array(seq, n: int, name: str):
         a = np.asarray(seq)
         if a.ndim != 1 or a.shape[0] != n or a.dtype.kind not in "iu" or a.dtype.itemsize != 8:
             raise ValueError(f"{name}: a 1-D array of {n} 8-byte integers")
+        if a.dtype.byteorder not in "=|":
+            raise ValueError(f"{name}: integers in the machine's byte order")
+        if a.dtype.kind == "i" and n and int(a.min()) < 0:
+            raise ValueError(f"{name}: negative values")
         if not a.flags.c_contiguous:
             a = np.ascontiguousarray(a)
         return a.ctypes.data, a
-    a = (ctypes.c_uint64 * n)(*[0 if v is None else v for v in seq])
+    vals = [0 if v is None else int(v) for v in seq]
+    if any(v < 0 for v in vals):
+        raise ValueError(f"{name}: negative values")
+    a = (ctypes.c_uint64 * n)(*vals)
     return ctypes.addressof(a), a
 
 class Stream:
     """Chunked stream with device-resident adaptive state (Sec. III.B / III.C).
     ``allocator``: None (cudaMalloc), a ``TorchAllocator``, or "torch" for a
-    new ``TorchAllocator`` on the current device."""
+    new ``TorchAllocator`` on the current device.  ``overlap``: set
+    HIST_OVERLAP_PUSHES -- the caller promises that every pushed chunk is
+    complete when it is pushed (written by work the host has synchronised
+    with), so consecutive pushes may overlap on the device."""
 
     def __init__(self, budget: int = BUDGET_MAX, theta_milli: int = THETA_MILLI_DEFAULT, mode: int = MODE_AUTO,
-                 grid: int = 0, window: int = 1, allocator=None):
+                 grid: int = 0, window: int = 1, allocator=None, overlap: bool = False):
         cfg = _abi.HistConfig()
         lib().hist_config_init(ctypes.byref(cfg))
         cfg.budget, cfg.theta_milli, cfg.mode, cfg.grid, cfg.window = budget, theta_milli, mode, grid, window
+        cfg.flags = _abi.HIST_OVERLAP_PUSHES if overlap else 0
         h = ctypes.c_void_p()
         if allocator == "torch":
             allocator = TorchAllocator()

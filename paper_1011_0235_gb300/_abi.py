@@ -33,6 +33,7 @@ EBUSY = -6
 ESTATE = -7
 
 HIST_NOALLOC_MAX_CHUNKS = 128
+HIST_OVERLAP_PUSHES = 1
 HIST_BATCH_MAX_IMAGES = 4096
 HIST_WINDOW_MAX = 256
 HIST_CHANGE_TAU_MILLI_DEFAULT = 250
@@ -75,7 +76,8 @@ class HistConfig(ctypes.Structure):
         ("mode", ctypes.c_uint32),
         ("grid", ctypes.c_uint32),
         ("window", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 3),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 

@@ -82,8 +82,50 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t l
   }
 }
 
+#ifndef HIST_PLAIN_ORDER
+#define HIST_PLAIN_ORDER 2
+#endif
+
+// The order in which a lane of the per-warp layout takes the 16 bytes of its
+// vector: lane l counts byte s ^ (l mod 16) at step s.  The increments of one
+// step are one warp-wide shared-memory operation; when neighbouring pixels
+// differ by a constant (a ramp: lane l holds values 16 l .. 16 l + 15), the
+// natural order puts the warp's 16 distinct values in two banks (8-way
+// conflicts), while this order spreads them over 16 banks.  Equal values
+// still meet at one address, which costs nothing.  Two byte-permutes per
+// 4 bytes: the first takes word i or i ^ 1 with its bytes in xor order, the
+// second word i or i ^ 2 of the result.
+struct LaneOrder {
+  uint32_t a, b;  // byte-permute selectors
+};
+__device__ __forceinline__ LaneOrder lane_order() {
+  const uint32_t c = threadIdx.x & 15u, x = c & 3u, hi = (c >> 2) & 1u;
+  LaneOrder o;
+  o.a = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j) o.a |= (((j ^ x) + 4u * hi) << (4 * j));
+  o.b = (c >> 3) ? 0x7654u : 0x3210u;
+  return o;
+}
+__device__ __forceinline__ uint4 lane_permute(const uint4& q, const LaneOrder& o) {
+#if HIST_PLAIN_ORDER == 0
+  return q;
+#else
+  const uint32_t t0 = __byte_perm(q.x, q.y, o.a), t1 = __byte_perm(q.y, q.x, o.a);
+  const uint32_t t2 = __byte_perm(q.z, q.w, o.a), t3 = __byte_perm(q.w, q.z, o.a);
+#if HIST_PLAIN_ORDER == 1
+  return make_uint4(t0, t1, t2, t3);
+#else
+  return make_uint4(__byte_perm(t0, t2, o.b), __byte_perm(t1, t3, o.b), __byte_perm(t2, t0, o.b),
+                    __byte_perm(t3, t1, o.b));
+#endif
+#endif
+}
+
 template <int PATH, int LK>
-__device__ __forceinline__ void count_vec(const uint4& q, uint32_t base, uint32_t lutb, uint32_t table) {
+__device__ __forceinline__ void count_vec(const uint4& q0, uint32_t base, uint32_t lutb, uint32_t table,
+                                          const LaneOrder& o) {
+  const uint4 q = PATH == PATH_PLAIN ? lane_permute(q0, o) : q0;
   count_word<PATH, LK>(q.x, base, lutb, table);
   count_word<PATH, LK>(q.y, base, lutb, table);
   count_word<PATH, LK>(q.z, base, lutb, table);
@@ -112,6 +154,7 @@ static __device__ void count_range(const uint4* __restrict__ p, size_t begin, si
                                    const uint32_t* lut, int tid, int nthr) {
   uint32_t base, lutb, tab;
   thread_bases<PATH, LK>(table, lut, base, lutb, tab);
+  const LaneOrder o = lane_order();
   size_t i = begin + tid;
   if (i + (size_t)(UNROLL - 1) * nthr < end) {
     uint4 v[UNROLL];
@@ -123,14 +166,14 @@ static __device__ void count_range(const uint4* __restrict__ p, size_t begin, si
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) w[u] = ldg_stream(p + i + (size_t)u * nthr);
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) count_vec<PATH, LK>(v[u], base, lutb, tab);
+      for (int u = 0; u < UNROLL; ++u) count_vec<PATH, LK>(v[u], base, lutb, tab, o);
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) v[u] = w[u];
     }
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) count_vec<PATH, LK>(v[u], base, lutb, tab);
+    for (int u = 0; u < UNROLL; ++u) count_vec<PATH, LK>(v[u], base, lutb, tab, o);
   }
-  for (; i < end; i += nthr) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, tab);
+  for (; i < end; i += nthr) count_vec<PATH, LK>(ldg_stream(p + i), base, lutb, tab, o);
 }
 
 // The whole CTA, two loads in flight.

@@ -406,7 +406,9 @@ uint32_t retire(hist_server* s, hist_completion* out, uint32_t cap, int* err) {
     for (uint32_t i = 0; i < count && f.n_reported < count && (!out || n < cap); ++i) {
       if (f.reported[i]) continue;
       // the acquire pairs with the epilogue's release: the request's output
-      // and its stream's state are written before the word is
+      // is written before the word is; its stream's state is written after
+      // it and is complete once the batch's event fires, which is when the
+      // stream is released for admission
       if (!all && __atomic_load_n(f.h_done + i, __ATOMIC_ACQUIRE) != f.seq) continue;
       const PendingReq& r = f.reqs[i];
       if (out) {

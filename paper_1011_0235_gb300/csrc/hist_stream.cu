@@ -97,7 +97,7 @@ struct BatchArgs {
   unsigned long long first_chunk;   // flat: number of this batch's first chunk among the stream's flat chunks
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
   uint32_t window;                  // chunks in the moving window
-  uint32_t pad3;
+  uint32_t early;                   // flat: chunks may be read before the work before the launch completes
   ChunkDesc c[CAP];
 };
 using SmallArgs = BatchArgs<kSmallBatch>;
@@ -437,12 +437,17 @@ __device__ __forceinline__ void flat_mark(const A& a, uint32_t j, int phase) {
 
 // Launches of one stream overlap (programmatic dependent launch): every
 // CTA lets the next launch start as soon as it starts, so the next launch's
-// CTAs take the SM slots that this launch's CTAs free as they finish.  A
-// CTA waits for the previous launch to complete before its first epilogue,
-// which reads and writes the stream state (flat_release), and before it
-// first adds into a chunk ring slot, the last user of the slot -- a launch
-// at least kChunkRing / kMaxBatch - 1 launches back -- must have written
-// its state (flat_ring_ready, a bounded wait).  All threads call both.
+// CTAs take the SM slots that this launch's CTAs free as they finish, clear
+// their tables and split the work.  Unless the caller has declared every
+// chunk complete when it was pushed (a.early, HIST_OVERLAP_PUSHES), a CTA
+// then waits for the work before the launch on the CUDA stream to complete
+// before it reads a chunk byte: that work may be the kernel that wrote the
+// chunk, and only the wait makes its writes visible.  A CTA also waits for
+// the previous launch to complete before its first epilogue, which reads
+// and writes the stream state (flat_release), and before it first adds
+// into a chunk ring slot, the last user of the slot -- a launch at least
+// kChunkRing / kMaxBatch - 1 launches back -- must have written its state
+// (flat_ring_ready, a bounded wait).  All threads call both.
 template <class F>
 __device__ __forceinline__ void flat_release(F& fs) {
   if (!fs.released) pdl_wait();
@@ -605,6 +610,11 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   }
   zero_table(table);
   flat_prefix(a, pre, fs.wt);
+  if (!a.early) {
+    // the chunks may come from the work just before this launch
+    pdl_wait();
+    if (t == 0) fs.released = 1;
+  }
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
   if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, table, lut, fs);
@@ -937,8 +947,10 @@ __global__ void __launch_bounds__(HIST_BINS) stream_change_kernel(const StreamDe
 }
 
 // The stream state of hist_stream_run_noalloc: one fixed array of the
-// library, so that the call allocates no device memory.
-__device__ StreamDev g_noalloc_state;
+// library (file scope, 256-byte aligned, sizeof(StreamDev) bytes), so that
+// the call allocates no device memory.  Host code reaches it only through
+// the address cudaGetSymbolAddress returns (noalloc_setup).
+static __device__ __align__(256) StreamDev g_noalloc_state;
 
 // The totals and status of a no-alloc run, to the caller's buffers.
 __global__ void noalloc_out_kernel(const StreamDev* st, unsigned long long* totals, uint32_t* status) {
@@ -1033,6 +1045,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   a->trace = st->trace;
   a->trace_cap = st->trace_cap;
   a->trace_first = st->trace_next;
+  a->early = (st->cfg.flags & HIST_OVERLAP_PUSHES) ? 1u : 0u;
   for (uint32_t i = 0; i < count; ++i) {
     a->c[i].in = ins[i];
     a->c[i].n = (uint32_t)ns[i];
@@ -1103,7 +1116,8 @@ int push_chunks(hist_stream* st, uint32_t count, const uint8_t* const* ins, cons
 
 bool config_ok(const hist_config* c) {
   return c && c->budget >= HIST_BUDGET_MIN && c->budget <= HIST_BUDGET_MAX && c->theta_milli <= 1000 &&
-         c->mode <= HIST_MODE_ADAPTIVE && c->window >= 1 && c->window <= HIST_WINDOW_MAX;
+         c->mode <= HIST_MODE_ADAPTIVE && c->window >= 1 && c->window <= HIST_WINDOW_MAX &&
+         (c->flags & ~HIST_OVERLAP_PUSHES) == 0;
 }
 
 int grid_for(const hist_config* cfg, int sms, const void* fn, size_t smem) {

@@ -84,6 +84,8 @@ def _dev_lib():
         P, Z, U = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64
         l.synth_fill_device.argtypes = [P, Z, P, U, U, P]
         l.synth_fill_device.restype = ctypes.c_int
+        l.synth_fill_device_early.argtypes = [P, Z, P, U, U, P]
+        l.synth_fill_device_early.restype = ctypes.c_int
         l.synth_ramp_device.argtypes = [P, Z, U, P]
         l.synth_ramp_device.restype = ctypes.c_int
         _dev = l
@@ -172,6 +174,15 @@ def device_fill(ptr: int, n: int, thr, seed: int, counter0: int = 0, stream: int
     rc = _dev_lib().synth_fill_device(ptr, n, t.ctypes.data, seed, counter0, stream)
     if rc != 0:
         raise RuntimeError("synth_fill_device failed with CUDA error %d" % rc)
+
+
+def device_fill_early(ptr: int, n: int, thr, seed: int, counter0: int = 0, stream: int = 0) -> None:
+    """device_fill whose kernel lets the next kernel on the stream start early
+    (the case of a producer kernel that triggers its dependents at once)."""
+    t = np.ascontiguousarray(thr, dtype=np.uint64)
+    rc = _dev_lib().synth_fill_device_early(ptr, n, t.ctypes.data, seed, counter0, stream)
+    if rc != 0:
+        raise RuntimeError("synth_fill_device_early failed with CUDA error %d" % rc)
 
 
 def device_ramp(ptr: int, n: int, counter0: int = 0, stream: int = 0) -> None:

@@ -38,6 +38,13 @@ void synth_fill_host_mt(uint8_t* out, size_t n, const uint64_t thr[256], uint64_
 int synth_fill_device(uint8_t* d_out, size_t n, const uint64_t thr[256], uint64_t seed,
                       uint64_t counter0, void* stream);
 
+/* synth_fill_device whose kernel lets the next kernel on `stream` start
+ * early (griddepcontrol.launch_dependents at its start), as some library
+ * kernels do: a kernel launched next with programmatic stream serialisation
+ * may run while these bytes are written.  Same bytes. */
+int synth_fill_device_early(uint8_t* d_out, size_t n, const uint64_t thr[256], uint64_t seed,
+                            uint64_t counter0, void* stream);
+
 /* Device ramp: d_out[j] = (counter0 + j) mod 256. */
 int synth_ramp_device(uint8_t* d_out, size_t n, uint64_t counter0, void* stream);
 

@@ -28,7 +28,12 @@ __device__ __forceinline__ uint32_t pick(const unsigned long long* thr, uint64_t
   return lo;
 }
 
+template <bool EARLY>
 __global__ void fill_kernel(uint8_t* out, size_t n, Thr thr, uint64_t seed, uint64_t counter0) {
+  // EARLY: let a kernel launched after this one with programmatic stream
+  // serialisation start at once (as some library kernels do), so that it
+  // runs while these bytes are still being written
+  if (EARLY) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ unsigned long long t[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) t[i] = thr.v[i];
   __syncthreads();
@@ -70,7 +75,16 @@ extern "C" int synth_fill_device(uint8_t* d_out, size_t n, const uint64_t thr[25
   if (n == 0) return 0;
   Thr t;
   for (int i = 0; i < 256; ++i) t.v[i] = thr[i];
-  fill_kernel<<<grid_for((n + 15) / 16), 256, 0, (cudaStream_t)stream>>>(d_out, n, t, seed, counter0);
+  fill_kernel<false><<<grid_for((n + 15) / 16), 256, 0, (cudaStream_t)stream>>>(d_out, n, t, seed, counter0);
+  return (int)cudaGetLastError();
+}
+
+extern "C" int synth_fill_device_early(uint8_t* d_out, size_t n, const uint64_t thr[256], uint64_t seed,
+                                       uint64_t counter0, void* stream) {
+  if (n == 0) return 0;
+  Thr t;
+  for (int i = 0; i < 256; ++i) t.v[i] = thr[i];
+  fill_kernel<true><<<grid_for((n + 15) / 16), 256, 0, (cudaStream_t)stream>>>(d_out, n, t, seed, counter0);
   return (int)cudaGetLastError();
 }
 

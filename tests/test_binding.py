@@ -63,3 +63,18 @@ def test_chunk_tables_from_lists_and_arrays():
         hl._u64_array(np.zeros((2, 2), dtype=np.uint64), 2, "x")
     with pytest.raises(ValueError):
         hl._u64_array(np.zeros(4, dtype=np.float64), 4, "x")
+
+
+def test_chunk_tables_refuse_negative_and_byte_swapped_integers():
+    # a byte-swapped array would reach C with its addresses and sizes read
+    # the wrong way round; a negative int64 is no address or size
+    import numpy as np
+
+    with pytest.raises(ValueError):
+        hl._u64_array(np.array([1, 2], dtype=">i8"), 2, "x")
+    with pytest.raises(ValueError):
+        hl._u64_array(np.array([1, -2], dtype=np.int64), 2, "x")
+    with pytest.raises(ValueError):
+        hl._u64_array([3, -1], 2, "x")
+    addr, keep = hl._u64_array(np.array([7, 9], dtype="<u8"), 2, "x")
+    assert keep[1] == 9

@@ -119,6 +119,10 @@ def test_device_generator_matches_host():
         synth.device_fill(xd.data_ptr() + 3, n, thr, seed, c0, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert np.array_equal(xd[3:3 + n].cpu().numpy(), synth.host(n, thr, seed, c0))
+        xd.zero_()
+        synth.device_fill_early(xd.data_ptr() + 3, n, thr, seed, c0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(xd[3:3 + n].cpu().numpy(), synth.host(n, thr, seed, c0))
     xd = torch.empty(1000, dtype=torch.uint8, device="cuda")
     synth.device_ramp(xd.data_ptr(), 1000, 250, torch.cuda.current_stream().cuda_stream)
     assert np.array_equal(xd.cpu().numpy(), synth.host_ramp(1000, 250))

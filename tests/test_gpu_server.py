@@ -301,8 +301,13 @@ def test_bad_arguments():
 def test_full_size_serving_workload():
     """The serving workload at full size: 256 streams with 64 MiB regions
     (16 GiB of payloads), sizes 4 KiB .. 64 MiB, Poisson arrivals at 10k
-    requests/s, 32 GiB admission budget.  Every histogram sums to its
-    request's size; eight streams are checked against the oracle in full."""
+    requests/s, 32 GiB admission budget.  Every request's histogram and every
+    stream's end state are checked against StreamOracle fed that stream's
+    requests in order, counted from the workload's own bytes (each stream's
+    region copied back from the device) on every host core."""
+    import concurrent.futures as cf
+    import os
+
     streams, region = 256, 64 << 20
     laws = workloads.serving_streams(streams, region, seed=SEED)
     dev = torch.empty(streams * region + 16, dtype=torch.uint8, device="cuda")
@@ -320,16 +325,32 @@ def test_full_size_serving_workload():
     srv.replay(R, timeout_ms=300000)
     h = out.cpu().numpy().view(np.uint32)
     assert np.array_equal(h.sum(axis=1, dtype=np.uint64), np.array([r.n for r in reqs], np.uint64))
-    for s in (1, 50, 99, 128, 170, 200, 233, 255):
+    states = {s: srv.stream_state(s) for s in range(streams)}
+    srv.close()
+    by_stream = {}
+    for i, r in enumerate(reqs):
+        by_stream.setdefault(r.stream, []).append(i)
+
+    def check(s):
         law = laws[s]
-        host = synth.host(region, law.thr, SEED, law.counter0, threads=8)
+        host = dev[law.offset:law.offset + region].cpu().numpy()
         ref = oracle.StreamOracle(oracle.BUDGET_MAX)
         rec = None
-        for i, r in enumerate(reqs):
-            if r.stream != s:
-                continue
+        for i in by_stream.get(s, []):
+            r = reqs[i]
             rec = ref.push(host[r.offset - law.offset:r.offset - law.offset + r.n])
             assert np.array_equal(h[i], rec.hist), "stream %d request %d" % (s, i)
         if rec is not None:
-            _check_state(srv.stream_state(s), ref, rec)
-    srv.close()
+            _check_state(states[s], ref, rec)
+        else:
+            assert states[s].chunks == 0
+        return len(by_stream.get(s, []))
+
+    with cf.ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        checked = sum(ex.map(check, range(streams)))
+    assert checked == len(reqs)
+    # the generator's bytes are the oracle's own (host generator) on two streams
+    for s in (50, 200):
+        law = laws[s]
+        assert np.array_equal(dev[law.offset:law.offset + region].cpu().numpy(),
+                              synth.host(region, law.thr, SEED, law.counter0, threads=8))

@@ -98,13 +98,16 @@ def test_stream_batched_matches_step_by_step_and_outputs():
     st.close()
 
 
-@pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 8192), (hl.MODE_PLAIN, 8192), (hl.MODE_AUTO, 8192),
-                                         (hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 960)])
-def test_back_to_back_batches(mode, budget):
+@pytest.mark.parametrize("mode,budget,overlap", [(hl.MODE_ADAPTIVE, 8192, False), (hl.MODE_PLAIN, 8192, False),
+                                                 (hl.MODE_AUTO, 8192, False), (hl.MODE_ADAPTIVE, 960, False),
+                                                 (hl.MODE_AUTO, 960, False), (hl.MODE_ADAPTIVE, 8192, True),
+                                                 (hl.MODE_PLAIN, 8192, True)])
+def test_back_to_back_batches(mode, budget, overlap):
     """Many small push_many calls in a row on one stream, with empty and
     ragged chunks and a checkpoint in the middle: launches of the flat path
-    overlap their predecessors, so every chunk's output, the totals and the
-    state after every few calls must still match the oracle."""
+    start before their predecessors end (and with HIST_OVERLAP_PUSHES count
+    while they end), so every chunk's output, the totals and the state after
+    every few calls must still match the oracle."""
     rng = np.random.default_rng(11 + mode)
     sizes = [int(x) for x in rng.choice([0, 1, 15, 4096, 65_536, 300_001, 1 << 20], size=160)]
     chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 5, SEED + 20 + mode)
@@ -120,7 +123,7 @@ def test_back_to_back_batches(mode, budget):
         buf[o:o + ch.size] = ch
     bd = dev(buf)
     outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
-    st = hl.Stream(budget=budget, mode=mode)
+    st = hl.Stream(budget=budget, mode=mode, overlap=overlap)
     i = 0
     calls = 0
     while i < len(chunks):
@@ -139,6 +142,33 @@ def test_back_to_back_batches(mode, budget):
     for j, r in enumerate(recs):
         assert np.array_equal(got[j], r.hist), j
     _check_state(st.state(), ref, recs[-1])
+    st.close()
+
+
+@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
+def test_chunk_written_by_the_kernel_just_before_the_push(mode):
+    """A producer kernel writes each chunk on the push's CUDA stream right
+    before the push, and lets the next kernel start at once (as some library
+    kernels do).  Without HIST_OVERLAP_PUSHES the counting launch, which may
+    itself start early, reads no chunk byte before the producer has
+    completed: every chunk's histogram equals the oracle's count of the
+    bytes the producer wrote.  Each round writes different bytes into the
+    same buffer, so a read of the previous round's bytes would show."""
+    n = 64 << 20
+    buf = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+    out = torch.full((256,), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=mode)
+    ref = oracle.StreamOracle(8192, mode=mode)
+    cs = torch.cuda.current_stream().cuda_stream
+    laws = [synth.uniform(), synth.degenerate(90, 0.95), synth.normal(40, 6), synth.constant(200)]
+    for r in range(8):
+        thr = laws[r % len(laws)]
+        sz = n - 4096 * r
+        synth.device_fill_early(buf.data_ptr() + (r % 3), sz, thr, SEED + 900 + r, 0, cs)
+        st.push_ptr(buf.data_ptr() + (r % 3), sz, out.data_ptr())
+        rec = ref.push(synth.host(sz, thr, SEED + 900 + r, 0, threads=8))
+        assert np.array_equal(u32(out), rec.hist), "round %d" % r
+    _check_state(st.state(), ref, rec)
     st.close()
 
 

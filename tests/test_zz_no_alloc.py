@@ -7,8 +7,9 @@ device memory).  This entry point keeps its scratch in a fixed device array
 of the library instead.  The test calls it through the C ABI twice in a row
 -- the second call starts from the scratch the first one left behind -- and
 compares its per-chunk histograms and totals with those of the allocating
-stream API (hist_stream_create + hist_stream_push_many) on the same chunks.
-Both are exact integer results, so the comparison is bit for bit.
+stream API (hist_stream_create + hist_stream_push_many) on the same chunks,
+and both with the CPU oracle's stream (StreamOracle) fed the same bytes.
+All are exact integer results, so the comparisons are bit for bit.
 
 This file is collected last so that a run stopping at the first failure has
 run every other test first; it also passes alone in a fresh process.
@@ -19,6 +20,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +43,14 @@ def _chunks():
     buf = np.zeros(pos + 16, np.uint8)
     for o, h in zip(offs, host):
         buf[o:o + h.size] = h
-    return sizes, offs, torch.from_numpy(buf).cuda()
+    return sizes, offs, torch.from_numpy(buf).cuda(), host
+
+
+def _oracle_run(host, budget, mode, window):
+    """Per-chunk histograms and totals of the oracle's stream over the chunks."""
+    ref = oracle.StreamOracle(budget, mode=mode, window=window)
+    hists = np.stack([ref.push(h).hist for h in host])
+    return hists, ref.totals
 
 
 def _config(lib, abi, budget, mode, window=1):
@@ -58,7 +67,7 @@ def test_noalloc_matches_stream_api(cuda_ok, budget, mode, window):
 
     build.build()
     lib = _abi.load()
-    sizes, offs, dbuf = _chunks()
+    sizes, offs, dbuf, host = _chunks()
     count = len(sizes)
     ptrs = [dbuf.data_ptr() + o for o in offs]
     P = (ctypes.c_void_p * count)(*ptrs)
@@ -79,6 +88,9 @@ def test_noalloc_matches_stream_api(cuda_ok, budget, mode, window):
     ref_outs = ref_outs.cpu().numpy().view(np.uint32)
     ref_tot = ref_tot.cpu().numpy().view(np.uint64)
     assert int(ref_tot.sum()) == sum(sizes)
+    o_hists, o_tot = _oracle_run(host, budget, mode, window)
+    assert np.array_equal(ref_outs, o_hists), "stream API per-chunk histograms vs the oracle"
+    assert np.array_equal(ref_tot, o_tot), "stream API totals vs the oracle"
 
     # the entry point without allocation, twice in a row
     for call in range(2):
@@ -90,8 +102,12 @@ def test_noalloc_matches_stream_api(cuda_ok, budget, mode, window):
         assert rc == 0, "call %d returned %d" % (call, rc)
         torch.cuda.synchronize()
         assert int(status.item()) == 0
-        assert np.array_equal(outs.cpu().numpy().view(np.uint32), ref_outs), "per-chunk histograms, call %d" % call
-        assert np.array_equal(tot.cpu().numpy().view(np.uint64), ref_tot), "totals, call %d" % call
+        got_outs = outs.cpu().numpy().view(np.uint32)
+        got_tot = tot.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got_outs, ref_outs), "per-chunk histograms, call %d" % call
+        assert np.array_equal(got_tot, ref_tot), "totals, call %d" % call
+        assert np.array_equal(got_outs, o_hists), "per-chunk histograms vs the oracle, call %d" % call
+        assert np.array_equal(got_tot, o_tot), "totals vs the oracle, call %d" % call
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum(cuda_ok):
@@ -121,7 +137,7 @@ def test_noalloc_inside_a_cuda_graph_capture(cuda_ok):
 
     build.build()
     lib = _abi.load()
-    sizes, offs, dbuf = _chunks()
+    sizes, offs, dbuf, host = _chunks()
     count = len(sizes)
     P = (ctypes.c_void_p * count)(*[dbuf.data_ptr() + o for o in offs])
     Z = (ctypes.c_size_t * count)(*sizes)
@@ -149,6 +165,7 @@ def test_noalloc_inside_a_cuda_graph_capture(cuda_ok):
         rc = lib.hist_stream_run_noalloc(P, Z, count, ctypes.byref(cfg), outs.data_ptr(), tot.data_ptr(),
                                          status.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert rc == 0
+    o_hists, o_tot = _oracle_run(host, 8192, 0, 1)
     for _ in range(2):
         outs.fill_(-1)
         tot.fill_(-1)
@@ -157,3 +174,5 @@ def test_noalloc_inside_a_cuda_graph_capture(cuda_ok):
         assert int(status.item()) == 0
         assert torch.equal(outs, ref_outs)
         assert torch.equal(tot, ref_tot)
+        assert np.array_equal(outs.cpu().numpy().view(np.uint32), o_hists)
+        assert np.array_equal(tot.cpu().numpy().view(np.uint64), o_tot)
