@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
         l.oracle_binning_pattern.restype = ctypes.c_int
         l.oracle_pattern_layout.argtypes = [P, P]
         l.oracle_pattern_layout.restype = ctypes.c_uint32
+        l.oracle_batch_regime.argtypes = [P, ctypes.c_size_t, ctypes.c_uint32]
+        l.oracle_batch_regime.restype = ctypes.c_uint32
         _lib = l
     return _lib
 
@@ -176,6 +178,22 @@ def pattern_layout(log2k) -> tuple[np.ndarray, int]:
     off = np.zeros(BINS, np.uint16)
     used = lib().oracle_pattern_layout(lk.ctypes.data, off.ctypes.data)
     return off, int(used)
+
+
+# ------------------------------------------------------- batch regimes ----
+
+REGIME_SAMPLE = 4096
+REGIME_DEGENERATE = 0
+REGIME_PEAKED = 1
+REGIME_WIDE = 2
+
+
+def batch_regime(x, theta_milli: int = THETA_MILLI_DEFAULT) -> int:
+    """Distribution regime of an image for the batched call's autotuner (rule
+    in oracle.h: degeneracy of Sec. III.C on a fixed sample of at most 4096
+    pixels, then at most 64 effective bins = peaked, else wide)."""
+    a = _u8(x)
+    return int(lib().oracle_batch_regime(a.ctypes.data, a.size, theta_milli))
 
 
 # ---------------------------------------------------------------- stream ----

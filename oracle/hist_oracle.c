@@ -138,3 +138,20 @@ int oracle_binning_pattern(const uint32_t h[ORACLE_BINS], uint32_t budget, oracl
   p->used = oracle_pattern_layout(p->log2k, p->off);
   return 0;
 }
+
+/* The batched call's regime of an image (oracle.h states the rule). */
+uint32_t oracle_batch_regime(const uint8_t* x, size_t n, uint32_t theta_milli) {
+  if (n == 0) return ORACLE_REGIME_WIDE;
+  uint64_t m = n < ORACLE_REGIME_SAMPLE ? (uint64_t)n : ORACLE_REGIME_SAMPLE;
+  uint64_t h[ORACLE_BINS];
+  for (int b = 0; b < ORACLE_BINS; ++b) h[b] = 0;
+  for (uint64_t j = 0; j < m; ++j) h[x[(j * (uint64_t)n) / m]] += 1;
+  uint64_t mx = 0, sq = 0;
+  for (int b = 0; b < ORACLE_BINS; ++b) {
+    if (h[b] > mx) mx = h[b];
+    sq += h[b] * h[b];
+  }
+  if (mx * 1000u >= (uint64_t)theta_milli * m) return ORACLE_REGIME_DEGENERATE;
+  if (64u * sq >= m * m) return ORACLE_REGIME_PEAKED;
+  return ORACLE_REGIME_WIDE;
+}

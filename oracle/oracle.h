@@ -24,6 +24,12 @@
  *   oracle_binning_pattern              pinned by invariants, special cases and
  *                                       hand-worked examples; the paper states
  *                                       no formula, so the rule is a reading
+ *   oracle_batch_regime                 pinned by closed forms (constant, ramp,
+ *                                       cycles at the 64-bin boundary, normal
+ *                                       laws), the degeneracy boundary and a
+ *                                       case that fixes the sample positions;
+ *                                       no counterpart in the paper (the
+ *                                       batched call's autotuner)
  */
 #ifndef HIST_ORACLE_H
 #define HIST_ORACLE_H
@@ -91,6 +97,24 @@ int oracle_default_pattern(uint32_t budget, oracle_pattern* p);
  *   of k[b].
  * Returns 0, or -1 if budget is out of range. */
 int oracle_binning_pattern(const uint32_t h[ORACLE_BINS], uint32_t budget, oracle_pattern* p);
+
+/* Distribution regime of one image of a batched call, from a sample (the
+ * batch autotuner keeps one setting per regime; the paper has no such
+ * classifier -- only its first test is the paper's, the degeneracy of
+ * Sec. III.C):
+ *   m = min(n, ORACLE_REGIME_SAMPLE); the sample is the m pixels
+ *   x[floor(j * n / m)], j = 0 .. m-1 (every pixel when n <= 4096); h its
+ *   256-bin histogram.
+ *   ORACLE_REGIME_DEGENERATE  max_b h[b] * 1000 >= theta_milli * m
+ *   ORACLE_REGIME_PEAKED      otherwise, 64 * sum_b h[b]^2 >= m^2: the chance
+ *                             that two sampled pixels are equal is at least
+ *                             1/64 (at most 64 "effective" bins)
+ *   ORACLE_REGIME_WIDE        otherwise, and for an empty image. */
+#define ORACLE_REGIME_SAMPLE 4096u
+#define ORACLE_REGIME_DEGENERATE 0u
+#define ORACLE_REGIME_PEAKED 1u
+#define ORACLE_REGIME_WIDE 2u
+uint32_t oracle_batch_regime(const uint8_t* x, size_t n, uint32_t theta_milli);
 
 /* Offsets for given sub-bin counts (the layout step of the two functions
  * above).  log2k[b] in 0..5.  Returns the number of slots used. */

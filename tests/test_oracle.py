@@ -543,3 +543,88 @@ def test_change_after_a_phase_change():
         flags.append(oracle.change(st.totals, st.mw, 250))
     assert flags[:20] == [0] * 20
     assert all(flags[21:])
+
+
+# ------------------------------------------------- batch regime classifier ----
+# The batched call's autotuner keeps one setting per distribution regime; the
+# regime of an image comes from a fixed sample (oracle.h).  Pinned by
+# hand-worked closed forms, not by restating the rule.
+
+def test_regime_constant_and_empty_images():
+    for n in (1, 100, 4096, 4097, 1 << 20):
+        assert oracle.batch_regime(np.full(n, 201, np.uint8)) == oracle.REGIME_DEGENERATE, n
+    assert oracle.batch_regime(np.zeros(0, np.uint8)) == oracle.REGIME_WIDE
+
+
+def test_regime_ramp_is_wide():
+    # a ramp sampled at 4096 points: every value about equally often (16 each at n = 4096)
+    for n in (256, 4096, 10 ** 6):
+        x = (np.arange(n) % 256).astype(np.uint8)
+        assert oracle.batch_regime(x) == oracle.REGIME_WIDE, n
+
+
+def test_regime_effective_bins_boundary():
+    # n = 4096, x = i mod 64: 64 values x 64 pixels, sum h^2 = 64 * 64^2, so
+    # 64 * sum h^2 = 4096^2 exactly: peaked (the bound is inclusive)
+    x = (np.arange(4096) % 64).astype(np.uint8)
+    assert oracle.batch_regime(x) == oracle.REGIME_PEAKED
+    # x = i mod 65: 4096 = 65 * 63 + 1, one value 64 times and 64 values 63
+    # times: 64 * (64^2 + 64 * 63^2) = 16,519,168 < 4096^2: wide
+    x = (np.arange(4096) % 65).astype(np.uint8)
+    assert oracle.batch_regime(x) == oracle.REGIME_WIDE
+    # 32 values: far inside
+    x = (np.arange(4096) % 32).astype(np.uint8)
+    assert oracle.batch_regime(x) == oracle.REGIME_PEAKED
+
+
+def test_regime_degeneracy_boundary():
+    # n = 1000 (the whole image is the sample): 450 pixels of value 9 reach
+    # 450 per mille exactly; 449 do not (and leave a peaked image: 449^2 * 64 > 1000^2)
+    rest = np.array([v for v in range(256) if v != 9] * 3, np.uint8)
+    for k, want in ((450, oracle.REGIME_DEGENERATE), (449, oracle.REGIME_PEAKED)):
+        x = np.concatenate([np.full(k, 9, np.uint8), rest[:1000 - k]])
+        assert x.size == 1000
+        assert oracle.batch_regime(x) == want, k
+    # the threshold is the switch's theta: 0 makes every image degenerate,
+    # 1000 only a constant sample
+    x = (np.arange(4096) % 256).astype(np.uint8)
+    assert oracle.batch_regime(x, theta_milli=0) == oracle.REGIME_DEGENERATE
+    x = np.concatenate([np.full(4095, 3, np.uint8), np.full(1, 4, np.uint8)])
+    assert oracle.batch_regime(x, theta_milli=1000) == oracle.REGIME_PEAKED
+    assert oracle.batch_regime(x, theta_milli=999) == oracle.REGIME_DEGENERATE
+
+
+def _interleaved(n, const_pos, period):
+    """Value 7 where i mod period == const_pos, a ramp elsewhere."""
+    i = np.arange(n)
+    x = (i % 256).astype(np.uint8)
+    x[i % period == const_pos] = 7
+    x[(i % period != const_pos) & (x == 7)] = 8
+    return x
+
+
+def test_regime_sample_positions():
+    # n = 8192: the sample is x[floor(j * 8192 / 4096)] = x[2 j], the even pixels
+    x = _interleaved(8192, 1, 2)  # odd pixels 7: the whole image is half 7
+    assert oracle.batch_regime(x) == oracle.REGIME_WIDE
+    x = _interleaved(8192, 0, 2)
+    assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
+    # n = 8191: floor(j * 8191 / 4096) = 2 j - 1 for j >= 1: the odd pixels
+    x = _interleaved(8191, 1, 2)
+    assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
+    x = _interleaved(8191, 0, 2)
+    assert oracle.batch_regime(x) == oracle.REGIME_WIDE
+    # n = 12288: the sample is x[3 j]; the pixels with i mod 6 == 3 are half
+    # of it (a sample of 2048 would see none of them)
+    x = _interleaved(12288, 3, 6)
+    assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
+
+
+def test_regime_of_the_benchmark_laws():
+    # N(128, 4): about 14 effective bins (1 / sum p^2 = 2 sigma sqrt(pi)); N(100, 40):
+    # about 142; uniform: 256; the 95 % mixture of the degenerate stream
+    n = 1 << 20
+    cases = ((synth.normal(128, 4), oracle.REGIME_PEAKED), (synth.normal(100, 40), oracle.REGIME_WIDE),
+             (synth.uniform(), oracle.REGIME_WIDE), (synth.degenerate(90, 0.95), oracle.REGIME_DEGENERATE))
+    for t, (thr, want) in enumerate(cases):
+        assert oracle.batch_regime(synth.host(n, thr, SEED + 300 + t)) == want, t

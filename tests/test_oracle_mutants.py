@@ -51,6 +51,14 @@ MUTANTS = [
      "if (total == 0) total = 1;"),
     ("budget range", "if (budget < ORACLE_BUDGET_MIN || budget > ORACLE_BUDGET_MAX) return -1;\n  uint64_t total",
      "if (budget < ORACLE_BUDGET_MIN) return -1;\n  uint64_t total"),
+    ("regime sample rounds up", "h[x[(j * (uint64_t)n) / m]] += 1;", "h[x[(j * (uint64_t)n + m - 1) / m]] += 1;"),
+    ("regime sample of 2048", "uint64_t m = n < ORACLE_REGIME_SAMPLE ? (uint64_t)n : ORACLE_REGIME_SAMPLE;",
+     "uint64_t m = n < 2048 ? (uint64_t)n : 2048;"),
+    ("regime degeneracy strict", "if (mx * 1000u >= (uint64_t)theta_milli * m)", "if (mx * 1000u > (uint64_t)theta_milli * m)"),
+    ("regime peaked strict", "if (64u * sq >= m * m)", "if (64u * sq > m * m)"),
+    ("regime 32 effective bins", "if (64u * sq >= m * m)", "if (32u * sq >= m * m)"),
+    ("regime squares dropped", "sq += h[b] * h[b];", "sq += h[b];"),
+    ("regime empty is degenerate", "if (n == 0) return ORACLE_REGIME_WIDE;", "if (n == 0) return ORACLE_REGIME_DEGENERATE;"),
 ]
 
 
