@@ -65,6 +65,9 @@ def workload_config(chunks):
         "chunks": chunks,
         "budget": 8192,
         "theta_milli": 450,
+        "pushes": "HIST_OVERLAP_PUSHES: the chunks are resident and complete before the timed region, so a "
+                  "push's counting launch may start reading while the previous push finishes (without the "
+                  "flag a launch reads nothing before the work before it completes: extras.adaptive_stream_default_gbs)",
         "l2": "inputs larger than L2 (1 GiB vs 129 MB); no flush needed" if chunks * CHUNK > 256 * MiB
         else "inputs smaller than 2x L2: numbers include L2 reuse",
     }
@@ -372,11 +375,62 @@ def batch_extras(torch, hl, synth, hbm, steps, autotune=True):
     e5 = time_steps(torch, lambda: _abi.check("hist_batch_graph_launch", lib.hist_batch_graph_launch(
         gexec, torch.cuda.current_stream().cuda_stream)), 2 if autotune else 0, steps)
     lib.hist_batch_graph_destroy(gexec)
-    return {"batch_images": len(images), "batch_bytes": bbytes,
-            "batch_graph_gbs": round(bbytes * steps / e5 / 1e9, 2),
-            "batch_frac_of_hbm": round(bbytes * steps / e5 / 1e9 / hbm, 4),
-            "batch_tuning": {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll,
-                             "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}}
+    out = {"batch_images": len(images), "batch_bytes": bbytes,
+           "batch_graph_gbs": round(bbytes * steps / e5 / 1e9, 2),
+           "batch_frac_of_hbm": round(bbytes * steps / e5 / 1e9 / hbm, 4),
+           "batch_tuning": {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll,
+                            "small_bytes": best.small_bytes, "small_log2k": best.small_log2k}}
+    if autotune:
+        out["batch_regimes"] = regime_extras(torch, lib, _abi, images, bbuf, bptrs, bsizes, bout, hbm, steps)
+        # the same batch with a third of the images given the degenerate law
+        for k, im in enumerate(images):
+            if k % 3 == 0:
+                synth.device_fill(bbuf.data_ptr() + im.offset, im.n, synth.degenerate(90, 0.95), synth.SEED_BASE + 4,
+                                  im.counter0, sq)
+        torch.cuda.synchronize()
+        out["batch_regimes_with_degenerate_third"] = regime_extras(torch, lib, _abi, images, bbuf, bptrs, bsizes,
+                                                                   bout, hbm, steps)
+    return out
+
+
+def regime_extras(torch, lib, _abi, images, bbuf, bptrs, bsizes, bout, hbm, steps):
+    """The batch tuned per distribution regime: the table the autotuner picks,
+    each regime's images alone with that setting and with the default full
+    table, and the whole batch as one graph (classification + counting)."""
+    import ctypes
+    names = ("degenerate", "peaked", "wide")
+    reg = torch.empty(len(images), dtype=torch.uint8, device="cuda")
+    best = _abi.BatchTable()
+    lib.hist_batch_table_init(ctypes.byref(best))
+    rep = _abi.RegimeReport()
+    _abi.check("hist_batch_autotune_regimes", lib.hist_batch_autotune_regimes(
+        bptrs.data_ptr(), bsizes.data_ptr(), len(images), bout.data_ptr(), reg.data_ptr(), 2, ctypes.byref(best),
+        ctypes.byref(rep)))
+
+    def lay(v):
+        return "per_warp" if v == _abi.LAYOUT_PER_WARP else "k=%d" % (1 << v)
+
+    table = {}
+    for r, nm in enumerate(names):
+        st = best.regime[r]
+        b = rep.bytes[r]
+        table[nm] = {"images": rep.images[r], "bytes": b, "layout": lay(st.layout),
+                     "small_bytes": st.small_bytes, "small_layout": lay(st.small_layout) if st.small_bytes else None,
+                     "gbs": round(b / rep.ms[r] / 1e6, 1) if rep.ms[r] > 0 else None,
+                     "default_full_table_gbs": round(b / rep.ms_default[r] / 1e6, 1) if rep.ms_default[r] > 0 else None}
+    bbytes = sum(im.n for im in images)
+    g = ctypes.c_void_p()
+    _abi.check("hist_batch_regimes_capture", lib.hist_batch_regimes_capture(
+        bptrs.data_ptr(), bsizes.data_ptr(), len(images), bout.data_ptr(), reg.data_ptr(), ctypes.byref(best),
+        ctypes.byref(g)))
+    el = time_steps(torch, lambda: _abi.check("hist_batch_graph_launch", lib.hist_batch_graph_launch(
+        g, torch.cuda.current_stream().cuda_stream)), 2, steps)
+    lib.hist_batch_graph_destroy(g)
+    return {"ctas_per_sm": best.ctas_per_sm, "unroll": best.unroll, "candidates_per_regime": rep.candidates,
+            "regimes": table, "graph_gbs": round(bbytes * steps / el / 1e9, 2),
+            "graph_frac_of_hbm": round(bbytes * steps / el / 1e9 / hbm, 4),
+            "autotuner_batch_gbs": round(bbytes / rep.batch_ms / 1e6, 1),
+            "autotuner_default_table_gbs": round(bbytes / rep.batch_default_ms / 1e6, 1)}
 
 
 def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
@@ -519,6 +573,44 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
 
 # ---------------------------------------------------------- reference ----
 
+def summary_of(ex, value, hbm):
+    """The figures the extras are read for, last in the line (a reader of its
+    tail sees them): fractions are of the measured HBM copy bandwidth."""
+    def g(*path):
+        d = ex
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    sm = {"hbm_gbs": hbm, "adaptive_stream_gbs": round(value, 1), "adaptive_frac": round(value / hbm, 4),
+          "adaptive_stream_default_gbs": g("adaptive_stream_default_gbs"),
+          "plain_stream_gbs": g("plain_stream_gbs"), "plain_stream_default_gbs": g("plain_stream_default_gbs")}
+    ad, pl, au = g("degenerate_adaptive_gbs"), g("degenerate_plain_gbs"), g("degenerate_auto_gbs")
+    if ad and pl:
+        sm["degenerate_gbs"] = {"adaptive": ad, "plain": pl, "auto": au, "auto_window32": g("degenerate_auto_window32_gbs"),
+                                "adaptive_over_plain": round(ad / pl, 2),
+                                "note": "3x would need %.0f GB/s, above the HBM copy peak: same-bin increments of "
+                                        "the per-warp kernel are not serialised on this GPU" % (3 * pl)}
+    sm["table2_plain_gbs"] = dict(zip(g("table2", "inputs") or [], g("table2", "plain_gbs") or []))
+    sm["batch_graph_gbs"] = g("batch_graph_gbs")
+    sm["batch_regimes_graph_gbs"] = g("batch_regimes", "graph_gbs")
+    cs = g("stream_chunk_sizes")
+    if cs:
+        sm["chunk_kib"] = cs.get("chunk_kib")
+        sm["adaptive_by_chunk_gbs"] = cs.get("adaptive_stream_gbs")
+        sm["launch_us_1024x16B"] = cs.get("launch_us_1024x16B")
+    sb = g("stream_budgets")
+    if sb:
+        sm["budgets"] = sb.get("budgets")
+        sm["adaptive_by_budget_frac"] = [round(v / hbm, 3) for v in sb.get("adaptive_stream_gbs", [])]
+    sv = g("serving")
+    if sv:
+        sm["serving"] = {k: {"gbs": v.get("served_gbs"), "p50_us": v.get("p50_us"), "p99_us": v.get("p99_us")}
+                         for k, v in sv.items() if isinstance(v, dict) and "served_gbs" in v}
+    return sm
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
@@ -653,7 +745,7 @@ def run_native(args):
             st.flush()
         return step
 
-    st_ad = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE)
+    st_ad = hl.Stream(budget=8192, mode=hl.MODE_ADAPTIVE, overlap=True)
     sampler = ClockSampler(local)
     step = stream_step(st_ad)
     if not args.profile:
@@ -691,19 +783,26 @@ def run_native(args):
 
     if not args.profile:
         # plain kernel on the same stream of data
-        st_pl = hl.Stream(budget=8192, mode=hl.MODE_PLAIN)
+        st_pl = hl.Stream(budget=8192, mode=hl.MODE_PLAIN, overlap=True)
         el_pl = time_steps(torch, stream_step(st_pl), args.warmup, args.steps, barrier)
         extras["plain_stream_gbs"] = round(world * nbytes * args.steps / el_pl / 1e9, 2)
         extras["adaptive_stream_gbs"] = round(value, 2)
         extras["adaptive_frac_of_hbm"] = round(value / world / hbm, 4)
         extras["plain_frac_of_hbm"] = round(extras["plain_stream_gbs"] / world / hbm, 4)
+        # the same streams without HIST_OVERLAP_PUSHES (the library's default:
+        # each launch reads its chunks only after the work before it completes)
+        for name, mode in (("adaptive", hl.MODE_ADAPTIVE), ("plain", hl.MODE_PLAIN)):
+            sd = hl.Stream(budget=8192, mode=mode)
+            eld = time_steps(torch, stream_step(sd), args.warmup, args.steps, barrier)
+            extras["%s_stream_default_gbs" % name] = round(world * nbytes * args.steps / eld / 1e9, 2)
+            sd.close()
         # degenerate workload: 95 % = 90 + 5 % uniform, switching to uniform every 8 chunks
         xdg = gen_workload_device(torch, synth, chunks, synth.SEED_BASE + 3,
                                   lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform())
         pd = [xdg.data_ptr() + c * CHUNK for c in range(chunks)]
         for name, mode, window in (("auto", hl.MODE_AUTO, 1), ("plain", hl.MODE_PLAIN, 1),
                                    ("adaptive", hl.MODE_ADAPTIVE, 1), ("auto_window32", hl.MODE_AUTO, 32)):
-            s2 = hl.Stream(budget=8192, mode=mode, window=window)
+            s2 = hl.Stream(budget=8192, mode=mode, window=window, overlap=True)
 
             def st2(s2=s2):
                 s2.push_many(pd, sizes)
@@ -711,6 +810,18 @@ def run_native(args):
             e2 = time_steps(torch, st2, args.warmup, args.steps, barrier)
             extras["degenerate_%s_gbs" % name] = round(world * nbytes * args.steps / e2 / 1e9, 2)
             s2.close()
+        # the adaptive stream below the full table on the same data
+        row = []
+        for b in (960, 2048, 4096):
+            s3 = hl.Stream(budget=b, mode=hl.MODE_ADAPTIVE)
+
+            def st3(s3=s3):
+                s3.push_many(pd, sizes)
+            e5 = time_steps(torch, st3, 2, 10)
+            row.append(round(nbytes * 10 / e5 / 1e9, 2))
+            s3.close()
+        extras["stream_budgets_degenerate"] = {"budgets": [960, 2048, 4096], "adaptive_stream_gbs": row,
+                                               "frac_of_hbm": [round(v / hbm, 4) for v in row]}
         del xdg
         extras.update(batch_extras(torch, hl, synth, hbm, steps=max(3, min(args.steps, 10))))
         extras["serving"] = serving_extras(torch, np, hl, synth, hbm)
@@ -751,6 +862,7 @@ def run_native(args):
             e6 = time_steps(torch, lambda: hl.hist_adaptive(x, pb, o), 2, 10)
             row.append(round(nbytes * 10 / e6 / 1e9, 2))
         sb["oneshot_adaptive_gbs"] = row
+        sb["adaptive_frac_of_hbm"] = [round(v / hbm, 4) for v in sb["adaptive_stream_gbs"]]
         extras["stream_budgets"] = sb
         # the same 1 GiB pushed as smaller chunks (one push_many per GiB):
         # the fixed cost per launch and per chunk against the bytes
@@ -761,7 +873,7 @@ def run_native(args):
                 k = nbytes // (kib << 10)
                 cp = x.data_ptr() + np.arange(k, dtype=np.uint64) * np.uint64(kib << 10)
                 cz = np.full(k, kib << 10, dtype=np.uint64)
-                s4 = hl.Stream(budget=8192, mode=mode)
+                s4 = hl.Stream(budget=8192, mode=mode, overlap=True)
 
                 def st4(s4=s4, cp=cp, cz=cz):
                     s4.push_many(cp, cz)
@@ -772,7 +884,7 @@ def run_native(args):
             # the fixed cost: one launch of 1024 chunks of 16 bytes
             tp = x.data_ptr() + np.arange(1024, dtype=np.uint64) * np.uint64(4096)
             tz = np.full(1024, 16, dtype=np.uint64)
-            s5 = hl.Stream(budget=8192, mode=mode)
+            s5 = hl.Stream(budget=8192, mode=mode, overlap=True)
             e8 = time_steps(torch, lambda: s5.push_many(tp, tz), 3, 20)
             cs.setdefault("launch_us_1024x16B", {})[name] = round(e8 / 20 * 1e6, 1)
             s5.close()
@@ -839,6 +951,9 @@ def run_native(args):
             "value": round(trate, 3), "unit": UNIT, "cores": threads, "kind": "oracle counting loop per thread",
             "sample": "the first %d chunks (%d MiB), split into %d contiguous slices, repeated for %.1f s (%d MiB)"
                       % (sample, sample * 16, threads, tsecs, tdone // MiB)}
+
+    if extras and not args.profile:
+        extras["summary"] = summary_of(extras, value, hbm)
 
     if rank == 0:
         out = {

@@ -358,6 +358,96 @@ int hist_batch_graph_destroy(hist_batch_graph* graph);
 int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
                         uint32_t repeats, hist_batch_tuning* best, float* best_ms);
 
+/* Batches tuned per distribution regime.  The autotuner keeps one setting
+ * per regime of image (the paper has no autotuner: Sec. III.B batches small
+ * slices into one call, and Sec. III.C chooses a kernel by degeneracy; the
+ * regimes extend that choice to the batched call).  An image's regime comes
+ * from a fixed sample of it:
+ *   m = min(n, HIST_REGIME_SAMPLE); the sample is the m pixels
+ *   x[floor(j n / m)], j = 0 .. m-1 (every pixel of an image of at most 4096);
+ *   h is its 256-bin histogram.
+ *   HIST_REGIME_DEGENERATE  max h * 1000 >= theta_milli * m (Sec. III.C's test)
+ *   HIST_REGIME_PEAKED      otherwise, 64 * sum h^2 >= m^2: two sampled pixels
+ *                           are equal with a chance of at least 1/64
+ *   HIST_REGIME_WIDE        otherwise, and an empty image.
+ * A setting names the layout an image of the regime is counted with: a
+ * shift layout with 2^layout sub-bins per bin (0..5; 5 = the lane-private
+ * table) or HIST_LAYOUT_PER_WARP (one 256-bin table per warp, the NVHist
+ * layout), with a second layout for the regime's images below small_bytes
+ * (whose table is cleared and reduced for few pixels).  Every layout gives
+ * the exact histogram; the setting changes speed only. */
+#define HIST_REGIMES 3u
+#define HIST_REGIME_DEGENERATE 0u
+#define HIST_REGIME_PEAKED 1u
+#define HIST_REGIME_WIDE 2u
+#define HIST_REGIME_SAMPLE 4096u
+#define HIST_LAYOUT_PER_WARP 6u
+
+typedef struct hist_regime_setting {
+  uint32_t layout;       /* 0..5 or HIST_LAYOUT_PER_WARP */
+  uint32_t small_bytes;  /* images of the regime below this size use small_layout (0: none) */
+  uint32_t small_layout; /* 0..5 or HIST_LAYOUT_PER_WARP */
+  uint32_t reserved;
+} hist_regime_setting;
+
+typedef struct hist_batch_table {
+  uint32_t ctas_per_sm; /* 1 or 2, for the whole launch (default 2) */
+  uint32_t unroll;      /* 2 or 4 loads in flight per thread (4 needs ctas_per_sm 1; default 2) */
+  uint32_t theta_milli; /* the classifier's degeneracy threshold, 0..1000 (default 450) */
+  uint32_t reserved;
+  hist_regime_setting regime[HIST_REGIMES]; /* default: layout 5 for every regime, no small cut */
+} hist_batch_table;
+
+void hist_batch_table_init(hist_batch_table* t);
+
+/* The regime of each image (rule above): d_regime is a device array of
+ * `count` bytes, overwritten.  One kernel (a CTA per image, 4096 sampled
+ * bytes at most).  theta_milli > 1000 or null arrays with count > 0 ->
+ * HIST_EINVAL. */
+int hist_batch_classify(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t theta_milli,
+                        uint8_t* d_regime, hist_cuda_stream s);
+
+/* hist_batch with a per-regime table: a memset of d_out, hist_batch_classify
+ * into d_regime (count bytes on the device, the caller's; the regimes stay
+ * there), then one counting kernel per HIST_BATCH_MAX_IMAGES images in which
+ * each image is counted with its regime's setting.  No other device memory.
+ * table null = hist_batch_table_init.  HIST_EINVAL for a bad table. */
+int hist_batch_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                       uint8_t* d_regime, const hist_batch_table* table, hist_cuda_stream s);
+
+/* The same as an instantiated CUDA graph (memset, classification, counting),
+ * destroyed with hist_batch_graph_destroy. */
+int hist_batch_regimes_capture(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count,
+                               uint32_t* d_out, uint8_t* d_regime, const hist_batch_table* table,
+                               hist_batch_graph** graph);
+
+/* What hist_batch_autotune_regimes measured (milliseconds, CUDA events,
+ * mean of the repeats). */
+typedef struct hist_regime_report {
+  uint32_t images[HIST_REGIMES];      /* images of each regime */
+  uint32_t candidates;                /* settings timed per regime */
+  uint64_t bytes[HIST_REGIMES];       /* their bytes */
+  float ms[HIST_REGIMES];             /* the regime's images alone, chosen setting */
+  float ms_default[HIST_REGIMES];     /* the same images, the default setting (layout 5) */
+  float batch_ms;                     /* the whole batch, chosen table */
+  float batch_default_ms;             /* the whole batch, hist_batch_table_init */
+  uint32_t reserved[4];
+} hist_regime_report;
+
+/* Autotuner, one setting per regime: classifies the batch (into d_regime),
+ * then for each regime times every candidate setting (layouts per-warp and
+ * 0..5, each with no small cut or a small cut at 64 KiB / 1 MiB with a
+ * smaller layout) on that regime's images alone, `repeats` times each, and
+ * keeps the fastest; then times the whole batch with the chosen settings
+ * for each launch shape (CTAs per SM, loads in flight) and keeps the
+ * fastest.  Synchronous; allocates temporary device arrays for the
+ * sub-batches (freed before it returns).  Writes the table to *best and the
+ * times to *report (may be null); d_out receives the batch's histograms
+ * under the chosen table.  repeats 0 = 3. */
+int hist_batch_autotune_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count,
+                                uint32_t* d_out, uint8_t* d_regime, uint32_t repeats, hist_batch_table* best,
+                                hist_regime_report* report);
+
 /* ------------------------------------------------ stream without allocation -- */
 /* The paper has no counterpart of this call: it serves callers that cannot
  * allocate device memory where they need histograms -- code running while a

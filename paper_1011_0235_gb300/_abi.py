@@ -91,6 +91,45 @@ class BatchTuning(ctypes.Structure):
     ]
 
 
+HIST_REGIMES = 3
+REGIME_DEGENERATE = 0
+REGIME_PEAKED = 1
+REGIME_WIDE = 2
+LAYOUT_PER_WARP = 6
+
+
+class RegimeSetting(ctypes.Structure):
+    _fields_ = [
+        ("layout", ctypes.c_uint32),
+        ("small_bytes", ctypes.c_uint32),
+        ("small_layout", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+class BatchTable(ctypes.Structure):
+    _fields_ = [
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("unroll", ctypes.c_uint32),
+        ("theta_milli", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("regime", RegimeSetting * HIST_REGIMES),
+    ]
+
+
+class RegimeReport(ctypes.Structure):
+    _fields_ = [
+        ("images", ctypes.c_uint32 * HIST_REGIMES),
+        ("candidates", ctypes.c_uint32),
+        ("bytes", ctypes.c_uint64 * HIST_REGIMES),
+        ("ms", ctypes.c_float * HIST_REGIMES),
+        ("ms_default", ctypes.c_float * HIST_REGIMES),
+        ("batch_ms", ctypes.c_float),
+        ("batch_default_ms", ctypes.c_float),
+        ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
 class StreamState(ctypes.Structure):
     _fields_ = [
         ("totals", ctypes.c_uint64 * BINS),
@@ -199,6 +238,12 @@ SIGNATURES = [
     ("hist_batch_graph_launch", _I, [_P, _P]),
     ("hist_batch_graph_destroy", _I, [_P]),
     ("hist_batch_autotune", _I, [_P, _P, _U32, _P, _U32, ctypes.POINTER(BatchTuning), ctypes.POINTER(ctypes.c_float)]),
+    ("hist_batch_table_init", None, [ctypes.POINTER(BatchTable)]),
+    ("hist_batch_classify", _I, [_P, _P, _U32, _U32, _P, _P]),
+    ("hist_batch_regimes", _I, [_P, _P, _U32, _P, _P, ctypes.POINTER(BatchTable), _P]),
+    ("hist_batch_regimes_capture", _I, [_P, _P, _U32, _P, _P, ctypes.POINTER(BatchTable), ctypes.POINTER(_P)]),
+    ("hist_batch_autotune_regimes", _I, [_P, _P, _U32, _P, _P, _U32, ctypes.POINTER(BatchTable),
+                                         ctypes.POINTER(RegimeReport)]),
     ("hist_change", _I, [_P, _P, _U32, _P, _P]),
     ("hist_stream_change", _I, [_P, _U32, _P, _P]),
     ("hist_ablation_grid", _I, [_Z]),

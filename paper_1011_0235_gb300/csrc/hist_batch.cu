@@ -28,14 +28,23 @@ constexpr uint32_t kBatchMaxImages = HIST_BATCH_MAX_IMAGES;
 // dynamic shared memory: the table, then the size prefix (u64 per image + 1)
 constexpr size_t kBatchSmem = (size_t)kTableWords * 4 + (size_t)(kBatchMaxImages + 1) * 8;
 
+constexpr uint32_t kPerWarp = HIST_LAYOUT_PER_WARP;
+
+// The layout of an image: per regime (index 0 for every image when the
+// launch has no regimes) a layout, and a second one below a size.
+struct RegimeLayouts {
+  uint32_t layout[HIST_REGIMES];
+  uint32_t small_bytes[HIST_REGIMES];
+  uint32_t small_layout[HIST_REGIMES];
+};
+
 struct BatchImgArgs {
   const uint8_t* const* ptrs;
   const size_t* sizes;
   uint32_t* out;
+  const uint8_t* regime;  // per image, or null: every image takes entry 0
   uint32_t count;
-  uint32_t small_bytes;  // images below this size use small_lk
-  uint32_t small_lk;
-  uint32_t large_lk;
+  RegimeLayouts lay;
 };
 
 // Exclusive prefix of the image sizes into pre[0..count] (all threads).
@@ -100,17 +109,24 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgAr
     const size_t off = (size_t)(lo - pre[i]);
     const size_t len = (size_t)(seg_end - lo);
     const uint8_t* base = a.ptrs[i] + off;
-    const int lk = a.sizes[i] < a.small_bytes ? (int)a.small_lk : (int)a.large_lk;
+    const uint32_t r = a.regime ? a.regime[i] : 0u;
+    // selects rather than an index, so the parameters stay out of local memory
+    const uint32_t big = r == 0 ? a.lay.layout[0] : (r == 1 ? a.lay.layout[1] : a.lay.layout[2]);
+    const uint32_t cut = r == 0 ? a.lay.small_bytes[0] : (r == 1 ? a.lay.small_bytes[1] : a.lay.small_bytes[2]);
+    const uint32_t sml = r == 0 ? a.lay.small_layout[0] : (r == 1 ? a.lay.small_layout[1] : a.lay.small_layout[2]);
+    const uint32_t lay = a.sizes[i] < cut ? sml : big;
+    const int path = lay == kPerWarp ? PATH_PLAIN : PATH_SHIFT;
+    const int lk = lay == kPerWarp ? 0 : (int)(lay > 5u ? 5u : lay);
     const Split sp = split_bytes(base, len);
-    count_range_dispatch<UNROLL>(PATH_SHIFT, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table,
+    count_range_dispatch<UNROLL>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table,
                                  part, threadIdx.x, blockDim.x);
-    flush_table(PATH_SHIFT, lk, table, cs.pat, part, cs);  // the pattern is not read for SHIFT
+    flush_table(path, lk, table, cs.pat, part, cs);  // the pattern is not read for SHIFT or PLAIN
     count_edges(base, sp, cs);
     __syncthreads();
     if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x])
       atomicAdd(a.out + (size_t)i * HIST_BINS + threadIdx.x, cs.res[threadIdx.x]);
-    // clear the slots this layout used
-    const int words = HIST_BINS << lk;
+    // clear the slots this layout used (the per-warp tables fill the table)
+    const int words = path == PATH_PLAIN ? kTableWords : (HIST_BINS << lk);
     uint4* t4 = reinterpret_cast<uint4*>(table);
     for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -119,8 +135,82 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgAr
   }
 }
 
-int launch_batch_images(const hist_batch_tuning& tu, const uint8_t* const* d_ptrs, const size_t* d_sizes,
-                        uint32_t count, uint32_t* d_out, cudaStream_t s) {
+// The regime of image blockIdx.x (rule in hist.h): 256 threads, the sample
+// of m = min(n, 4096) pixels x[floor(j n / m)] -- j when n <= 4096, else
+// (j n) >> 12, so no division -- counted in shared memory, then the largest
+// bin and the sum of squares (below 2^25: m <= 4096).
+__global__ void __launch_bounds__(HIST_BINS) regime_kernel(const uint8_t* const* ptrs, const size_t* sizes,
+                                                           uint32_t theta, uint8_t* regime) {
+  __shared__ uint32_t h[HIST_BINS];
+  __shared__ uint32_t wmax[HIST_BINS / 32], wsq[HIST_BINS / 32];
+  const int t = threadIdx.x;
+  const uint32_t i = blockIdx.x;
+  const unsigned long long n = sizes[i];
+  const uint8_t* x = ptrs[i];
+  h[t] = 0;
+  __syncthreads();
+  const unsigned long long m = n < HIST_REGIME_SAMPLE ? n : HIST_REGIME_SAMPLE;
+  for (unsigned long long j = (unsigned long long)t; j < m; j += HIST_BINS) {
+    const unsigned long long at = n <= HIST_REGIME_SAMPLE ? j : (j * n) >> 12;
+    atomicAdd(&h[__ldg(x + at)], 1u);
+  }
+  __syncthreads();
+  const uint32_t v = h[t];
+  const uint32_t mx = __reduce_max_sync(0xffffffffu, v);
+  const uint32_t sq = __reduce_add_sync(0xffffffffu, v * v);
+  if ((t & 31) == 0) {
+    wmax[t >> 5] = mx;
+    wsq[t >> 5] = sq;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t M = 0, S = 0;
+    for (int w = 0; w < HIST_BINS / 32; ++w) {
+      M = wmax[w] > M ? wmax[w] : M;
+      S += wsq[w];
+    }
+    uint8_t r = (uint8_t)HIST_REGIME_WIDE;
+    if (m == 0) r = (uint8_t)HIST_REGIME_WIDE;
+    else if ((unsigned long long)M * 1000ull >= (unsigned long long)theta * m) r = (uint8_t)HIST_REGIME_DEGENERATE;
+    else if (64ull * S >= m * m) r = (uint8_t)HIST_REGIME_PEAKED;
+    regime[i] = r;
+  }
+}
+
+int launch_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t theta,
+                   uint8_t* d_regime, cudaStream_t s) {
+  for (uint32_t first = 0; first < count; first += 65535u) {
+    const uint32_t c = count - first < 65535u ? count - first : 65535u;
+    regime_kernel<<<c, HIST_BINS, 0, s>>>(d_ptrs + first, d_sizes + first, theta, d_regime + first);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return HIST_OK;
+}
+
+RegimeLayouts layouts_of(const hist_batch_tuning& tu) {
+  RegimeLayouts l;
+  for (uint32_t r = 0; r < HIST_REGIMES; ++r) {
+    l.layout[r] = 5;
+    l.small_bytes[r] = tu.small_bytes;
+    l.small_layout[r] = tu.small_log2k;
+  }
+  return l;
+}
+
+RegimeLayouts layouts_of(const hist_batch_table& tb) {
+  RegimeLayouts l;
+  for (uint32_t r = 0; r < HIST_REGIMES; ++r) {
+    l.layout[r] = tb.regime[r].layout;
+    l.small_bytes[r] = tb.regime[r].small_bytes;
+    l.small_layout[r] = tb.regime[r].small_layout;
+  }
+  return l;
+}
+
+int launch_batch_images(const hist_batch_tuning& tu, const RegimeLayouts& lay, const uint8_t* regime,
+                        const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                        cudaStream_t s) {
   // one CTA per SM with 64 registers (2 or 4 loads in flight), or two with 32
   // registers (2 loads in flight)
   static int attr21[kMaxDevices], attr41[kMaxDevices], attr22[kMaxDevices];
@@ -149,10 +239,9 @@ int launch_batch_images(const hist_batch_tuning& tu, const uint8_t* const* d_ptr
     a.ptrs = d_ptrs + first;
     a.sizes = d_sizes + first;
     a.out = d_out + (size_t)first * HIST_BINS;
+    a.regime = regime ? regime + first : nullptr;
     a.count = count - first < kBatchMaxImages ? count - first : kBatchMaxImages;
-    a.small_bytes = tu.small_bytes;
-    a.small_lk = tu.small_log2k;
-    a.large_lk = 5;
+    a.lay = lay;
     void* params[] = {&a};
     e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kThreads), params, kBatchSmem, s);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -163,6 +252,68 @@ int launch_batch_images(const hist_batch_tuning& tu, const uint8_t* const* d_ptr
 bool tuning_ok(const hist_batch_tuning* t) {
   return t && (t->unroll == 2 || t->unroll == 4) && t->ctas_per_sm >= 1 && t->ctas_per_sm <= 2 &&
          !(t->ctas_per_sm == 2 && t->unroll == 4) && t->small_log2k <= 5;
+}
+
+bool layout_ok(uint32_t l) { return l <= 5 || l == kPerWarp; }
+
+bool table_ok(const hist_batch_table* t) {
+  if (!t || !(t->unroll == 2 || t->unroll == 4) || t->ctas_per_sm < 1 || t->ctas_per_sm > 2 ||
+      (t->ctas_per_sm == 2 && t->unroll == 4) || t->theta_milli > 1000)
+    return false;
+  for (uint32_t r = 0; r < HIST_REGIMES; ++r)
+    if (!layout_ok(t->regime[r].layout) || !layout_ok(t->regime[r].small_layout)) return false;
+  return true;
+}
+
+hist_batch_tuning shape_of(const hist_batch_table& t) {
+  hist_batch_tuning tu;
+  memset(&tu, 0, sizeof(tu));
+  tu.ctas_per_sm = t.ctas_per_sm;
+  tu.unroll = t.unroll;
+  return tu;
+}
+
+// The regimes call: memset, classification, counting.
+int batch_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                  uint8_t* d_regime, const hist_batch_table& tb, cudaStream_t s) {
+  if (count == 0) return HIST_OK;
+  cudaError_t e = cudaMemsetAsync(d_out, 0, (size_t)count * HIST_BINS * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int rc = launch_regimes(d_ptrs, d_sizes, count, tb.theta_milli, d_regime, s);
+  if (rc) return rc;
+  return launch_batch_images(shape_of(tb), layouts_of(tb), d_regime, d_ptrs, d_sizes, count, d_out, s);
+}
+
+// Capture `enqueue` (which enqueues on the stream it is given) into an
+// instantiated graph; the kernels' attributes are set up by `prepare`
+// outside the capture.
+template <class Prep, class Enq>
+int capture_graph(Prep prepare, Enq enqueue, hist_batch_graph** out) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e);
+  int rc = prepare(cs);
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (rc == HIST_OK) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue(cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (rc == HIST_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
+    } else {
+      rc = cuda_fail(e);
+    }
+  }
+  if (rc == HIST_OK) {
+    e = cudaGraphInstantiate(&ge, g, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (rc) return rc;
+  *out = reinterpret_cast<hist_batch_graph*>(ge);
+  return HIST_OK;
 }
 
 }  // namespace
@@ -188,7 +339,7 @@ int hist_batch(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t cou
   if (count == 0) return HIST_OK;
   cudaError_t e = cudaMemsetAsync(d_out, 0, (size_t)count * HIST_BINS * sizeof(uint32_t), (cudaStream_t)s);
   if (e != cudaSuccess) return cuda_fail(e);
-  return launch_batch_images(tu, d_ptrs, d_sizes, count, d_out, (cudaStream_t)s);
+  return launch_batch_images(tu, layouts_of(tu), nullptr, d_ptrs, d_sizes, count, d_out, (cudaStream_t)s);
 }
 
 int hist_batch_capture(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
@@ -199,32 +350,54 @@ int hist_batch_capture(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint
   if (tuning) tu = *tuning;
   else hist_batch_tuning_init(&tu);
   if (!tuning_ok(&tu) || count == 0 || !d_ptrs || !d_sizes || !d_out) return HIST_EINVAL;
-  cudaStream_t cs;
-  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return cuda_fail(e);
-  // attributes and occupancy are set up outside the capture
-  int rc = launch_batch_images(tu, d_ptrs, d_sizes, 0, d_out, cs);
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
-  if (rc == HIST_OK) {
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      rc = hist_batch(d_ptrs, d_sizes, count, d_out, &tu, (hist_cuda_stream)cs);
-      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-      if (rc == HIST_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
-    } else {
-      rc = cuda_fail(e);
-    }
+  // attributes and occupancy are set up outside the capture (a launch of no images)
+  return capture_graph(
+      [&](cudaStream_t cs) { return launch_batch_images(tu, layouts_of(tu), nullptr, d_ptrs, d_sizes, 0, d_out, cs); },
+      [&](cudaStream_t cs) { return hist_batch(d_ptrs, d_sizes, count, d_out, &tu, (hist_cuda_stream)cs); }, out);
+}
+
+void hist_batch_table_init(hist_batch_table* t) {
+  if (!t) return;
+  memset(t, 0, sizeof(*t));
+  t->ctas_per_sm = 2;
+  t->unroll = 2;
+  t->theta_milli = HIST_THETA_MILLI_DEFAULT;
+  for (uint32_t r = 0; r < HIST_REGIMES; ++r) {
+    t->regime[r].layout = 5;
+    t->regime[r].small_bytes = 0;
+    t->regime[r].small_layout = 5;
   }
-  if (rc == HIST_OK) {
-    e = cudaGraphInstantiate(&ge, g, 0);
-    if (e != cudaSuccess) rc = cuda_fail(e);
-  }
-  if (g) cudaGraphDestroy(g);
-  cudaStreamDestroy(cs);
-  if (rc) return rc;
-  *out = reinterpret_cast<hist_batch_graph*>(ge);
-  return HIST_OK;
+}
+
+int hist_batch_classify(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t theta_milli,
+                        uint8_t* d_regime, hist_cuda_stream s) {
+  if (theta_milli > 1000 || (count && (!d_ptrs || !d_sizes || !d_regime))) return HIST_EINVAL;
+  return launch_regimes(d_ptrs, d_sizes, count, theta_milli, d_regime, (cudaStream_t)s);
+}
+
+int hist_batch_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count, uint32_t* d_out,
+                       uint8_t* d_regime, const hist_batch_table* table, hist_cuda_stream s) {
+  hist_batch_table tb;
+  if (table) tb = *table;
+  else hist_batch_table_init(&tb);
+  if (!table_ok(&tb) || (count && (!d_ptrs || !d_sizes || !d_out || !d_regime))) return HIST_EINVAL;
+  return batch_regimes(d_ptrs, d_sizes, count, d_out, d_regime, tb, (cudaStream_t)s);
+}
+
+int hist_batch_regimes_capture(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count,
+                               uint32_t* d_out, uint8_t* d_regime, const hist_batch_table* table,
+                               hist_batch_graph** out) {
+  if (!out) return HIST_EINVAL;
+  *out = nullptr;
+  hist_batch_table tb;
+  if (table) tb = *table;
+  else hist_batch_table_init(&tb);
+  if (!table_ok(&tb) || count == 0 || !d_ptrs || !d_sizes || !d_out || !d_regime) return HIST_EINVAL;
+  return capture_graph(
+      [&](cudaStream_t cs) {
+        return launch_batch_images(shape_of(tb), layouts_of(tb), d_regime, d_ptrs, d_sizes, 0, d_out, cs);
+      },
+      [&](cudaStream_t cs) { return batch_regimes(d_ptrs, d_sizes, count, d_out, d_regime, tb, cs); }, out);
 }
 
 int hist_batch_graph_launch(hist_batch_graph* g, hist_cuda_stream s) {
@@ -297,3 +470,164 @@ int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uin
 }
 
 }  // extern "C"
+
+namespace {
+
+// Mean time of `enqueue` on `s` over `repeats` runs after one warm-up run
+// (CUDA events), or a negative HIST_E* code.
+template <class Enq>
+float time_runs(Enq enqueue, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, uint32_t repeats, int* rc) {
+  *rc = enqueue();
+  if (*rc) return 0.0f;
+  float tot = 0.0f;
+  for (uint32_t r = 0; r < repeats; ++r) {
+    cudaEventRecord(e0, s);
+    *rc = enqueue();
+    cudaEventRecord(e1, s);
+    if (*rc) return 0.0f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      *rc = cuda_fail(e);
+      return 0.0f;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    tot += ms;
+  }
+  return tot / (float)repeats;
+}
+
+}  // namespace
+
+extern "C" int hist_batch_autotune_regimes(const uint8_t* const* d_ptrs, const size_t* d_sizes, uint32_t count,
+                                           uint32_t* d_out, uint8_t* d_regime, uint32_t repeats,
+                                           hist_batch_table* best, hist_regime_report* report) {
+  if (!best || count == 0 || !d_ptrs || !d_sizes || !d_out || !d_regime) return HIST_EINVAL;
+  if (repeats == 0) repeats = 3;
+  hist_batch_table tb;
+  hist_batch_table_init(&tb);
+  tb.theta_milli = best->theta_milli <= 1000 && best->theta_milli ? best->theta_milli : HIST_THETA_MILLI_DEFAULT;
+  hist_regime_report rep;
+  memset(&rep, 0, sizeof(rep));
+  cudaStream_t s;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // the images' regimes, pointers and sizes on the host
+  std::vector<uint8_t> reg(count);
+  std::vector<const uint8_t*> ptrs(count);
+  std::vector<size_t> sizes(count);
+  int rc = launch_regimes(d_ptrs, d_sizes, count, tb.theta_milli, d_regime, s);
+  if (rc == HIST_OK) {
+    e = cudaMemcpyAsync(reg.data(), d_regime, count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ptrs.data(), d_ptrs, count * sizeof(void*), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sizes.data(), d_sizes, count * sizeof(size_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  // candidate settings: a layout, and none or one smaller layout for small images
+  std::vector<hist_regime_setting> cands;
+  const uint32_t layouts[] = {kPerWarp, 0, 1, 2, 3, 4, 5};
+  const uint32_t smalls[][2] = {{0, 5}, {64u << 10, 0}, {64u << 10, kPerWarp}, {1u << 20, 2}};
+  for (uint32_t l : layouts)
+    for (const auto& sm : smalls) {
+      if (sm[0] && sm[1] == l) continue;
+      hist_regime_setting c;
+      memset(&c, 0, sizeof(c));
+      c.layout = l;
+      c.small_bytes = sm[0];
+      c.small_layout = sm[0] ? sm[1] : l;
+      cands.push_back(c);
+    }
+  rep.candidates = (uint32_t)cands.size();
+  // per regime: its images alone, every candidate (each image counted with
+  // the setting in entry 0: no regime array)
+  const hist_batch_tuning shape = shape_of(tb);
+  for (uint32_t r = 0; r < HIST_REGIMES && rc == HIST_OK; ++r) {
+    std::vector<const uint8_t*> rp;
+    std::vector<size_t> rz;
+    for (uint32_t i = 0; i < count; ++i)
+      if (reg[i] == r) {
+        rp.push_back(ptrs[i]);
+        rz.push_back(sizes[i]);
+        rep.bytes[r] += sizes[i];
+      }
+    rep.images[r] = (uint32_t)rp.size();
+    if (rp.empty()) continue;
+    const uint32_t rc_n = (uint32_t)rp.size();
+    const uint8_t** dp = nullptr;
+    size_t* dz = nullptr;
+    uint32_t* dout = nullptr;
+    e = cudaMalloc((void**)&dp, rc_n * sizeof(void*));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dz, rc_n * sizeof(size_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dout, (size_t)rc_n * HIST_BINS * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(dp, rp.data(), rc_n * sizeof(void*), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dz, rz.data(), rc_n * sizeof(size_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? HIST_ENOMEM : cuda_fail(e);
+    float bms = 1e30f;
+    for (size_t k = 0; k < cands.size() && rc == HIST_OK; ++k) {
+      RegimeLayouts lay;
+      for (uint32_t q = 0; q < HIST_REGIMES; ++q) {
+        lay.layout[q] = cands[k].layout;
+        lay.small_bytes[q] = cands[k].small_bytes;
+        lay.small_layout[q] = cands[k].small_layout;
+      }
+      const float ms = time_runs(
+          [&]() {
+            cudaError_t me = cudaMemsetAsync(dout, 0, (size_t)rc_n * HIST_BINS * sizeof(uint32_t), s);
+            if (me != cudaSuccess) return cuda_fail(me);
+            return launch_batch_images(shape, lay, nullptr, dp, dz, rc_n, dout, s);
+          },
+          s, e0, e1, repeats, &rc);
+      if (rc) break;
+      if (cands[k].layout == 5 && cands[k].small_bytes == 0) rep.ms_default[r] = ms;
+      if (ms < bms) {
+        bms = ms;
+        tb.regime[r] = cands[k];
+      }
+    }
+    rep.ms[r] = bms < 1e30f ? bms : 0.0f;
+    cudaFree(dp);
+    cudaFree(dz);
+    cudaFree(dout);
+  }
+  // the launch shape of the whole batch with the chosen settings
+  const uint32_t shapes[][2] = {{2, 2}, {1, 2}, {1, 4}};
+  float bms = 1e30f;
+  hist_batch_table chosen = tb;
+  for (const auto& sh : shapes) {
+    if (rc) break;
+    hist_batch_table t = tb;
+    t.ctas_per_sm = sh[0];
+    t.unroll = sh[1];
+    const float ms = time_runs([&]() { return batch_regimes(d_ptrs, d_sizes, count, d_out, d_regime, t, s); }, s, e0,
+                               e1, repeats, &rc);
+    if (rc) break;
+    if (ms < bms) {
+      bms = ms;
+      chosen = t;
+    }
+  }
+  if (rc == HIST_OK) {
+    rep.batch_ms = bms;
+    hist_batch_table def;
+    hist_batch_table_init(&def);
+    def.theta_milli = tb.theta_milli;
+    rep.batch_default_ms =
+        time_runs([&]() { return batch_regimes(d_ptrs, d_sizes, count, d_out, d_regime, def, s); }, s, e0, e1,
+                  repeats, &rc);
+  }
+  // leave d_out holding the batch under the chosen table
+  if (rc == HIST_OK) rc = batch_regimes(d_ptrs, d_sizes, count, d_out, d_regime, chosen, s);
+  e = cudaStreamSynchronize(s);
+  if (rc == HIST_OK && e != cudaSuccess) rc = cuda_fail(e);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (rc) return rc;
+  *best = chosen;
+  if (report) *report = rep;
+  return HIST_OK;
+}

@@ -82,10 +82,6 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t l
   }
 }
 
-#ifndef HIST_PLAIN_ORDER
-#define HIST_PLAIN_ORDER 2
-#endif
-
 // The order in which a lane of the per-warp layout takes the 16 bytes of its
 // vector: lane l counts byte s ^ (l mod 16) at step s.  The increments of one
 // step are one warp-wide shared-memory operation; when neighbouring pixels
@@ -94,7 +90,9 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t l
 // conflicts), while this order spreads them over 16 banks.  Equal values
 // still meet at one address, which costs nothing.  Two byte-permutes per
 // 4 bytes: the first takes word i or i ^ 1 with its bytes in xor order, the
-// second word i or i ^ 2 of the result.
+// second word i or i ^ 2 of the result.  Measured on 1 GiB (one-shot per-warp
+// kernel): a ramp 1.19 -> 6.2 TB/s; uniform, constant and N(128, 8) data
+// within 1.5 % of the natural order.
 struct LaneOrder {
   uint32_t a, b;  // byte-permute selectors
 };
@@ -108,18 +106,10 @@ __device__ __forceinline__ LaneOrder lane_order() {
   return o;
 }
 __device__ __forceinline__ uint4 lane_permute(const uint4& q, const LaneOrder& o) {
-#if HIST_PLAIN_ORDER == 0
-  return q;
-#else
   const uint32_t t0 = __byte_perm(q.x, q.y, o.a), t1 = __byte_perm(q.y, q.x, o.a);
   const uint32_t t2 = __byte_perm(q.z, q.w, o.a), t3 = __byte_perm(q.w, q.z, o.a);
-#if HIST_PLAIN_ORDER == 1
-  return make_uint4(t0, t1, t2, t3);
-#else
   return make_uint4(__byte_perm(t0, t2, o.b), __byte_perm(t1, t3, o.b), __byte_perm(t2, t0, o.b),
                     __byte_perm(t3, t1, o.b));
-#endif
-#endif
 }
 
 template <int PATH, int LK>

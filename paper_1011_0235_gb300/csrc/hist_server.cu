@@ -250,9 +250,16 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
       }
       continue;
     }
-    // this CTA's bytes of the request: its cost range cut to [0, n)
-    const unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
-    const unsigned long long e0 = hi - p0 < (unsigned long long)q.n ? hi - p0 : (unsigned long long)q.n;
+    // this CTA's bytes of the request: its cost range cut to [0, n); a
+    // request of at most a quarter of a CTA's range is not split (the range
+    // holding its first cost position counts it whole, with no accumulator)
+    unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
+    unsigned long long e0 = hi - p0 < (unsigned long long)q.n ? hi - p0 : (unsigned long long)q.n;
+    if ((unsigned long long)q.n * 4 <= W / gridDim.x) {
+      if (p0 < lo) continue;
+      b0 = 0;
+      e0 = q.n;
+    }
     if (b0 >= e0) continue;
     const uint32_t c = ctl[r];
     int path = PATH_PLAIN, lk = 0;

@@ -351,17 +351,47 @@ template <class A>
 __device__ __forceinline__ uint32_t flat_check(const A& a) {
   return a.mode == HIST_MODE_PLAIN ? kCheckNever : (a.mode == HIST_MODE_ADAPTIVE ? kCheckAlways : kCheckPredicted);
 }
+// The switch of a chunk whose histogram is cs.hist (n pixels): its largest
+// bin against theta (threads 0..255 hold the bins; all threads call; two
+// barriers).  Returned to every thread.
+__device__ __forceinline__ uint32_t block_flag(const uint32_t* hist, uint32_t n, uint32_t theta, EpiShared& es) {
+  const int t = threadIdx.x;
+  if (t < HIST_BINS) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, hist[t]);
+    if ((t & 31) == 0) es.wmax[t >> 5] = m;
+  }
+  __syncthreads();
+  uint32_t mx = 0;
+#pragma unroll
+  for (int i = 0; i < HIST_BINS / 32; ++i) mx = es.wmax[i] > mx ? es.wmax[i] : mx;
+  __syncthreads();
+  return reaches_theta(mx, n, theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+}
+
 template <class A>
-__device__ __noinline__ void flat_epilogue(const A& a, uint32_t j, uint32_t check, uint32_t last_kernel,
-                                           hist_pattern& next, CtaShared& cs, EpiShared& es) {
+__device__ __noinline__ void flat_epilogue(const A& a, uint32_t j, uint32_t check, hist_pattern& next,
+                                           CtaShared& cs, EpiShared& es) {
   StreamDev* st = a.st;
   const int t = threadIdx.x;
   const uint32_t n = a.c[j].n;
   __syncthreads();
-  const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
-  if (t == 0) cs.flag = r.flag;  // r is valid in threads 0..255 only
-  __syncthreads();
-  const uint32_t flag = cs.flag;
+  // The stream state keeps the patterns of the launch's last two chunks and
+  // the last chunk's switch; an AUTO launch records every chunk's switch.
+  // At the full budget every other chunk's pattern is known without the
+  // rule's arithmetic (the full table after a non-empty chunk, the default
+  // pattern after an empty one: the layout the next chunk was counted
+  // with), and below it the next chunk's layout came from its prediction,
+  // so those patterns are not computed here.
+  const bool want_pattern = j + 2 >= a.count;
+  uint32_t flag = HIST_FLAG_PLAIN;
+  if (want_pattern) {
+    const hist_degeneracy_result r = block_epilogue(cs.hist, n, a.budget, a.theta, next, es);
+    if (t == 0) cs.flag = r.flag;  // r is valid in threads 0..255 only
+    __syncthreads();
+    flag = cs.flag;
+  } else if (check == kCheckPredicted) {
+    flag = block_flag(cs.hist, n, a.theta, es);
+  }
   if (t < HIST_BINS) {
     const uint32_t h = cs.hist[t];
     if (a.c[j].out) a.c[j].out[t] = h;
@@ -371,18 +401,31 @@ __device__ __noinline__ void flat_epilogue(const A& a, uint32_t j, uint32_t chec
   const uint32_t rs = (uint32_t)((a.first_chunk + j) % kChunkRing);
   if (check == kCheckPredicted && t == 0) st->rflag[rs] = flag;
   if (a.window > 1 && t < HIST_BINS) st->whist[rs][t] = cs.hist[t];
-  if (j + 1 < a.count && a.budget == HIST_BUDGET_MAX &&
+  if (want_pattern && j + 1 < a.count && a.budget == HIST_BUDGET_MAX &&
       (check == kCheckAlways || (check == kCheckPredicted && __ldcg(&st->rpred[rs]) == HIST_FLAG_ADAPTIVE))) {
     // chunk j+1 was counted with the layout the rule gives after n pixels
     saturated_pattern(n, a.budget, cs, es);
     if (!same_pattern(next, cs.pat) && t == 0) atomicExch(&st->status, kStatusPattern);
   }
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
-  if (j + 2 >= a.count) copy_pattern(&st->lpat[ls][j + 1 == a.count ? 1 : 0], &next);
+  if (want_pattern) copy_pattern(&st->lpat[ls][j + 1 == a.count ? 1 : 0], &next);
   if (j + 1 == a.count && t == 0) st->lflag[ls] = flag;
+  __syncthreads();
+}
+
+// A CTA that ran `epis` chunk epilogues adds them to the launch's count once
+// it is done (after a fence that publishes them); the CTA whose add completes
+// the launch's chunks writes the stream state after the batch.  All threads
+// call.
+template <class A>
+__device__ __noinline__ void flat_finish(const A& a, uint32_t epis, uint32_t check, uint32_t last_kernel,
+                                         CtaShared& cs) {
+  StreamDev* st = a.st;
+  const int t = threadIdx.x;
+  const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
   __threadfence();
   __syncthreads();
-  if (t == 0) cs.kernel = atomicAdd(&st->lchunks[ls], 1ull) + 1 == a.count ? 1u : 0u;
+  if (t == 0) cs.kernel = atomicAdd(&st->lchunks[ls], (unsigned long long)epis) + epis == a.count ? 1u : 0u;
   __syncthreads();
   if (cs.kernel) {
     // every chunk's epilogue is done: the stream state after the batch
@@ -425,6 +468,7 @@ struct FlatShared {
   int last;
   int released;  // this CTA has waited for the previous launch
   int ring_ok;   // the chunk ring slots of this launch are free
+  uint32_t epis; // chunk epilogues this CTA ran
   uint32_t wt[CAP];  // cost weight of each chunk (flat_prefix)
 };
 
@@ -504,7 +548,8 @@ __device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* l
     // the whole chunk
     if (t < HIST_BINS) fs.cs.hist[t] = fs.cs.res[t];
     flat_release(fs);
-    flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, flat_check(a), fs.next, fs.cs, fs.es);
+    if (t == 0) fs.epis += 1;
     flat_mark(a, j, 7);
     return;
   }
@@ -525,7 +570,8 @@ __device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* l
     }
     if (t == 0) st->rdone[slot] = 0;
     flat_release(fs);
-    flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
+    flat_epilogue(a, j, flat_check(a), fs.next, fs.cs, fs.es);
+    if (t == 0) fs.epis += 1;
   }
   flat_mark(a, j, 7);
   __syncthreads();
@@ -562,8 +608,8 @@ __device__ __forceinline__ void flat_piece(const A& a, uint32_t j, uint32_t b0, 
 // holds.  All threads call.
 template <class A>
 __device__ void flat_range(const A& a, const unsigned long long* pre, const uint32_t* wt,
-                           unsigned long long x0, unsigned long long x1, uint32_t* table, uint32_t* lut,
-                           FlatShared<A::kCap>& fs) {
+                           unsigned long long x0, unsigned long long x1, unsigned long long range, uint32_t* table,
+                           uint32_t* lut, FlatShared<A::kCap>& fs) {
   uint32_t j = 0, jh = a.count;
   while (j + 1 < jh) {
     const uint32_t mid = (j + jh) >> 1;
@@ -580,9 +626,17 @@ __device__ void flat_range(const A& a, const unsigned long long* pre, const uint
         flat_mark(a, j, 0);
         if (threadIdx.x < HIST_BINS) fs.cs.hist[threadIdx.x] = 0;
         flat_release(fs);
-        flat_epilogue(a, j, flat_check(a), flat_last_kernel(a), fs.next, fs.cs, fs.es);
+        flat_epilogue(a, j, flat_check(a), fs.next, fs.cs, fs.es);
+        if (threadIdx.x == 0) fs.epis += 1;
         flat_mark(a, j, 7);
       }
+      continue;
+    }
+    if ((unsigned long long)n * w * 4 <= range) {
+      // a chunk of at most a quarter of a CTA's range is not split: the
+      // range holding its first cost position counts it whole, so it needs
+      // no accumulator, byte counter or ring
+      if (p0 >= x0) flat_piece(a, j, 0, n, table, lut, fs);
       continue;
     }
     const unsigned long long c0 = x0 > p0 ? (x0 - p0 + w - 1) / w : 0ull;
@@ -607,6 +661,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
     fs.cur = -1;
     fs.released = 0;
     fs.ring_ok = 0;
+    fs.epis = 0;
   }
   zero_table(table);
   flat_prefix(a, pre, fs.wt);
@@ -617,8 +672,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
   }
   const unsigned long long W = pre[a.count];
   const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-  if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, table, lut, fs);
+  if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, W / gridDim.x, table, lut, fs);
   flat_flush(a, table, lut, fs, true);
+  __syncthreads();
+  if (fs.epis) flat_finish(a, fs.epis, flat_check(a), flat_last_kernel(a), fs.cs);
 }
 
 // AUTO mode.  Chunk j's kernel is chunk j-1's switch (at the full budget

@@ -46,6 +46,15 @@ def test_struct_sizes(lib):
     assert ctypes.sizeof(_abi.HistPattern) == 776
     assert ctypes.sizeof(_abi.DegeneracyResult) == 24
     assert ctypes.sizeof(_abi.HistConfig) == 32
+    assert ctypes.sizeof(_abi.BatchTable) == 16 + 3 * 16
+    assert ctypes.sizeof(_abi.RegimeReport) == 16 + 24 + 12 + 12 + 8 + 16
+
+
+def test_batch_table_defaults(lib):
+    t = _abi.BatchTable()
+    lib.hist_batch_table_init(ctypes.byref(t))
+    assert (t.ctas_per_sm, t.unroll, t.theta_milli) == (2, 2, 450)
+    assert [(r.layout, r.small_bytes) for r in t.regime] == [(5, 0)] * 3
 
 
 def test_strerror_and_config(lib):

@@ -170,3 +170,151 @@ def test_batch_full_size_4096_images():
     rng = np.random.default_rng(1)
     for i in sorted(set(rng.integers(0, 4096, 8).tolist()) | {0, 4095}):
         assert np.array_equal(ref[i], _oracle(images[i])), i
+
+
+# ------------------------------------------------ batches tuned per regime ----
+
+def _mixed_images(count, seed, side_hi=1024):
+    """Images of the three regimes: the benchmark's laws (uniform, normal,
+    mixture) and, for a third of them, the degenerate stream's 95 % law or a
+    constant, with sizes from 0 up to side_hi^2 and 0..15-byte jitter."""
+    rng = np.random.default_rng(seed)
+    base = workloads.batch_images(count=count, seed=seed, side_lo=1, side_hi=side_hi, jitter=True)
+    for k, im in enumerate(base):
+        if k % 3 == 0:
+            im.thr = synth.degenerate(int(rng.integers(0, 256)), 0.95) if k % 2 else synth.constant(int(rng.integers(0, 256)))
+            im.kind = "degenerate"
+    for k, n in enumerate((0, 1, 4095, 4096, 4097, 8191, 8192, 12288)):
+        base[k + 1].n = n  # the sample's edge cases
+    # re-pack with the new sizes
+    off = 0
+    for im in base:
+        off += int(rng.integers(0, 16))
+        im.offset = off
+        off = (off + im.n + 255) // 256 * 256
+    return base
+
+
+def _host_image(im):
+    return synth.host(im.n, im.thr, synth.SEED_BASE + 4, im.counter0)
+
+
+def _table(**regimes):
+    t = _abi.BatchTable()
+    hl.lib().hist_batch_table_init(ctypes.byref(t))
+    for r, setting in regimes.items():
+        k = {"degenerate": 0, "peaked": 1, "wide": 2}[r]
+        for f, v in setting.items():
+            setattr(t.regime[k], f, v)
+    return t
+
+
+def test_regime_classifier_device_vs_oracle():
+    images = _mixed_images(400, synth.SEED_BASE + 40)
+    buf = _fill(images, workloads.packed_bytes(images) + 64)
+    ptrs, sizes = _arrays(buf, images)
+    reg = torch.full((len(images),), 255, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for theta in (450, 0, 1000, 300):
+        assert hl.lib().hist_batch_classify(ptrs.data_ptr(), sizes.data_ptr(), len(images), theta, reg.data_ptr(), s) == 0
+        torch.cuda.synchronize()
+        got = reg.cpu().numpy()
+        want = [oracle.batch_regime(_host_image(im), theta) for im in images]
+        assert got.tolist() == want, theta
+        if theta == 450:
+            assert set(want) == {0, 1, 2}
+    assert hl.lib().hist_batch_classify(ptrs.data_ptr(), sizes.data_ptr(), 1, 1001, reg.data_ptr(), s) == _abi.EINVAL
+
+
+TABLES = [
+    dict(),
+    dict(degenerate=dict(layout=_abi.LAYOUT_PER_WARP), peaked=dict(layout=2), wide=dict(layout=5)),
+    dict(degenerate=dict(layout=0, small_bytes=1 << 16, small_layout=_abi.LAYOUT_PER_WARP),
+         peaked=dict(layout=_abi.LAYOUT_PER_WARP, small_bytes=1 << 20, small_layout=1),
+         wide=dict(layout=3, small_bytes=4096, small_layout=0)),
+    dict(degenerate=dict(layout=4), peaked=dict(layout=5, small_bytes=1 << 16, small_layout=_abi.LAYOUT_PER_WARP),
+         wide=dict(layout=_abi.LAYOUT_PER_WARP)),
+]
+
+
+@pytest.mark.parametrize("tab", range(len(TABLES)))
+def test_batch_regimes_every_layout(tab):
+    images = _mixed_images(300, synth.SEED_BASE + 41 + tab, side_hi=700)
+    buf = _fill(images, workloads.packed_bytes(images) + 64)
+    ptrs, sizes = _arrays(buf, images)
+    reg = torch.empty(len(images), dtype=torch.uint8, device="cuda")
+    out = torch.full((len(images), 256), -1, dtype=torch.int32, device="cuda")
+    t = _table(**TABLES[tab])
+    for shape in ((2, 2), (1, 4)):
+        t.ctas_per_sm, t.unroll = shape
+        assert hl.lib().hist_batch_regimes(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(),
+                                           reg.data_ptr(), ctypes.byref(t), torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        for i, im in enumerate(images):
+            assert np.array_equal(got[i], oracle.hist_u32(_host_image(im))), (shape, i, im.n)
+
+
+def test_batch_regimes_autotuned_and_captured():
+    images = _mixed_images(600, synth.SEED_BASE + 45, side_hi=2048)
+    buf = _fill(images, workloads.packed_bytes(images) + 64)
+    ptrs, sizes = _arrays(buf, images)
+    reg = torch.empty(len(images), dtype=torch.uint8, device="cuda")
+    out = torch.full((len(images), 256), -1, dtype=torch.int32, device="cuda")
+    best = _table()
+    rep = _abi.RegimeReport()
+    assert hl.lib().hist_batch_autotune_regimes(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(),
+                                                reg.data_ptr(), 1, ctypes.byref(best), ctypes.byref(rep)) == 0
+    ref = [oracle.hist_u32(_host_image(im)) for im in images]
+    want_reg = [oracle.batch_regime(_host_image(im)) for im in images]
+    assert reg.cpu().numpy().tolist() == want_reg
+    assert [rep.images[r] for r in range(3)] == [want_reg.count(r) for r in range(3)]
+    assert all(rep.ms[r] > 0 for r in range(3)) and rep.batch_ms > 0 and rep.candidates > 7
+    assert all(best.regime[r].layout in (0, 1, 2, 3, 4, 5, _abi.LAYOUT_PER_WARP) for r in range(3))
+    got = out.cpu().numpy().view(np.uint32)  # left under the chosen table
+    for i in range(len(images)):
+        assert np.array_equal(got[i], ref[i]), i
+    # the tuned table in one call, and captured into a graph and replayed
+    out.fill_(-1)
+    assert hl.lib().hist_batch_regimes(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(),
+                                       reg.data_ptr(), ctypes.byref(best), torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    for i in range(len(images)):
+        assert np.array_equal(got[i], ref[i]), i
+    g = ctypes.c_void_p()
+    assert hl.lib().hist_batch_regimes_capture(ptrs.data_ptr(), sizes.data_ptr(), len(images), out.data_ptr(),
+                                               reg.data_ptr(), ctypes.byref(best), ctypes.byref(g)) == 0
+    for _ in range(2):
+        out.fill_(-1)
+        reg.fill_(255)
+        assert hl.lib().hist_batch_graph_launch(g, torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        for i in range(len(images)):
+            assert np.array_equal(got[i], ref[i]), i
+        assert reg.cpu().numpy().tolist() == want_reg
+    assert hl.lib().hist_batch_graph_destroy(g) == 0
+
+
+def test_batch_regimes_bad_tables():
+    x = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    ptrs = torch.tensor([x.data_ptr()], dtype=torch.int64, device="cuda")
+    sizes = torch.tensor([16], dtype=torch.int64, device="cuda")
+    reg = torch.empty(1, dtype=torch.uint8, device="cuda")
+    out = torch.empty(256, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for bad in (dict(ctas_per_sm=3), dict(unroll=3), dict(ctas_per_sm=2, unroll=4), dict(theta_milli=1001)):
+        t = _table()
+        for k, v in bad.items():
+            setattr(t, k, v)
+        assert hl.lib().hist_batch_regimes(ptrs.data_ptr(), sizes.data_ptr(), 1, out.data_ptr(), reg.data_ptr(),
+                                           ctypes.byref(t), s) == _abi.EINVAL
+    for f in ("layout", "small_layout"):
+        t = _table(wide={f: 7})
+        assert hl.lib().hist_batch_regimes(ptrs.data_ptr(), sizes.data_ptr(), 1, out.data_ptr(), reg.data_ptr(),
+                                           ctypes.byref(t), s) == _abi.EINVAL
+    assert hl.lib().hist_batch_regimes(ptrs.data_ptr(), sizes.data_ptr(), 1, out.data_ptr(), reg.data_ptr(), None,
+                                       s) == 0
+    torch.cuda.synchronize()
+    assert int(out.cpu()[0]) == 16
