@@ -145,7 +145,14 @@ uint32_t oracle_batch_regime(const uint8_t* x, size_t n, uint32_t theta_milli) {
   uint64_t m = n < ORACLE_REGIME_SAMPLE ? (uint64_t)n : ORACLE_REGIME_SAMPLE;
   uint64_t h[ORACLE_BINS];
   for (int b = 0; b < ORACLE_BINS; ++b) h[b] = 0;
-  for (uint64_t j = 0; j < m; ++j) h[x[(j * (uint64_t)n) / m]] += 1;
+  if (n <= ORACLE_REGIME_SAMPLE) {
+    for (uint64_t i = 0; i < n; ++i) h[x[i]] += 1;
+  } else {
+    for (uint64_t t = 0; t < 256; ++t) {
+      uint64_t start = (t * (uint64_t)n) / 256;
+      for (uint64_t u = 0; u < 16; ++u) h[x[start + u]] += 1;
+    }
+  }
   uint64_t mx = 0, sq = 0;
   for (int b = 0; b < ORACLE_BINS; ++b) {
     if (h[b] > mx) mx = h[b];

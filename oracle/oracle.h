@@ -102,9 +102,10 @@ int oracle_binning_pattern(const uint32_t h[ORACLE_BINS], uint32_t budget, oracl
  * batch autotuner keeps one setting per regime; the paper has no such
  * classifier -- only its first test is the paper's, the degeneracy of
  * Sec. III.C):
- *   m = min(n, ORACLE_REGIME_SAMPLE); the sample is the m pixels
- *   x[floor(j * n / m)], j = 0 .. m-1 (every pixel when n <= 4096); h its
- *   256-bin histogram.
+ *   the sample is every pixel when n <= ORACLE_REGIME_SAMPLE (4096), else
+ *   256 runs of 16 consecutive pixels, run t starting at floor(t * n / 256)
+ *   (the runs do not overlap and end inside the image since n > 4096);
+ *   m = min(n, 4096) is its size and h its 256-bin histogram.
  *   ORACLE_REGIME_DEGENERATE  max_b h[b] * 1000 >= theta_milli * m
  *   ORACLE_REGIME_PEAKED      otherwise, 64 * sum_b h[b]^2 >= m^2: the chance
  *                             that two sampled pixels are equal is at least

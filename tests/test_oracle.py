@@ -594,30 +594,44 @@ def test_regime_degeneracy_boundary():
     assert oracle.batch_regime(x, theta_milli=999) == oracle.REGIME_DEGENERATE
 
 
-def _interleaved(n, const_pos, period):
-    """Value 7 where i mod period == const_pos, a ramp elsewhere."""
+def _marked(n, mark):
+    """Value 7 where mark(i) holds, a ramp (never 7) elsewhere."""
     i = np.arange(n)
     x = (i % 256).astype(np.uint8)
-    x[i % period == const_pos] = 7
-    x[(i % period != const_pos) & (x == 7)] = 8
+    x[x == 7] = 8
+    x[mark(i)] = 7
     return x
 
 
-def test_regime_sample_positions():
-    # n = 8192: the sample is x[floor(j * 8192 / 4096)] = x[2 j], the even pixels
-    x = _interleaved(8192, 1, 2)  # odd pixels 7: the whole image is half 7
-    assert oracle.batch_regime(x) == oracle.REGIME_WIDE
-    x = _interleaved(8192, 0, 2)
+def test_regime_sample_runs():
+    # n = 8192: run t covers pixels 32 t .. 32 t + 15, the first half of every
+    # 32-pixel block; the whole image is half 7 either way
+    assert oracle.batch_regime(_marked(8192, lambda i: i % 32 < 16)) == oracle.REGIME_DEGENERATE
+    assert oracle.batch_regime(_marked(8192, lambda i: i % 32 >= 16)) == oracle.REGIME_WIDE
+    # n = 12288: runs at 48 t; 7 on the first 16 of every 48 pixels is all of
+    # the sample but only a third of the image (below theta as a whole)
+    assert oracle.batch_regime(_marked(12288, lambda i: i % 48 < 16)) == oracle.REGIME_DEGENERATE
+    assert oracle.batch_regime(_marked(12288, lambda i: (i % 48 >= 16) & (i % 48 < 32))) == oracle.REGIME_WIDE
+    # n = 8191: run t >= 1 starts at floor(8191 t / 256) = 32 t - 1, so the
+    # 255 pixels at 32 t - 1 are sampled (255 / 4096 = 62 per mille) and the
+    # 16 after each run start are not
+    x = _marked(8191, lambda i: i % 32 == 31)
+    assert oracle.batch_regime(x, theta_milli=62) == oracle.REGIME_DEGENERATE
+    assert oracle.batch_regime(x, theta_milli=63) == oracle.REGIME_WIDE
+    # n = 4097: runs at 16 t cover pixels 0 .. 4095; pixel 4096 is never sampled
+    x = np.full(4097, 9, np.uint8)
+    x[4096] = 200
+    y = np.full(4097, 200, np.uint8)
+    y[:4096] = (np.arange(4096) % 256).astype(np.uint8)
     assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
-    # n = 8191: floor(j * 8191 / 4096) = 2 j - 1 for j >= 1: the odd pixels
-    x = _interleaved(8191, 1, 2)
-    assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
-    x = _interleaved(8191, 0, 2)
-    assert oracle.batch_regime(x) == oracle.REGIME_WIDE
-    # n = 12288: the sample is x[3 j]; the pixels with i mod 6 == 3 are half
-    # of it (a sample of 2048 would see none of them)
-    x = _interleaved(12288, 3, 6)
-    assert oracle.batch_regime(x) == oracle.REGIME_DEGENERATE
+    assert oracle.batch_regime(y) == oracle.REGIME_WIDE
+    # and the sample of n = 4097 is 4096 pixels: 2047 nines in it fall one
+    # short of half at theta = 500; the unsampled last pixel is a nine too
+    ramp = np.array([v for v in range(256) if v != 9] * 9, np.uint8)[:2049]
+    z = np.concatenate([np.full(2047, 9, np.uint8), ramp, np.full(1, 9, np.uint8)])
+    assert z.size == 4097
+    assert oracle.batch_regime(z, theta_milli=500) == oracle.REGIME_PEAKED
+    assert oracle.batch_regime(z[:4096], theta_milli=499) == oracle.REGIME_DEGENERATE
 
 
 def test_regime_of_the_benchmark_laws():

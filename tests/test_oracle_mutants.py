@@ -51,7 +51,13 @@ MUTANTS = [
      "if (total == 0) total = 1;"),
     ("budget range", "if (budget < ORACLE_BUDGET_MIN || budget > ORACLE_BUDGET_MAX) return -1;\n  uint64_t total",
      "if (budget < ORACLE_BUDGET_MIN) return -1;\n  uint64_t total"),
-    ("regime sample rounds up", "h[x[(j * (uint64_t)n) / m]] += 1;", "h[x[(j * (uint64_t)n + m - 1) / m]] += 1;"),
+    ("regime run start rounds up", "uint64_t start = (t * (uint64_t)n) / 256;",
+     "uint64_t start = (t * (uint64_t)n + 255) / 256;"),
+    ("regime runs of 8", "for (uint64_t u = 0; u < 16; ++u) h[x[start + u]] += 1;",
+     "for (uint64_t u = 0; u < 8; ++u) h[x[start + u]] += 2;"),
+    ("regime runs spaced by 4096 / n", "uint64_t start = (t * (uint64_t)n) / 256;",
+     "uint64_t start = t * 16;"),
+    ("regime whole image up to 4097", "if (n <= ORACLE_REGIME_SAMPLE) {", "if (n <= ORACLE_REGIME_SAMPLE + 1) {"),
     ("regime sample of 2048", "uint64_t m = n < ORACLE_REGIME_SAMPLE ? (uint64_t)n : ORACLE_REGIME_SAMPLE;",
      "uint64_t m = n < 2048 ? (uint64_t)n : 2048;"),
     ("regime degeneracy strict", "if (mx * 1000u >= (uint64_t)theta_milli * m)", "if (mx * 1000u > (uint64_t)theta_milli * m)"),
