@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="headline stream only: no clock settling, extras, end-to-end or CPU legs (for ncu)")
     ap.add_argument("--profile-part", default=None,
-                    choices=["serving", "batch", "ablation", "table2", "auto", "budget960", "smallchunks"],
+                    choices=["serving", "batch", "ablation", "table2", "auto", "budget960", "smallchunks",
+                             "budgets", "regimes"],
                     help="run only one other workload once, for ncu: the serving capacity replay "
                          "(4000 requests), the 4096-image batch, 256 MiB cases of Table 1 and Table 2, "
                          "the degenerate workload through an AUTO stream, the N(128, 8) stream at "
@@ -446,14 +447,15 @@ def ablation_extras(torch, hl, synth, hbm, steps=10, n=1 << 30):
     sink = torch.empty(lib.hist_ablation_grid(n) * 256, dtype=torch.int32, device="cuda")
     out = torch.empty(256, dtype=torch.int32, device="cuda")
     res = {"bytes": n, "stages": ["read+write", "+init", "+pattern", "+atomics", "+reduce",
-                                  "complete, warp-aggregated increments"]}
+                                  "complete, warp-aggregated increments",
+                                  "complete, input staged by bulk copies (cp.async.bulk, 2 x 16 KiB per CTA)"]}
     for law_name, law in (("uniform", synth.uniform()), ("normal_sigma8", synth.normal(128, 8))):
         x = torch.empty(n, dtype=torch.uint8, device="cuda")
         synth.device_fill(x.data_ptr(), n, law, synth.SEED_BASE + 13, 0, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         for name, pd in pats.items():
             row = []
-            for stage in range(1, 7):
+            for stage in range(1, 8):
                 def step(stage=stage, pd=pd):
                     _abi.check("hist_ablation", lib.hist_ablation(
                         x.data_ptr(), n, pd.data_ptr() if pd is not None else None, stage,
@@ -694,6 +696,20 @@ def run_part(args):
         cp = x.data_ptr() + np.arange(k, dtype=np.uint64) * np.uint64(c64)
         el = time_steps(torch, lambda: st.push_many(cp, np.full(k, c64, dtype=np.uint64)), 1, 2)
         out = {"smallchunks_gbs": round(k * c64 * 2 / el / 1e9, 1)}
+    elif args.profile_part == "budgets":
+        # 256 MiB of N(128, 8) counted once by hist_adaptive with the rule's
+        # pattern at 960, 2048 and 4096 slots, and once at the full table
+        x = gen_workload_device(torch, synth, 16, synth.SEED_BASE + 2, lambda c: synth.normal(128, 8))
+        o = hl.empty_hist()
+        h = hl.hist_plain(x, o).clone()
+        out = {}
+        for b in (960, 2048, 4096, 8192):
+            pb = hl.binning_pattern(h, b)
+            el = time_steps(torch, lambda: hl.hist_adaptive(x, pb, o), 1, 1)
+            out["adaptive_%d_gbs" % b] = round(16 * CHUNK / el / 1e9, 1)
+    elif args.profile_part == "regimes":
+        # the 4096-image batch tuned per regime, then one graph launch
+        out = batch_extras(torch, hl, synth, 6800.0, steps=1, autotune=True)
     elif args.profile_part == "budget960":
         # the headline's N(128, 8) stream with the paper's 960-slot table:
         # predict_kernel, then the counting launch; 3 pushes of 64 chunks

@@ -363,9 +363,10 @@ int hist_batch_autotune(const uint8_t* const* d_ptrs, const size_t* d_sizes, uin
  * slices into one call, and Sec. III.C chooses a kernel by degeneracy; the
  * regimes extend that choice to the batched call).  An image's regime comes
  * from a fixed sample of it:
- *   m = min(n, HIST_REGIME_SAMPLE); the sample is the m pixels
- *   x[floor(j n / m)], j = 0 .. m-1 (every pixel of an image of at most 4096);
- *   h is its 256-bin histogram.
+ *   every pixel of an image of at most HIST_REGIME_SAMPLE (4096) pixels,
+ *   else 256 runs of 16 consecutive pixels, run t starting at pixel
+ *   floor(t n / 256); m = min(n, 4096) is the sample's size and h its 256-bin
+ *   histogram.
  *   HIST_REGIME_DEGENERATE  max h * 1000 >= theta_milli * m (Sec. III.C's test)
  *   HIST_REGIME_PEAKED      otherwise, 64 * sum h^2 >= m^2: two sampled pixels
  *                           are equal with a chance of at least 1/64
@@ -514,10 +515,15 @@ int hist_stream_change(hist_stream* st, uint32_t tau_milli, hist_change_result* 
  *   5  + sum the sub-bins per bin and write the histogram (= hist_adaptive,
  *        or hist_plain without a pattern);
  *   6  stage 5 with warp-aggregated increments (the lanes holding one value
- *        elect a leader, which adds the group's size).
- * Stages 5 and 6 overwrite d_out (uint32_t[256]); stages 1-4 write
+ *        elect a leader, which adds the group's size);
+ *   7  stage 5 with the input staged through shared memory by 1-D bulk
+ *        copies (cp.async.bulk into two 16 KiB buffers per CTA, completion
+ *        on mbarriers) instead of each thread's own 16-byte loads.
+ * Stages 5-7 overwrite d_out (uint32_t[256]); stages 1-4 write
  * hist_ablation_grid(n) x 256 words of scratch to d_sink, contents
- * unspecified.  n < 2^32; HIST_EINVAL for a bad stage or a missing buffer. */
+ * unspecified.  Stage 7 takes d_sink as an optional status word: 0, or 1 if
+ * an mbarrier wait ran out (bounded; the histogram is then incomplete).
+ * n < 2^32; HIST_EINVAL for a bad stage or a missing buffer. */
 int hist_ablation_grid(size_t n);
 int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint32_t stage, uint32_t* d_out,
                   uint32_t* d_sink, hist_cuda_stream s);

@@ -120,25 +120,29 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgAr
     const Split sp = split_bytes(base, len);
     count_range_dispatch<UNROLL>(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table,
                                  part, threadIdx.x, blockDim.x);
-    flush_table(path, lk, table, cs.pat, part, cs);  // the pattern is not read for SHIFT or PLAIN
+    // the pattern is not read for SHIFT or PLAIN
+    const bool cleared = flush_table(path, lk, table, cs.pat, part, cs, true);
     count_edges(base, sp, cs);
     __syncthreads();
     if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x])
       atomicAdd(a.out + (size_t)i * HIST_BINS + threadIdx.x, cs.res[threadIdx.x]);
-    // clear the slots this layout used (the per-warp tables fill the table)
-    const int words = path == PATH_PLAIN ? kTableWords : (HIST_BINS << lk);
-    uint4* t4 = reinterpret_cast<uint4*>(table);
-    for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
+    if (!cleared) {
+      // clear the slots this layout used (the per-warp tables fill the table)
+      const int words = path == PATH_PLAIN ? kTableWords : (HIST_BINS << lk);
+      uint4* t4 = reinterpret_cast<uint4*>(table);
+      for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
     lo = seg_end;
     ++i;
   }
 }
 
-// The regime of image blockIdx.x (rule in hist.h): 256 threads, the sample
-// of m = min(n, 4096) pixels x[floor(j n / m)] -- j when n <= 4096, else
-// (j n) >> 12, so no division -- counted in shared memory, then the largest
-// bin and the sum of squares (below 2^25: m <= 4096).
+// The regime of image blockIdx.x (rule in hist.h): 256 threads; thread t
+// takes run t of the sample (16 consecutive pixels from floor(t n / 256)),
+// or pixels t, t + 256, ... of an image of at most 4096 pixels, loading all
+// 16 bytes before counting them in shared memory; then the largest bin and
+// the sum of squares (below 2^25: m <= 4096).
 __global__ void __launch_bounds__(HIST_BINS) regime_kernel(const uint8_t* const* ptrs, const size_t* sizes,
                                                            uint32_t theta, uint8_t* regime) {
   __shared__ uint32_t h[HIST_BINS];
@@ -148,22 +152,30 @@ __global__ void __launch_bounds__(HIST_BINS) regime_kernel(const uint8_t* const*
   const unsigned long long n = sizes[i];
   const uint8_t* x = ptrs[i];
   h[t] = 0;
-  __syncthreads();
-  const unsigned long long m = n < HIST_REGIME_SAMPLE ? n : HIST_REGIME_SAMPLE;
-  for (unsigned long long j = (unsigned long long)t; j < m; j += HIST_BINS) {
-    const unsigned long long at = n <= HIST_REGIME_SAMPLE ? j : (j * n) >> 12;
-    atomicAdd(&h[__ldg(x + at)], 1u);
+  uint32_t v[16];
+  const bool runs = n > HIST_REGIME_SAMPLE;
+  const unsigned long long start = runs ? ((unsigned long long)t * n) >> 8 : (unsigned long long)t;
+  const unsigned long long step = runs ? 1ull : (unsigned long long)HIST_BINS;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const unsigned long long at = start + (unsigned long long)u * step;
+    v[u] = at < n ? (uint32_t)__ldg(x + at) : 0xffffffffu;
   }
   __syncthreads();
-  const uint32_t v = h[t];
-  const uint32_t mx = __reduce_max_sync(0xffffffffu, v);
-  const uint32_t sq = __reduce_add_sync(0xffffffffu, v * v);
+#pragma unroll
+  for (int u = 0; u < 16; ++u)
+    if (v[u] != 0xffffffffu) atomicAdd(&h[v[u]], 1u);
+  __syncthreads();
+  const uint32_t c = h[t];
+  const uint32_t mx = __reduce_max_sync(0xffffffffu, c);
+  const uint32_t sq = __reduce_add_sync(0xffffffffu, c * c);
   if ((t & 31) == 0) {
     wmax[t >> 5] = mx;
     wsq[t >> 5] = sq;
   }
   __syncthreads();
   if (t == 0) {
+    const unsigned long long m = n < HIST_REGIME_SAMPLE ? n : HIST_REGIME_SAMPLE;
     uint32_t M = 0, S = 0;
     for (int w = 0; w < HIST_BINS / 32; ++w) {
       M = wmax[w] > M ? wmax[w] : M;

@@ -223,10 +223,26 @@ __device__ __forceinline__ void zero_table(uint32_t* table) {
 }
 
 // Reduce the table to per-bin sums in cs.res (all threads call; ends with a barrier).
-// `part` is 1024 words of free shared memory.
-static __device__ void flush_table(int path, int lk, const uint32_t* table, const hist_pattern& pat,
-                            uint32_t* part, CtaShared& cs) {
+// `part` is 1024 words of free shared memory.  With `clear`, a layout whose
+// reduction reads every table word (the lane-private table) also zeroes the
+// table as it reads it; returns whether it did.
+static __device__ bool flush_table(int path, int lk, uint32_t* table, const hist_pattern& pat, uint32_t* part,
+                                   CtaShared& cs, bool clear = false) {
   __syncthreads();
+  if (path == PATH_SHIFT && lk == 5) {
+    // bin b is the 32 words of row b, one per lane: warp w reduces rows w,
+    // w + 32, ... with one read per lane and a warp-wide add
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int b = w; b < HIST_BINS; b += kWarps) {
+      const uint32_t v = table[(b << 5) + lane];
+      if (clear) table[(b << 5) + lane] = 0;
+      const uint32_t sum = __reduce_add_sync(0xffffffffu, v);
+      if (lane == 0) cs.res[b] = sum;
+    }
+    __syncthreads();
+    return clear;
+  }
   const int b = threadIdx.x & 255, q = threadIdx.x >> 8;
   uint32_t s = 0;
   if (path == PATH_PLAIN) {
@@ -250,6 +266,7 @@ static __device__ void flush_table(int path, int lk, const uint32_t* table, cons
     cs.res[threadIdx.x] = part[threadIdx.x] + part[256 + threadIdx.x] + part[512 + threadIdx.x] +
                           part[768 + threadIdx.x];
   __syncthreads();
+  return false;
 }
 
 // ----------------------------------------------------- block reductions --

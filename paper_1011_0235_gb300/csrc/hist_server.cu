@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
     const uint32_t len = (uint32_t)(e0 - b0);
     const Split sp = split_bytes(base, len);
     count_call(path, lk, reinterpret_cast<const uint4*>(base + sp.head), 0, sp.nvec, table, lut);
-    flush_table(path, lk, table, cs.pat, lut, cs);
+    const bool more = r + 1 < a.count && pre[r + 1] < hi;  // the CTA has another piece
+    const bool cleared = flush_table(path, lk, table, cs.pat, lut, cs, more);
     count_edges(base, sp, cs);
-    if (r + 1 < a.count && pre[r + 1] < hi) zero_table(table);  // the CTA has another piece
+    if (more && !cleared) zero_table(table);
     __syncthreads();
     if (b0 == 0 && e0 == q.n) {
       // the whole request
@@ -287,12 +288,14 @@ __global__ void __launch_bounds__(kThreads, 2) server_batch_kernel(const __grid_
       srv_epilogue(a, r, q, ctl[r], cs, es);
       continue;
     }
-    if (threadIdx.x < HIST_BINS) {
-      if (cs.res[threadIdx.x]) atomicAdd(&a.slot->acc[r][threadIdx.x], cs.res[threadIdx.x]);
-      __threadfence();
-    }
+    if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x]) atomicAdd(&a.slot->acc[r][threadIdx.x], cs.res[threadIdx.x]);
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&a.slot->done[r], (unsigned long long)len) + len == q.n;
+    if (threadIdx.x == 0) {
+      // the barrier orders the CTA's adds before this fence, which publishes
+      // them before the byte count
+      __threadfence();
+      last = atomicAdd(&a.slot->done[r], (unsigned long long)len) + len == q.n;
+    }
     __syncthreads();
     if (last) {
       // every other piece of r was added (and fenced) before its done count

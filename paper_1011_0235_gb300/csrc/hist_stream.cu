@@ -423,9 +423,12 @@ __device__ __noinline__ void flat_finish(const A& a, uint32_t epis, uint32_t che
   StreamDev* st = a.st;
   const int t = threadIdx.x;
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
-  __threadfence();
   __syncthreads();
-  if (t == 0) cs.kernel = atomicAdd(&st->lchunks[ls], (unsigned long long)epis) + epis == a.count ? 1u : 0u;
+  if (t == 0) {
+    // the barrier orders the CTA's epilogue writes before this fence
+    __threadfence();
+    cs.kernel = atomicAdd(&st->lchunks[ls], (unsigned long long)epis) + epis == a.count ? 1u : 0u;
+  }
   __syncthreads();
   if (cs.kernel) {
     // every chunk's epilogue is done: the stream state after the batch
@@ -534,12 +537,12 @@ __device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* l
   StreamDev* st = a.st;
   const uint32_t slot = (uint32_t)((a.first_chunk + (unsigned)j) % kChunkRing);
   const int t = threadIdx.x;
-  flush_table(fs.path, fs.lk, table, fs.cs.pat, lut, fs.cs);
+  const bool cleared = flush_table(fs.path, fs.lk, table, fs.cs.pat, lut, fs.cs, !last_flush);
   if (t < HIST_BINS) {
     fs.cs.res[t] += fs.eh[t];
     fs.eh[t] = 0;
   }
-  if (!last_flush) zero_table(table);
+  if (!last_flush && !cleared) zero_table(table);
   const uint32_t n = a.c[j].n, len = fs.bytes;
   __syncthreads();
   flat_mark(a, j, 5);
@@ -554,12 +557,14 @@ __device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* l
     return;
   }
   flat_ring_ready(a, fs);
-  if (t < HIST_BINS) {
-    if (fs.cs.res[t]) atomicAdd(&st->racc[slot][t], fs.cs.res[t]);
-    __threadfence();
-  }
+  if (t < HIST_BINS && fs.cs.res[t]) atomicAdd(&st->racc[slot][t], fs.cs.res[t]);
   __syncthreads();
-  if (t == 0) fs.last = atomicAdd(&st->rdone[slot], (unsigned long long)len) + len == n;
+  if (t == 0) {
+    // the barrier orders the CTA's adds before this fence, which publishes
+    // them before the byte count
+    __threadfence();
+    fs.last = atomicAdd(&st->rdone[slot], (unsigned long long)len) + len == n;
+  }
   __syncthreads();
   if (fs.last) {
     // every other piece of chunk j was added (and fenced) before its count
@@ -949,20 +954,20 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
     }
     const Geo g = chunk_geo(d);
     count_call(path, lk, g.body, g.begin, g.end, table, lut);
-    flush_table(path, lk, table, cs.pat, lut, cs);
+    const bool cleared = flush_table(path, lk, table, cs.pat, lut, cs, true);
     const Split sp = split_bytes(d.in, d.n);
     if (blockIdx.x == 0) {
       count_edges(d.in, sp, cs);
       __syncthreads();
     }
-    zero_table(table);
+    if (!cleared) zero_table(table);
     const uint32_t mine = (g.end - g.begin) * 16u + (blockIdx.x == 0 ? (uint32_t)(sp.head + sp.tail) : 0u);
-    if (threadIdx.x < HIST_BINS) {
-      if (cs.res[threadIdx.x]) atomicAdd(&st->racc[slot][threadIdx.x], cs.res[threadIdx.x]);
-      __threadfence();
-    }
+    if (threadIdx.x < HIST_BINS && cs.res[threadIdx.x]) atomicAdd(&st->racc[slot][threadIdx.x], cs.res[threadIdx.x]);
     __syncthreads();
-    if (threadIdx.x == 0) last = mine && atomicAdd(&st->rdone[slot], (unsigned long long)mine) + mine == d.n;
+    if (threadIdx.x == 0) {
+      __threadfence();  // after the barrier: publishes the CTA's adds before the byte count
+      last = mine && atomicAdd(&st->rdone[slot], (unsigned long long)mine) + mine == d.n;
+    }
     __syncthreads();
     if (last) {
       __threadfence();

@@ -1,6 +1,7 @@
-"""The Table 1 kernel variants: stage 5 is the complete kernel and stage 6
-the complete kernel with warp-aggregated increments, and both must give the
-exact histogram for every layout; stages 1-4 must run and write their
+"""The Table 1 kernel variants: stage 5 is the complete kernel, stage 6 the
+complete kernel with warp-aggregated increments and stage 7 the complete
+kernel with its input staged by bulk copies, and all must give the exact
+histogram for every layout; stages 1-4 must run and write their
 scratch result on the same inputs (their values are unspecified)."""
 import numpy as np
 import pytest
@@ -47,11 +48,14 @@ def test_ablation_stages(name, n, off):
     for stage in (1, 2, 3, 4):
         assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, stage, None, sink.data_ptr(), s) == 0
     ref = oracle.hist_u32(x)
-    for stage in (5, 6):
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    for stage in (5, 6, 7):
         out.fill_(-1)
-        assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, stage, out.data_ptr(), None, s) == 0
+        st = status.data_ptr() if stage == 7 else None
+        assert lib.hist_ablation(ptr, n, pd.data_ptr() if pd is not None else None, stage, out.data_ptr(), st, s) == 0
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint32), ref), stage
+    assert int(status.item()) == 0  # no bulk-copy wait ran out
 
 
 def test_ablation_argument_errors():
@@ -60,7 +64,7 @@ def test_ablation_argument_errors():
     out = torch.zeros(256, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     assert lib.hist_ablation(x.data_ptr(), 64, None, 0, out.data_ptr(), out.data_ptr(), s) == -1
-    assert lib.hist_ablation(x.data_ptr(), 64, None, 7, out.data_ptr(), out.data_ptr(), s) == -1
+    assert lib.hist_ablation(x.data_ptr(), 64, None, 8, out.data_ptr(), out.data_ptr(), s) == -1
     assert lib.hist_ablation(x.data_ptr(), 64, None, 6, None, None, s) == -1
     assert lib.hist_ablation(x.data_ptr(), 64, None, 5, None, None, s) == -1
     assert lib.hist_ablation(x.data_ptr(), 64, None, 2, None, None, s) == -1
