@@ -29,7 +29,6 @@ constexpr uint32_t kMaxBatch = 1024;   // chunks per launch
 constexpr uint32_t kSmallBatch = 128;  // chunks per launch of the smaller parameter block
 constexpr uint32_t kChunkRing = 4 * kMaxBatch;  // flat scratch: chunk accumulators
 constexpr uint32_t kLaunchRing = 8;             // flat scratch: per-launch records
-constexpr uint32_t kMaxPools = 512;         // work pools of a counting launch (one per SM pair of CTAs)
 constexpr uint32_t kPollLimit = 1u << 22;  // bounded wait: about a second
 constexpr uint32_t kStatusTimeout = 4;     // device status: a wait ran out
 constexpr uint32_t kStatusPattern = 8;     // device status: a layout differed from the rule's pattern
@@ -59,9 +58,6 @@ struct StreamDev {
   unsigned long long wmw[HIST_BINS];
   uint32_t lredo[kLaunchRing][kMaxBatch];
   unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
-  // counting launches whose CTAs start together: the cost consumed so far
-  // in each pool, tagged with the launch (bits 40..63: launch mod 2^24)
-  unsigned long long pcur[kLaunchRing][kMaxPools];
   hist_pattern lpat[kLaunchRing][2];
   uint32_t lflag[kLaunchRing];
   unsigned long long launches_done;            // flat launches whose stream state is written
@@ -476,8 +472,6 @@ struct FlatShared {
   int released;  // this CTA has waited for the previous launch
   int ring_ok;   // the chunk ring slots of this launch are free
   uint32_t epis; // chunk epilogues this CTA ran
-  unsigned long long tlo, thi;  // the cost interval this CTA counts next (pooled launches)
-  uint32_t open[kMaxPools / 32];  // pools seen with work left
   uint32_t wt[CAP];  // cost weight of each chunk (flat_prefix)
 };
 
@@ -657,116 +651,6 @@ __device__ void flat_range(const A& a, const unsigned long long* pre, const uint
   }
 }
 
-// ------------------------------------------------------------ work pools --
-//
-// When a launch's CTAs start counting together (every launch that waits for
-// the work before it), the two CTAs of an SM do not progress alike: the
-// scheduler favours the older one, which finishes its share well before the
-// other, and the SM then runs a single CTA at a lower rate (measured: the
-// last CTA finished counting 57 us after the first, in a 205 us launch).  So
-// such launches split their cost range into P = gridDim/2 pools and each CTA
-// takes tiles from the pool of its SM (smid mod P): both CTAs of an SM draw
-// from one pool until it is empty, the tiles shrinking as the pool does
-// (a quarter of what is left, at least kPoolTile), so the two finish within
-// a small tile of each other.  A CTA whose pool is empty looks (one parallel
-// read of every pool's cursor) for a pool with work left and takes tiles
-// from it.  A tile is a cost interval like a CTA's static range, so
-// counting, pieces, whole small chunks and publication are unchanged.
-
-constexpr unsigned long long kPoolTile = 128ull << 10;
-constexpr unsigned long long kPoolOff = (1ull << 40) - 1;
-
-__device__ __forceinline__ uint32_t pool_count() {
-  const uint32_t p = gridDim.x / 2;
-  return p < 1 ? 1u : (p > kMaxPools ? kMaxPools : p);
-}
-
-__device__ __forceinline__ uint32_t sm_id() {
-  uint32_t v;
-  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Claim the next tile of a pool of `len` cost units whose cursor is `cur`
-// (epoch-tagged for this launch): one thread.  Returns the tile's offset in
-// the pool and its length in `take` (0: the pool is empty).
-__device__ unsigned long long pool_claim(unsigned long long* cur, unsigned long long epoch, unsigned long long len,
-                                         unsigned long long& take) {
-  unsigned long long v = ld_relaxed(cur);
-  while ((v >> 40) != epoch) {
-    // first claim of this launch: start the pool at zero
-    const unsigned long long w = atomicCAS(cur, v, epoch << 40);
-    if (w == v) {
-      v = epoch << 40;
-      break;
-    }
-    v = w;
-  }
-  const unsigned long long used = v & kPoolOff;
-  if (used >= len) {
-    take = 0;
-    return 0;
-  }
-  unsigned long long want = (len - used) / 4;
-  want = want < kPoolTile ? kPoolTile : want;
-  const unsigned long long off = atomicAdd(cur, want) & kPoolOff;
-  take = off >= len ? 0ull : (len - off < want ? len - off : want);
-  return off;
-}
-
-template <class A>
-__device__ void flat_pools(const A& a, const unsigned long long* pre, const uint32_t* wt, unsigned long long W,
-                           uint32_t* table, uint32_t* lut, FlatShared<A::kCap>& fs) {
-  const uint32_t P = pool_count();
-  const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
-  const unsigned long long epoch = a.launch & 0xffffffull;
-  unsigned long long* cur = a.st->pcur[ls];
-  const unsigned long long range = W / gridDim.x;
-  const int t = threadIdx.x;
-  uint32_t p = sm_id() % P;
-  for (;;) {
-    // tiles of pool p until it is empty
-    const unsigned long long plo = W * p / P, len = W * (p + 1) / P - plo;
-    for (;;) {
-      if (t == 0) {
-        unsigned long long take;
-        const unsigned long long off = pool_claim(&cur[p], epoch, len, take);
-        fs.tlo = plo + off;
-        fs.thi = plo + off + take;
-      }
-      __syncthreads();
-      const unsigned long long x0 = fs.tlo, x1 = fs.thi;
-      __syncthreads();
-      if (x0 >= x1) break;
-      flat_range(a, pre, wt, x0, x1, range, table, lut, fs);
-    }
-    // another pool with work left: every thread reads one pool's cursor
-    for (uint32_t i = t; i < kMaxPools / 32; i += blockDim.x) fs.open[i] = 0;
-    __syncthreads();
-    if ((uint32_t)t < P) {
-      const unsigned long long v = ld_relaxed(&cur[t]);
-      const unsigned long long l = W * (t + 1) / P - W * t / P;
-      if ((v >> 40) != epoch || (v & kPoolOff) < l) atomicOr(&fs.open[t >> 5], 1u << (t & 31));
-    }
-    __syncthreads();
-    // the first open pool after p, in circular order
-    uint32_t next = P;
-    for (uint32_t k = 1; k < P && next == P; ++k) {
-      const uint32_t q = (p + k) % P;
-      if (fs.open[q >> 5] & (1u << (q & 31))) next = q;
-    }
-    __syncthreads();
-    if (next == P) break;
-    p = next;
-  }
-}
-
 template <class A>
 __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_constant__ A a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -792,19 +676,8 @@ __global__ void __launch_bounds__(kThreads, 2) batch_flat_kernel(const __grid_co
     if (t == 0) fs.released = 1;
   }
   const unsigned long long W = pre[a.count];
-  if (a.early) {
-    // launches that overlap their predecessor: CTAs start as slots free, and
-    // the next launch's CTAs fill the slots of those that finish early, so
-    // each CTA counts one static range
-    const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-    if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, W / gridDim.x, table, lut, fs);
-  } else if (W / pool_count() < (1ull << 39)) {
-    // (a pool's cost must fit the cursor's 40 bits)
-    if (W > 0) flat_pools(a, pre, fs.wt, W, table, lut, fs);
-  } else {
-    const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-    if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, W / gridDim.x, table, lut, fs);
-  }
+  const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
+  if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, W / gridDim.x, table, lut, fs);
   flat_flush(a, table, lut, fs, true);
   __syncthreads();
   if (fs.epis) flat_finish(a, fs.epis, flat_check(a), flat_last_kernel(a), fs.cs);
