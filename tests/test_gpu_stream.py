@@ -172,6 +172,32 @@ def test_chunk_written_by_the_kernel_just_before_the_push(mode):
     st.close()
 
 
+@pytest.mark.parametrize("grid,overlap", [(1, False), (2, False), (3, False), (7, False), (41, True), (0, False)])
+def test_counting_grids(grid, overlap):
+    """Counting launches of a few CTAs (an odd count among them) and the full
+    grid, with and without the overlap opt-in: every chunk's output and the
+    state equal the oracle's."""
+    rng = np.random.default_rng(700 + grid)
+    sizes = [int(x) for x in rng.choice([0, 1, 77, 4096, 65_536, 1 << 20, 3_000_001], size=40)]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 6, SEED + 80 + grid)
+    for mode in (hl.MODE_ADAPTIVE, hl.MODE_AUTO):
+        ref = oracle.StreamOracle(8192, mode=mode)
+        recs = [ref.push(ch) for ch in chunks]
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
+        outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+        st = hl.Stream(budget=8192, mode=mode, grid=grid, overlap=overlap)
+        for lo in (0, 25):
+            hi = 25 if lo == 0 else len(chunks)
+            st.push_many([bd.data_ptr() + int(offs[j]) for j in range(lo, hi)], sizes[lo:hi],
+                         [outs[j].data_ptr() for j in range(lo, hi)])
+        got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+        for j, r in enumerate(recs):
+            assert np.array_equal(got[j], r.hist), (mode, j)
+        _check_state(st.state(), ref, recs[-1])
+        st.close()
+
+
 @pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 8192), (hl.MODE_PLAIN, 8192)])
 def test_one_push_wrapping_the_rings(mode, budget):
     """One push_many of 4500 chunks: five counting launches of at most 1024
