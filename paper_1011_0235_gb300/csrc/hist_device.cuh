@@ -217,6 +217,14 @@ static __device__ __noinline__ void count_call(int path, int lk, const uint4* p,
   count_dispatch(path, lk, p, begin, end, table, lut);
 }
 
+// The whole CTA with four loads in flight per thread, for kernels that run
+// one CTA of 1024 threads per SM (64 registers): the SM then keeps as many
+// bytes in flight as two CTAs with two loads each.
+static __device__ __noinline__ void count_call4(int path, int lk, const uint4* p, size_t begin, size_t end,
+                                                uint32_t* table, const uint32_t* lut) {
+  count_range_dispatch<4>(path, lk, p, begin, end, table, lut, threadIdx.x, kThreads);
+}
+
 __device__ __forceinline__ void zero_table(uint32_t* table) {
   uint4* t4 = reinterpret_cast<uint4*>(table);
   for (int i = threadIdx.x; i < kTableWords / 4; i += kThreads) t4[i] = make_uint4(0, 0, 0, 0);
