@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
 }
 
 template <class A>
-__global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_constant__ A a) {
+__global__ void __launch_bounds__(kThreads, 1) auto_redo_kernel(const __grid_constant__ A a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table of a default-pattern layout, then scratch of the reduction
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(kThreads, 2) auto_redo_kernel(const __grid_con
       lk = cs.lk;
     }
     const Geo g = chunk_geo(d);
-    count_call(path, lk, g.body, g.begin, g.end, table, lut);
+    count_call4(path, lk, g.body, g.begin, g.end, table, lut);
     const bool cleared = flush_table(path, lk, table, cs.pat, lut, cs, true);
     const Split sp = split_bytes(d.in, d.n);
     if (blockIdx.x == 0) {
