@@ -62,8 +62,8 @@ __device__ __forceinline__ void ablate_word(uint32_t w, uint32_t base, uint32_t 
 
 template <int STAGE, int PATH, int LK>
 __device__ __forceinline__ void ablate_vec(const uint4& q0, uint32_t base, uint32_t lutb, uint32_t table, uint32_t& acc) {
-  // the per-warp layout's lane order of the bytes from the address stage on
-  const uint4 q = (STAGE >= 3 && PATH == PATH_PLAIN) ? lane_permute(q0, lane_order()) : q0;
+  // the counting kernels' lane order of the bytes from the address stage on
+  const uint4 q = (STAGE >= 3 && !(PATH == PATH_SHIFT && LK >= 4)) ? lane_permute(q0, lane_order()) : q0;
   ablate_word<STAGE, PATH, LK>(q.x, base, lutb, table, acc);
   ablate_word<STAGE, PATH, LK>(q.y, base, lutb, table, acc);
   ablate_word<STAGE, PATH, LK>(q.z, base, lutb, table, acc);

@@ -82,8 +82,9 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t l
   }
 }
 
-// The order in which a lane of the per-warp layout takes the 16 bytes of its
-// vector: lane l counts byte s ^ (l mod 16) at step s.  The increments of one
+// The order in which a lane takes the 16 bytes of its vector (every layout
+// but the shift layouts with 16 or 32 sub-bins per bin): lane l counts byte
+// s ^ (l mod 16) at step s.  The increments of one
 // step are one warp-wide shared-memory operation; when neighbouring pixels
 // differ by a constant (a ramp: lane l holds values 16 l .. 16 l + 15), the
 // natural order puts the warp's 16 distinct values in two banks (8-way
@@ -92,7 +93,8 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t base, uint32_t l
 // 4 bytes: the first takes word i or i ^ 1 with its bytes in xor order, the
 // second word i or i ^ 2 of the result.  Measured on 1 GiB (one-shot per-warp
 // kernel): a ramp 1.19 -> 6.2 TB/s; uniform, constant and N(128, 8) data
-// within 1.5 % of the natural order.
+// within 1.5 % of the natural order.  The same with the rule's 960-slot
+// pattern of a ramp (two sub-bins per bin): 1.19 -> 6.26 TB/s.
 struct LaneOrder {
   uint32_t a, b;  // byte-permute selectors
 };
@@ -115,7 +117,9 @@ __device__ __forceinline__ uint4 lane_permute(const uint4& q, const LaneOrder& o
 template <int PATH, int LK>
 __device__ __forceinline__ void count_vec(const uint4& q0, uint32_t base, uint32_t lutb, uint32_t table,
                                           const LaneOrder& o) {
-  const uint4 q = PATH == PATH_PLAIN ? lane_permute(q0, o) : q0;
+  // the shift layouts with 16 or 32 sub-bins per bin give each lane its own
+  // bank whatever the order (lane l uses bank l mod 2^LK of a bin's row)
+  const uint4 q = (PATH == PATH_SHIFT && LK >= 4) ? q0 : lane_permute(q0, o);
   count_word<PATH, LK>(q.x, base, lutb, table);
   count_word<PATH, LK>(q.y, base, lutb, table);
   count_word<PATH, LK>(q.z, base, lutb, table);
