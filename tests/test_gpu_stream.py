@@ -198,6 +198,51 @@ def test_counting_grids(grid, overlap):
         st.close()
 
 
+@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
+def test_pushes_of_many_small_chunks(mode):
+    """Pushes of many small chunks, most of them counted whole by one CTA:
+    sizes 1 B .. 200 KiB with empty chunks among them, every chunk at another
+    alignment, the degenerate and uniform laws alternating (AUTO switches
+    kernels inside a push); every chunk's output, the totals and the state
+    equal the oracle's, and the trace records each chunk's phases in
+    order."""
+    rng = np.random.default_rng(900 + mode)
+    sizes = [int(x) for x in rng.choice([0, 1, 17, 4096, 40_000, 65_536, 200_000], size=700,
+                                        p=[0.05, 0.1, 0.1, 0.2, 0.25, 0.2, 0.1])]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 9, SEED + 95 + mode)
+    ref = oracle.StreamOracle(8192, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    offs, pos = [], 0
+    for c, ch in enumerate(chunks):
+        pos += c % 16
+        offs.append(pos)
+        pos += ch.size
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=mode)
+    tr = st.trace(len(chunks))
+    for lo, hi in ((0, 300), (300, 700)):
+        st.push_many(np.array([bd.data_ptr() + offs[j] for j in range(lo, hi)], dtype=np.uint64),
+                     np.array(sizes[lo:hi], dtype=np.uint64),
+                     np.array([outs[j].data_ptr() for j in range(lo, hi)], dtype=np.uint64))
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    _check_state(st.state(), ref, recs[-1])
+    t = tr.cpu().numpy().view(np.uint64).reshape(len(chunks), 3, 8)
+    for j in range(len(chunks)):
+        for k in range(3):
+            ph = t[j, k]
+            if ph[0]:
+                assert ph[7] >= ph[0], (j, k)
+                if sizes[j]:  # an empty chunk has nothing to reduce (no phase 5)
+                    assert ph[0] <= ph[5] <= ph[7], (j, k)
+    st.close()
+
+
 @pytest.mark.parametrize("mode,budget", [(hl.MODE_ADAPTIVE, 960), (hl.MODE_AUTO, 8192), (hl.MODE_PLAIN, 8192)])
 def test_one_push_wrapping_the_rings(mode, budget):
     """One push_many of 4500 chunks: five counting launches of at most 1024
