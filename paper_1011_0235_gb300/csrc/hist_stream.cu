@@ -27,6 +27,7 @@ namespace {
 
 constexpr uint32_t kMaxBatch = 1024;   // chunks per launch
 constexpr uint32_t kSmallBatch = 128;  // chunks per launch of the smaller parameter block
+constexpr uint32_t kPlanCtas = 160;    // largest grid whose ranges the host plans
 constexpr uint32_t kChunkRing = 4 * kMaxBatch;  // flat scratch: chunk accumulators
 constexpr uint32_t kLaunchRing = 8;             // flat scratch: per-launch records
 constexpr uint32_t kPollLimit = 1u << 22;  // bounded wait: about a second
@@ -98,10 +99,25 @@ struct BatchArgs {
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
   uint32_t window;                  // chunks in the moving window
   uint32_t early;                   // flat: chunks may be read before the work before the launch completes
+  // flat, every chunk of cost weight 1 (all but AUTO mode): the host splits
+  // the batch's cost into the CTAs' ranges, so a CTA reads its own range
+  // instead of scanning the chunk table (see flat_plan)
+  uint32_t planned;
+  unsigned long long W;                        // the batch's total cost
+  unsigned long long range;                    // W / grid
+  unsigned long long plan_lo[kPlanCtas + 1];   // CTA b's range is [plan_lo[b], plan_lo[b + 1])
+  unsigned long long plan_pre[kPlanCtas];      // cost position of its first chunk
+  uint16_t plan_j[kPlanCtas];                  // its first chunk
+  // CTA b with bit b of plan_groups set has only whole chunks for the
+  // groups: chunks [plan_s[b], plan_s[b + 1]) start in its range, and any
+  // chunk that overlaps the range from before is whole (an earlier CTA's)
+  uint16_t plan_s[kPlanCtas + 1];
+  uint32_t plan_groups[(kPlanCtas + 31) / 32];
   ChunkDesc c[CAP];
 };
 using SmallArgs = BatchArgs<kSmallBatch>;
 using LargeArgs = BatchArgs<kMaxBatch>;
+static_assert(sizeof(LargeArgs) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 // Phase timestamps (%globaltimer, ns) of chunk j by CTA slot k (0: the first
 // CTA, 1: the middle one, 2: the last one), eight slots per chunk and CTA, of
@@ -183,7 +199,7 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 // from a sample of the previous chunk, and the epilogues record the exact
 // switch and pattern.  batch_flat_kernel splits the batch's chunks, placed end to end,
 // into one contiguous range per CTA by a cost model (a chunk costs its bytes
-// plus kFlatChunkCost), so a CTA counts one or two pieces of chunks and
+// plus kFlatChunkCost, flat_cost), so a CTA counts one or two pieces of chunks and
 // reduces its table only where its range crosses a chunk boundary.  A CTA
 // adds a piece's per-bin sums into the chunk's accumulator and its bytes
 // into the chunk's counter; the CTA whose bytes complete a chunk runs the
@@ -194,14 +210,37 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 // accumulator returns to zero in its epilogue.
 
 constexpr unsigned long long kFlatChunkCost = 64ull << 10;  // cost of a chunk beyond its bytes
-// dynamic shared memory: table, slot table, chunk cost prefix (u64 per chunk + 1)
+// The batch's last two chunks also cost kFlatTailCost, placed before their
+// bytes: their epilogues derive the patterns the stream keeps, CTA-wide
+// (about 5 us each), so the CTAs holding them should take fewer other
+// chunks.
+constexpr unsigned long long kFlatTailCost = 1ull << 20;
+__host__ __device__ __forceinline__ unsigned long long flat_cost(unsigned long long bytes, uint32_t j,
+                                                                 uint32_t count) {
+  return bytes + kFlatChunkCost + (j + 2 >= count ? kFlatTailCost : 0ull);
+}
+
+// Whole small chunks are counted by groups of warps (flat_groups), thread b
+// of a group holding bin b of its chunk.  Two groups take the table and the
+// slot table as their tables; more groups need tables of their own.
+constexpr int kGroups = 2;
+constexpr int kGroupThreads = kThreads / kGroups;
+constexpr int kGroupWarps = kGroupThreads / 32;
+constexpr uint32_t kGroupChunkMax = 256u << 10;  // largest chunk a group counts
+constexpr int kGroupOwnTables = kGroups > 2 ? kGroups : 0;
+constexpr uint32_t kGroupPrefetch = 64;  // list entries whose pointers are read ahead
+static_assert(kGroupThreads >= HIST_BINS, "one bin per thread of a group");
+static_assert(kTableWords == kLutWords, "a group table in the slot table");
+
+// dynamic shared memory: table, slot table, the groups' own tables, chunk
+// cost prefix (u64 per chunk + 1)
 template <class A>
 constexpr size_t flat_smem_bytes() {
-  return (size_t)(kTableWords + kLutWords) * 4 + (size_t)(A::kCap + 1) * 8;
+  return (size_t)(kTableWords + kLutWords + kGroupOwnTables * kTableWords) * 4 + (size_t)(A::kCap + 1) * 8;
 }
 static_assert(kMaxBatch <= (uint32_t)kThreads, "one prefix lane per chunk");
 
-// pre[j] = sum over chunks before j of (n + kFlatChunkCost); pre[count] = total.
+// pre[j] = sum over chunks before j of their costs (flat_cost); pre[count] = total.
 // The kernel a flat launch runs chunk j with: the mode's, or in AUTO mode
 // the predicted switch of chunk j-1 (chunk 0: the stream's switch, exact, as
 // predict_kernel copied it before the launch; the launch rewrites the
@@ -219,11 +258,11 @@ __device__ __forceinline__ uint32_t flat_kernel_of(const A& a, uint32_t j) {
 // The chunk table sits in the kernel's parameters, which are read through the
 // constant cache: the distinct addresses of one warp's load are served one
 // after another (4 us per launch when thread t read chunk t's size), so each
-// warp reads its chunks' sizes with a warp-uniform index into shared memory.
+// warp reads its chunks' sizes with a warp-uniform index into shared memory
+// (sz), where the rest of the launch reads them.
 template <class A>
-__device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt) {
+__device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt, uint32_t* sz) {
   __shared__ unsigned long long wsum[kWarps];
-  __shared__ uint32_t sz[A::kCap];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (uint32_t j = (uint32_t)w; j < a.count; j += kWarps) {
     const uint32_t n = a.c[j].n;
@@ -233,7 +272,7 @@ __device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt) {
   uint32_t weight = 1;
   if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = 2;
   if (t < (int)a.count) wt[t] = weight;
-  const unsigned long long c = t < (int)a.count ? (unsigned long long)sz[t] * weight + kFlatChunkCost : 0ull;
+  const unsigned long long c = t < (int)a.count ? flat_cost((unsigned long long)sz[t] * weight, t, a.count) : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -433,9 +472,12 @@ __device__ __noinline__ void flat_finish(const A& a, uint32_t epis, uint32_t che
   if (cs.kernel) {
     // every chunk's epilogue is done: the stream state after the batch
     __threadfence();
-    if (a.count == 1) copy_pattern(&st->last_pattern, &st->pattern);
-    else copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
-    __syncthreads();
+    if (a.count == 1) {
+      copy_pattern(&st->last_pattern, &st->pattern);
+      __syncthreads();
+    } else {
+      copy_pattern_cg(&st->last_pattern, &st->lpat[ls][0]);
+    }
     copy_pattern_cg(&st->pattern, &st->lpat[ls][1]);
     if (check == kCheckPredicted && a.window == 1) {
       const uint32_t nr = redo_list(st, a.first_chunk, a.count, ls, last_kernel);
@@ -473,13 +515,25 @@ struct FlatShared {
   int ring_ok;   // the chunk ring slots of this launch are free
   uint32_t epis; // chunk epilogues this CTA ran
   uint32_t wt[CAP];  // cost weight of each chunk (flat_prefix)
+  uint32_t sz[CAP];  // size of each chunk (flat_prefix)
+  uint16_t wl[CAP];  // whole chunks left to the groups, in batch order
+  const uint8_t* gin[kGroupPrefetch];  // input and output of the first wl entries
+  uint32_t* gout[kGroupPrefetch];
+  uint32_t take;     // next entry of wl a group takes
+  uint32_t gitem[kGroups];
+  uint32_t gmax[kGroups][kGroupWarps];
+  uint32_t gres[kGroups][HIST_BINS];  // each group's chunk histogram
 };
 
 template <class A>
-__device__ __forceinline__ void flat_mark(const A& a, uint32_t j, int phase) {
+__device__ __forceinline__ void flat_mark(const A& a, uint32_t j, int phase, bool lead) {
   const int tslot = blockIdx.x == 0 ? 0 : (blockIdx.x == gridDim.x / 2 ? 1 : (blockIdx.x == gridDim.x - 1 ? 2 : -1));
-  if (a.trace && tslot >= 0 && threadIdx.x == 0 && a.trace_first + j < a.trace_cap)
+  if (a.trace && tslot >= 0 && lead && a.trace_first + j < a.trace_cap)
     a.trace[((size_t)(a.trace_first + j) * kTraceCtas + tslot) * kTracePhases + phase] = globaltimer();
+}
+template <class A>
+__device__ __forceinline__ void flat_mark(const A& a, uint32_t j, int phase) {
+  flat_mark(a, j, phase, threadIdx.x == 0);
 }
 
 // Launches of one stream overlap (programmatic dependent launch): every
@@ -543,7 +597,7 @@ __device__ __noinline__ void flat_flush(const A& a, uint32_t* table, uint32_t* l
     fs.eh[t] = 0;
   }
   if (!last_flush && !cleared) zero_table(table);
-  const uint32_t n = a.c[j].n, len = fs.bytes;
+  const uint32_t n = fs.sz[j], len = fs.bytes;
   __syncthreads();
   flat_mark(a, j, 5);
   if (t == 0) fs.cur = -1;
@@ -608,22 +662,70 @@ __device__ __forceinline__ void flat_piece(const A& a, uint32_t j, uint32_t b0, 
   if (threadIdx.x == 0) fs.bytes += e0 - b0;
 }
 
-// Count the cost range [x0, x1) of the batch.  Chunk j's byte b sits at
-// cost pre[j] + b wt[j]; a range takes the bytes whose cost position it
-// holds.  All threads call.
+// Whether a whole chunk j goes to the groups: not empty, at most
+// kGroupChunkMax bytes, not one of the batch's last two chunks (their
+// epilogues keep the stream's patterns), and counted with a layout known
+// without a pattern -- the plain kernel's tables, or the full table at the
+// full budget after a non-empty chunk.
 template <class A>
-__device__ void flat_range(const A& a, const unsigned long long* pre, const uint32_t* wt,
-                           unsigned long long x0, unsigned long long x1, unsigned long long range, uint32_t* table,
-                           uint32_t* lut, FlatShared<A::kCap>& fs) {
-  uint32_t j = 0, jh = a.count;
-  while (j + 1 < jh) {
-    const uint32_t mid = (j + jh) >> 1;
-    if (pre[mid] <= x0) j = mid;
-    else jh = mid;
+__device__ __forceinline__ bool group_chunk(const A& a, uint32_t j, uint32_t n, uint32_t prev_n) {
+  if (n == 0 || n > kGroupChunkMax || j + 2 >= a.count) return false;
+  if (flat_kernel_of(a, j) != HIST_FLAG_ADAPTIVE) return true;
+  return a.budget == HIST_BUDGET_MAX && prev_n > 0;
+}
+
+// Sizes of chunks [j0, j0 + kWarps) into sz, warp w reading chunk j0 + w's;
+// returns the end of the chunks read.  All threads call (ends with a
+// barrier).
+template <class A>
+__device__ __noinline__ uint32_t flat_sizes(const A& a, uint32_t j0, uint32_t* sz) {
+  const uint32_t j = j0 + (threadIdx.x >> 5);
+  if (j < a.count) {
+    const uint32_t n = a.c[j].n;
+    if ((threadIdx.x & 31) == 0) sz[j] = n;
   }
-  for (; j < a.count && pre[j] < x1; ++j) {
-    const unsigned long long p0 = pre[j];
-    const uint32_t n = a.c[j].n, w = wt[j];
+  __syncthreads();
+  return j0 + kWarps;
+}
+
+// Count the cost range [x0, x1) of the batch.  Chunk j's byte b sits at
+// cost pre[j] + b wt[j] (after kFlatTailCost for the last two chunks); a
+// range takes the bytes whose cost position it holds.  All threads call.
+template <class A>
+__device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const uint32_t* wt,
+                               unsigned long long x0, unsigned long long x1, unsigned long long range, uint32_t* table,
+                               uint32_t* lut, FlatShared<A::kCap>& fs) {
+  uint32_t nwl = 0;
+  uint32_t j = 0;
+  unsigned long long p0;  // cost position of chunk j
+  if (a.planned) {
+    j = a.plan_j[blockIdx.x];
+    p0 = a.plan_pre[blockIdx.x];
+  } else {
+    uint32_t jh = a.count;
+    while (j + 1 < jh) {
+      const uint32_t mid = (j + jh) >> 1;
+      if (pre[mid] <= x0) j = mid;
+      else jh = mid;
+    }
+    p0 = pre[j];
+  }
+  // A planned launch reads the sizes of the chunks it meets here, kWarps
+  // at a time from chunk j-1 on, warp w one chunk's with a warp-uniform
+  // index, so the warps' constant-cache misses overlap (chunk after chunk:
+  // 0.5 us each).  Chunk weights are 1 there.
+  uint32_t wend = 0;
+  if (a.planned) wend = flat_sizes(a, j > 0 ? j - 1 : 0, fs.sz);
+  // the size of chunk j-1 (before chunk 0: the stream's last chunk, known
+  // to be non-empty when chunk0_full)
+  uint32_t prev_n = j > 0 ? fs.sz[j - 1] : a.chunk0_full;
+  unsigned long long p1 = 0;
+  for (; j < a.count && p0 < x1; ++j, p0 = p1) {
+    if (a.planned && j == wend) wend = flat_sizes(a, j, fs.sz);
+    const uint32_t n = fs.sz[j], w = a.planned ? 1u : wt[j];
+    p1 = p0 + flat_cost((unsigned long long)n * w, j, a.count);
+    const uint32_t pn = prev_n;
+    prev_n = n;
     if (n == 0) {
       // no bytes: the range holding the chunk's first cost position folds it
       if (p0 >= x0) {
@@ -640,15 +742,149 @@ __device__ void flat_range(const A& a, const unsigned long long* pre, const uint
     if ((unsigned long long)n * w * 4 <= range) {
       // a chunk of at most a quarter of a CTA's range is not split: the
       // range holding its first cost position counts it whole, so it needs
-      // no accumulator, byte counter or ring
-      if (p0 >= x0) flat_piece(a, j, 0, n, table, lut, fs);
+      // no accumulator, byte counter or ring; a small one whose layout and
+      // epilogue need no pattern is left to the groups
+      if (p0 >= x0) {
+        if (group_chunk(a, j, n, pn)) {
+          if (threadIdx.x == 0) fs.wl[nwl] = (uint16_t)j;
+          ++nwl;
+        } else {
+          flat_piece(a, j, 0, n, table, lut, fs);
+        }
+      }
       continue;
     }
-    const unsigned long long c0 = x0 > p0 ? (x0 - p0 + w - 1) / w : 0ull;
-    const unsigned long long c1 = (x1 - p0 + w - 1) / w;
+    // byte b sits at cost q0 + b w, after the chunk's tail cost
+    const unsigned long long q0 = p0 + (j + 2 >= a.count ? kFlatTailCost : 0ull);
+    if (x1 <= q0) continue;
+    const unsigned long long c0 = x0 > q0 ? (x0 - q0 + w - 1) / w : 0ull;
+    const unsigned long long c1 = (x1 - q0 + w - 1) / w;
     const unsigned long long e0 = c1 < (unsigned long long)n ? c1 : (unsigned long long)n;
     if (c0 < e0) flat_piece(a, j, (uint32_t)c0, (uint32_t)e0, table, lut, fs);
   }
+  return nwl;
+}
+
+// ------------------------------------------------ whole small chunks --
+//
+// A CTA that counts a small chunk whole spends little of its time loading
+// it: a 64 KiB chunk is one round of four loads per thread, after which the
+// CTA reduces its table and runs the chunk's epilogue between CTA-wide
+// barriers, with no load in flight.  So the CTA leaves such chunks to the
+// end of its range and counts them with kGroups groups of warps.  Each
+// group has its own table and named barrier and takes the next chunk from a
+// shared counter, so one group's reduction and epilogue run while the other
+// groups' loads are in flight.  A group chunk's epilogue is the part of
+// flat_epilogue that such a chunk needs: its output, the totals, its window
+// entry and, in AUTO mode, its exact switch.
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kGroupThreads) : "memory");
+}
+
+// Count vectors [0, nvec) of p with thread gt of a group into the group's
+// table: the full table, or the per-warp tables of the group's warps (the
+// plain layout indexes them by the CTA's warp number w, so they sit at
+// words 256 w of the group's table, g kGroupWarps <= w < (g + 1) kGroupWarps).
+static __device__ __noinline__ void group_count(bool adaptive, const uint4* p, size_t nvec, uint32_t* table,
+                                                int gt) {
+  if (adaptive) count_range<PATH_SHIFT, 5, 4>(p, 0, nvec, table, table, gt, kGroupThreads);
+  else count_range<PATH_PLAIN, 0, 4>(p, 0, nvec, table, table, gt, kGroupThreads);
+}
+
+// All threads call (after a CTA barrier); returns after the CTA's groups
+// have counted the nwl chunks listed in fs.wl and run their epilogues.
+template <class A>
+__device__ __noinline__ void flat_groups(const A& a, uint32_t nwl, uint32_t* gtables, FlatShared<A::kCap>& fs) {
+  StreamDev* st = a.st;
+  const int t = threadIdx.x, g = t / kGroupThreads, gt = t % kGroupThreads;
+  const int gw = gt >> 5, lane = t & 31;
+  uint32_t* table = gtables + (size_t)g * kTableWords;
+  uint32_t* res = fs.gres[g];
+  const uint32_t check = flat_check(a);
+  bool released = fs.released != 0;
+  uint32_t epis = 0;
+  {
+    uint4* t4 = reinterpret_cast<uint4*>(table);
+    for (int i = gt; i < kTableWords / 4; i += kGroupThreads) t4[i] = make_uint4(0, 0, 0, 0);
+    if (gt < HIST_BINS) res[gt] = 0;
+  }
+  for (;;) {
+    group_sync(g);  // the table is clear and the last epilogue has read res
+    if (gt == 0) fs.gitem[g] = atomicAdd(&fs.take, 1u);
+    group_sync(g);
+    const uint32_t i = fs.gitem[g];
+    if (i >= nwl) break;
+    const uint32_t j = fs.wl[i];
+    const uint32_t n = fs.sz[j];
+    const bool adaptive = flat_kernel_of(a, j) == HIST_FLAG_ADAPTIVE;
+    flat_mark(a, j, 0, gt == 0);
+    const uint8_t* base = i < kGroupPrefetch ? fs.gin[i] : a.c[j].in;
+    uint32_t* out = i < kGroupPrefetch ? fs.gout[i] : a.c[j].out;
+    const Split sp = split_bytes(base, n);
+    group_count(adaptive, reinterpret_cast<const uint4*>(base + sp.head), sp.nvec, table, gt);
+    if (gt < (int)sp.head) atomicAdd(&res[base[gt]], 1u);
+    else if (gt >= 16 && gt < 16 + (int)sp.tail) atomicAdd(&res[base[sp.head + sp.nvec * 16 + (gt - 16)]], 1u);
+    group_sync(g);
+    // reduce the table into res and clear it as it is read
+    if (adaptive) {
+      if (gt < HIST_BINS) {
+        // bin b is the 32 words of row b; thread b reads them starting at
+        // word b mod 32, so the 32 threads of a warp read 32 banks, with
+        // all its loads in flight (a row per warp with a warp-wide add is a
+        // chain of dependent steps per row: 1.2 us per chunk)
+        uint32_t* row = table + (gt << 5);
+        uint32_t sum = 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const int c = (k + gt) & 31;
+          sum += row[c];
+          row[c] = 0;
+        }
+        res[gt] += sum;
+      }
+    } else if (gt < HIST_BINS) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < kGroupWarps; ++w) {
+        uint32_t* q = table + (g * kGroupWarps + w) * HIST_BINS + gt;
+        sum += *q;
+        *q = 0;
+      }
+      res[gt] += sum;
+    }
+    group_sync(g);
+    flat_mark(a, j, 5, gt == 0);
+    if (!released) {
+      // the previous launch writes the stream state and may write the
+      // same outputs
+      pdl_wait();
+      released = true;
+    }
+    const uint32_t rs = (uint32_t)((a.first_chunk + j) % kChunkRing);
+    uint32_t h = 0;
+    if (gt < HIST_BINS) {
+      h = res[gt];
+      res[gt] = 0;
+      if (out) out[gt] = h;
+      if (h) atomicAdd(&st->totals[gt], (unsigned long long)h);
+      if (a.window > 1) st->whist[rs][gt] = h;
+    }
+    if (check == kCheckPredicted) {
+      const uint32_t m = __reduce_max_sync(0xffffffffu, h);
+      if (lane == 0) fs.gmax[g][gw] = m;
+      group_sync(g);
+      if (gt == 0) {
+        uint32_t mx = 0;
+#pragma unroll
+        for (int k = 0; k < HIST_BINS / 32; ++k) mx = fs.gmax[g][k] > mx ? fs.gmax[g][k] : mx;
+        st->rflag[rs] = reaches_theta(mx, n, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+      }
+    }
+    epis += 1;
+    flat_mark(a, j, 7, gt == 0);
+  }
+  if (gt == 0 && epis) atomicAdd(&fs.epis, epis);
 }
 
 // One CTA of 1024 threads per SM, each thread with four 16-byte loads in
@@ -664,7 +900,9 @@ __global__ void __launch_bounds__(kThreads, 1) batch_flat_kernel(const __grid_co
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* table = smem;
   uint32_t* lut = smem + kTableWords;  // slot table while counting, then scratch of the reduction
-  unsigned long long* pre = reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords);
+  uint32_t* gtables = kGroupOwnTables ? smem + kTableWords + kLutWords : smem;
+  unsigned long long* pre =
+      reinterpret_cast<unsigned long long*>(smem + kTableWords + kLutWords + kGroupOwnTables * kTableWords);
   __shared__ FlatShared<A::kCap> fs;
   const int t = threadIdx.x;
 
@@ -675,19 +913,55 @@ __global__ void __launch_bounds__(kThreads, 1) batch_flat_kernel(const __grid_co
     fs.released = 0;
     fs.ring_ok = 0;
     fs.epis = 0;
+    fs.take = 0;
   }
   zero_table(table);
-  flat_prefix(a, pre, fs.wt);
+  if (a.planned) __syncthreads();
+  else flat_prefix(a, pre, fs.wt, fs.sz);
   if (!a.early) {
     // the chunks may come from the work just before this launch
     pdl_wait();
     if (t == 0) fs.released = 1;
   }
-  const unsigned long long W = pre[a.count];
-  const unsigned long long lo = W * blockIdx.x / gridDim.x, hi = W * (blockIdx.x + 1) / gridDim.x;
-  if (lo < hi) flat_range(a, pre, fs.wt, lo, hi, W / gridDim.x, table, lut, fs);
+  unsigned long long lo, hi, range;
+  if (a.planned) {
+    lo = a.plan_lo[blockIdx.x];
+    hi = a.plan_lo[blockIdx.x + 1];
+    range = a.range;
+  } else {
+    const unsigned long long W = pre[a.count];
+    lo = W * blockIdx.x / gridDim.x;
+    hi = W * (blockIdx.x + 1) / gridDim.x;
+    range = W / gridDim.x;
+  }
+  uint32_t nwl = 0;
+  if (a.planned && (a.plan_groups[blockIdx.x >> 5] >> (blockIdx.x & 31) & 1u)) {
+    // the range holds whole chunks for the groups only
+    const uint32_t s0 = a.plan_s[blockIdx.x], s1 = a.plan_s[blockIdx.x + 1];
+    nwl = s1 - s0;
+    for (uint32_t i = (uint32_t)t; i < nwl; i += kThreads) fs.wl[i] = (uint16_t)(s0 + i);
+    for (uint32_t j = s0; j < s1; j += kWarps) flat_sizes(a, j, fs.sz);
+  } else if (lo < hi) {
+    nwl = flat_range(a, pre, fs.wt, lo, hi, range, table, lut, fs);
+  }
   flat_flush(a, table, lut, fs, true);
   __syncthreads();
+  if (nwl) {
+    // the pointers of the groups' first chunks, warp w reading entries w,
+    // w + 32 with warp-uniform indices (their misses overlap)
+    for (uint32_t i = (uint32_t)(t >> 5); i < nwl && i < kGroupPrefetch; i += kWarps) {
+      const ChunkDesc& d = a.c[fs.wl[i]];
+      const uint8_t* in = d.in;
+      uint32_t* out = d.out;
+      if ((t & 31) == 0) {
+        fs.gin[i] = in;
+        fs.gout[i] = out;
+      }
+    }
+    __syncthreads();
+    flat_groups(a, nwl, gtables, fs);
+    __syncthreads();
+  }
   if (fs.epis) flat_finish(a, fs.epis, flat_check(a), flat_last_kernel(a), fs.cs);
 }
 
@@ -1071,6 +1345,8 @@ struct hist_stream {
   unsigned long long host_pushes;
   // the caller's device allocator (alloc null: cudaMalloc / cudaFree)
   hist_allocator alloc;
+  // host buffer of a launch's parameters (null: one is allocated per launch)
+  void* args;
 };
 
 namespace {
@@ -1098,11 +1374,71 @@ void dev_free(hist_stream* st, void* p, size_t bytes) {
   else cudaFree(p);
 }
 
+// The host's copy of the CTAs' ranges of a flat launch whose chunks all
+// have cost weight 1: the batch's chunks placed end to end at their costs
+// (flat_cost), total W; CTA b takes [W b / grid, W (b + 1) / grid)
+// and starts at the last chunk whose cost position is at most the range's
+// start -- what batch_flat_kernel's prefix and search compute otherwise
+// (they read every chunk's size from the parameters: about 8 us per launch
+// of 1024 chunks).
+template <class A>
+void flat_plan(A* a, uint32_t count, const size_t* ns, uint32_t grid) {
+  unsigned long long W = 0;
+  for (uint32_t i = 0; i < count; ++i) W += flat_cost(ns[i], i, count);
+  a->planned = 1;
+  a->W = W;
+  a->range = W / grid;
+  uint32_t j = 0;
+  unsigned long long pj = 0;  // cost position of chunk j
+  for (uint32_t b = 0; b <= grid; ++b) {
+    const unsigned long long lo = W * b / grid;
+    a->plan_lo[b] = lo;
+    if (b == grid) break;
+    while (j + 1 < count && pj + flat_cost(ns[j], j, count) <= lo) {
+      pj += flat_cost(ns[j], j, count);
+      ++j;
+    }
+    a->plan_j[b] = (uint16_t)j;
+    a->plan_pre[b] = pj;
+  }
+  // the chunks the groups take (group_chunk, on the host's copy of the sizes)
+  const unsigned long long range = W / grid;
+  auto whole = [&](uint32_t i) { return (unsigned long long)ns[i] * 4 <= range; };
+  auto grouped = [&](uint32_t i) {
+    if (ns[i] == 0 || ns[i] > kGroupChunkMax || i + 2 >= count || !whole(i)) return false;
+    if (a->mode == HIST_MODE_PLAIN) return true;
+    return a->budget == HIST_BUDGET_MAX && (i > 0 ? ns[i - 1] > 0 : a->chunk0_full != 0);
+  };
+  uint32_t i = 0;  // first chunk whose cost position is at least the range's start
+  unsigned long long pi = 0;
+  for (uint32_t b = 0; b <= grid; ++b) {
+    const unsigned long long lo = a->plan_lo[b];
+    while (i < count && pi < lo) {
+      pi += flat_cost(ns[i], i, count);
+      ++i;
+    }
+    a->plan_s[b] = (uint16_t)i;
+  }
+  for (uint32_t b = 0; b < grid; ++b) {
+    bool only = true;
+    const uint32_t j0 = a->plan_j[b], s0 = a->plan_s[b], s1 = a->plan_s[b + 1];
+    // a chunk that starts before the range and reaches into it
+    for (uint32_t k = j0; k < s0 && only; ++k) only = whole(k);
+    for (uint32_t k = s0; k < s1 && only; ++k) only = grouped(k);
+    if (only) a->plan_groups[b >> 5] |= 1u << (b & 31);
+  }
+}
+
 template <class A>
 int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, const size_t* ns, uint32_t* const* outs,
                  cudaStream_t s) {
-  A* a = (A*)calloc(1, sizeof(A));
+  // the stream's parameter buffer: the header and the plan are cleared, the
+  // chunk entries written (the launch copies the parameters)
+  static_assert(sizeof(A) <= sizeof(LargeArgs), "one buffer for both parameter blocks");
+  const bool own = st->args == nullptr;
+  A* a = own ? (A*)calloc(1, sizeof(A)) : (A*)st->args;
   if (!a) return HIST_ENOMEM;
+  if (!own) memset((void*)a, 0, offsetof(A, c));
   a->st = st->d;
   a->count = count;
   a->chunk0_full = st->flat_full ? 1u : 0u;
@@ -1121,6 +1457,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     a->c[i].n = (uint32_t)ns[i];
     a->c[i].out = outs ? outs[i] : nullptr;
   }
+  if (st->cfg.mode != HIST_MODE_AUTO && st->grid <= (int)kPlanCtas) flat_plan(a, count, ns, (uint32_t)st->grid);
   void* params[] = {a};
   cudaError_t e;
   const bool windowed = st->cfg.window > 1;
@@ -1161,7 +1498,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     lc.numAttrs = 1;
     e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel<A>, params);
   }
-  free(a);
+  if (own) free(a);
   if (e != cudaSuccess) return cuda_fail(e);
   st->flat_launches += 1;
   st->flat_chunks += count;
@@ -1311,6 +1648,7 @@ int hist_stream_create_with_allocator(const hist_config* cfg, const hist_allocat
     free(st);
     return cuda_fail(e);
   }
+  st->args = malloc(sizeof(LargeArgs));  // null: launches allocate their own
   *out = st;
   return HIST_OK;
 }
@@ -1320,6 +1658,7 @@ int hist_stream_destroy(hist_stream* st) {
   cudaError_t e = cudaDeviceSynchronize();
   release_staging(st);
   dev_free(st, st->d, sizeof(StreamDev));
+  free(st->args);
   free(st);
   return e == cudaSuccess ? HIST_OK : cuda_fail(e);
 }
