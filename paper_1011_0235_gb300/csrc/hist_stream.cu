@@ -99,9 +99,10 @@ struct BatchArgs {
   unsigned long long launch;        // flat: number of this launch among the stream's flat launches (from 1)
   uint32_t window;                  // chunks in the moving window
   uint32_t early;                   // flat: chunks may be read before the work before the launch completes
-  // flat, every chunk of cost weight 1 (all but AUTO mode): the host splits
-  // the batch's cost into the CTAs' ranges, so a CTA reads its own range
-  // instead of scanning the chunk table (see flat_plan)
+  // flat: the host splits the batch's cost into the CTAs' ranges, every
+  // chunk of weight 1 (all modes but AUTO; AUTO with a window of one chunk
+  // when every chunk is small), so a CTA reads its own range instead of
+  // scanning the chunk table (see flat_plan)
   uint32_t planned;
   unsigned long long W;                        // the batch's total cost
   unsigned long long range;                    // W / grid
@@ -210,14 +211,21 @@ __device__ __forceinline__ bool same_pattern(const hist_pattern& x, const hist_p
 // accumulator returns to zero in its epilogue.
 
 constexpr unsigned long long kFlatChunkCost = 64ull << 10;  // cost of a chunk beyond its bytes
-// The batch's last two chunks also cost kFlatTailCost, placed before their
-// bytes: their epilogues derive the patterns the stream keeps, CTA-wide
-// (about 5 us each), so the CTAs holding them should take fewer other
-// chunks.
+constexpr uint32_t kGroupChunkMax = 256u << 10;  // largest chunk a group counts (flat_groups)
+// The batch's last two chunks, when small, also cost kFlatTailCost, placed
+// before their bytes: their epilogues derive the patterns the stream keeps,
+// CTA-wide (about 5 us each), and in a launch of many small chunks the CTAs
+// holding them should take fewer other chunks (1024 chunks of 64 KiB: 34.8
+// -> 24.0 us per launch).  Beside 16 MiB chunks the epilogues are noise and
+// the extra cost only shifts the split (AUTO, 64 chunks: 209 -> 220 us).
 constexpr unsigned long long kFlatTailCost = 1ull << 20;
-__host__ __device__ __forceinline__ unsigned long long flat_cost(unsigned long long bytes, uint32_t j,
+__host__ __device__ __forceinline__ unsigned long long flat_tail(unsigned long long n, uint32_t j, uint32_t count) {
+  return j + 2 >= count && n <= kGroupChunkMax ? kFlatTailCost : 0ull;
+}
+// chunk j's cost: n bytes of weight w, the fixed cost, the tail cost
+__host__ __device__ __forceinline__ unsigned long long flat_cost(unsigned long long n, uint32_t w, uint32_t j,
                                                                  uint32_t count) {
-  return bytes + kFlatChunkCost + (j + 2 >= count ? kFlatTailCost : 0ull);
+  return n * w + kFlatChunkCost + flat_tail(n, j, count);
 }
 
 // Whole small chunks are counted by groups of warps (flat_groups), thread b
@@ -226,7 +234,6 @@ __host__ __device__ __forceinline__ unsigned long long flat_cost(unsigned long l
 constexpr int kGroups = 2;
 constexpr int kGroupThreads = kThreads / kGroups;
 constexpr int kGroupWarps = kGroupThreads / 32;
-constexpr uint32_t kGroupChunkMax = 256u << 10;  // largest chunk a group counts
 constexpr int kGroupOwnTables = kGroups > 2 ? kGroups : 0;
 constexpr uint32_t kGroupPrefetch = 64;  // list entries whose pointers are read ahead
 static_assert(kGroupThreads >= HIST_BINS, "one bin per thread of a group");
@@ -252,9 +259,10 @@ __device__ __forceinline__ uint32_t flat_kernel_of(const A& a, uint32_t j) {
   return j == 0 ? a.st->lk0[a.launch % kLaunchRing] : a.st->rpred[(a.first_chunk + j - 1) % kChunkRing];
 }
 
-// In AUTO mode a chunk predicted to run the plain kernel costs twice its
-// bytes (the plain kernel's rate on wide data is about half the full
-// table's); wt[j] holds chunk j's weight.
+// In AUTO mode (the launches whose ranges the host does not plan) a chunk
+// predicted to run the plain kernel
+// costs twice its bytes (the plain kernel's rate on wide data is about half
+// the full table's); wt[j] holds chunk j's weight.
 // The chunk table sits in the kernel's parameters, which are read through the
 // constant cache: the distinct addresses of one warp's load are served one
 // after another (4 us per launch when thread t read chunk t's size), so each
@@ -272,7 +280,7 @@ __device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt, u
   uint32_t weight = 1;
   if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = 2;
   if (t < (int)a.count) wt[t] = weight;
-  const unsigned long long c = t < (int)a.count ? flat_cost((unsigned long long)sz[t] * weight, t, a.count) : 0ull;
+  const unsigned long long c = t < (int)a.count ? flat_cost(sz[t], weight, t, a.count) : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -723,7 +731,7 @@ __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const 
   for (; j < a.count && p0 < x1; ++j, p0 = p1) {
     if (a.planned && j == wend) wend = flat_sizes(a, j, fs.sz);
     const uint32_t n = fs.sz[j], w = a.planned ? 1u : wt[j];
-    p1 = p0 + flat_cost((unsigned long long)n * w, j, a.count);
+    p1 = p0 + flat_cost(n, w, j, a.count);
     const uint32_t pn = prev_n;
     prev_n = n;
     if (n == 0) {
@@ -755,7 +763,7 @@ __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const 
       continue;
     }
     // byte b sits at cost q0 + b w, after the chunk's tail cost
-    const unsigned long long q0 = p0 + (j + 2 >= a.count ? kFlatTailCost : 0ull);
+    const unsigned long long q0 = p0 + flat_tail(n, j, a.count);
     if (x1 <= q0) continue;
     const unsigned long long c0 = x0 > q0 ? (x0 - q0 + w - 1) / w : 0ull;
     const unsigned long long c1 = (x1 - q0 + w - 1) / w;
@@ -916,13 +924,14 @@ __global__ void __launch_bounds__(kThreads, 1) batch_flat_kernel(const __grid_co
     fs.take = 0;
   }
   zero_table(table);
+  // in AUTO mode the work just before this launch is the prediction, whose
+  // switches the cost split and the range read; otherwise the chunks may
+  // come from the work just before this launch
+  const bool wait_first = a.mode == HIST_MODE_AUTO || !a.early;
+  if (wait_first) pdl_wait();
   if (a.planned) __syncthreads();
   else flat_prefix(a, pre, fs.wt, fs.sz);
-  if (!a.early) {
-    // the chunks may come from the work just before this launch
-    pdl_wait();
-    if (t == 0) fs.released = 1;
-  }
+  if (wait_first && t == 0) fs.released = 1;
   unsigned long long lo, hi, range;
   if (a.planned) {
     lo = a.plan_lo[blockIdx.x];
@@ -999,6 +1008,13 @@ __global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constan
   __shared__ uint32_t wm[HIST_BINS / 32];
   __shared__ EpiShared es;
   const int t = threadIdx.x;
+  // An AUTO stream chains its launches (prediction, count, recount, the next
+  // push's prediction) with programmatic dependent launch: this launch may
+  // start while the work before it ends.  It reads the chunks only after
+  // that work completes, unless the caller declared them complete, and it
+  // waits before it reads or writes the stream's state.
+  pdl_launch_dependents();
+  if (!a.early) pdl_wait();
   const ChunkDesc d = a.c[blockIdx.x];
   h[t] = 0;
   __syncthreads();
@@ -1022,6 +1038,7 @@ __global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constan
     sampled = d.n;
   }
   __syncthreads();
+  pdl_wait();  // the stream's state is the work before's to write
   if (a.window > 1 && a.mode == HIST_MODE_AUTO) {
     // the window's prediction needs every sample (window_predict_kernel)
     const uint32_t slot = (uint32_t)((a.first_chunk + blockIdx.x) % kChunkRing);
@@ -1207,6 +1224,9 @@ __global__ void __launch_bounds__(kThreads, 1) auto_redo_kernel(const __grid_con
   __shared__ int last;
   StreamDev* st = a.st;
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+  // chained after the counting launch (see predict_kernel)
+  pdl_launch_dependents();
+  pdl_wait();
   const uint32_t nr = st->lredo_n[ls];
   if (nr == 0) return;
   zero_table(table);
@@ -1374,8 +1394,37 @@ void dev_free(hist_stream* st, void* p, size_t bytes) {
   else cudaFree(p);
 }
 
-// The host's copy of the CTAs' ranges of a flat launch whose chunks all
-// have cost weight 1: the batch's chunks placed end to end at their costs
+// A launch that may start while the work before it on `s` ends
+// (programmatic dependent launch); the kernel waits (griddepcontrol.wait)
+// before it reads what that work writes.
+cudaError_t launch_chained(const void* fn, dim3 grid, dim3 block, void** params, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = block;
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelExC(&lc, fn, params);
+}
+
+// Whether every chunk is at most kGroupChunkMax bytes: an AUTO launch of
+// such chunks is split by the host, every chunk of weight 1 (the fixed
+// costs dominate); with larger chunks the device's split, which weighs a
+// chunk predicted to run the plain kernel twice, keeps the CTAs even
+// (the degenerate workload in 16 MiB chunks, AUTO: 313 us per push with the
+// weights, 399 us with every chunk of weight 1).
+bool all_small(const size_t* ns, uint32_t count) {
+  for (uint32_t i = 0; i < count; ++i)
+    if (ns[i] > kGroupChunkMax) return false;
+  return true;
+}
+
+// The host's copy of the CTAs' ranges of a flat launch, every chunk of cost
+// weight 1: the batch's chunks placed end to end at their costs
 // (flat_cost), total W; CTA b takes [W b / grid, W (b + 1) / grid)
 // and starts at the last chunk whose cost position is at most the range's
 // start -- what batch_flat_kernel's prefix and search compute otherwise
@@ -1384,7 +1433,7 @@ void dev_free(hist_stream* st, void* p, size_t bytes) {
 template <class A>
 void flat_plan(A* a, uint32_t count, const size_t* ns, uint32_t grid) {
   unsigned long long W = 0;
-  for (uint32_t i = 0; i < count; ++i) W += flat_cost(ns[i], i, count);
+  for (uint32_t i = 0; i < count; ++i) W += flat_cost(ns[i], 1, i, count);
   a->planned = 1;
   a->W = W;
   a->range = W / grid;
@@ -1394,8 +1443,8 @@ void flat_plan(A* a, uint32_t count, const size_t* ns, uint32_t grid) {
     const unsigned long long lo = W * b / grid;
     a->plan_lo[b] = lo;
     if (b == grid) break;
-    while (j + 1 < count && pj + flat_cost(ns[j], j, count) <= lo) {
-      pj += flat_cost(ns[j], j, count);
+    while (j + 1 < count && pj + flat_cost(ns[j], 1, j, count) <= lo) {
+      pj += flat_cost(ns[j], 1, j, count);
       ++j;
     }
     a->plan_j[b] = (uint16_t)j;
@@ -1414,7 +1463,7 @@ void flat_plan(A* a, uint32_t count, const size_t* ns, uint32_t grid) {
   for (uint32_t b = 0; b <= grid; ++b) {
     const unsigned long long lo = a->plan_lo[b];
     while (i < count && pi < lo) {
-      pi += flat_cost(ns[i], i, count);
+      pi += flat_cost(ns[i], 1, i, count);
       ++i;
     }
     a->plan_s[b] = (uint16_t)i;
@@ -1457,20 +1506,32 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     a->c[i].n = (uint32_t)ns[i];
     a->c[i].out = outs ? outs[i] : nullptr;
   }
-  if (st->cfg.mode != HIST_MODE_AUTO && st->grid <= (int)kPlanCtas) flat_plan(a, count, ns, (uint32_t)st->grid);
+  if (st->grid <= (int)kPlanCtas && (st->cfg.mode != HIST_MODE_AUTO || (st->cfg.window == 1 && all_small(ns, count))))
+    flat_plan(a, count, ns, (uint32_t)st->grid);
   void* params[] = {a};
   cudaError_t e;
   const bool windowed = st->cfg.window > 1;
-  if (st->autok) {
-    // predictions, the flat launch with the predicted kernels, (the window,)
-    // the recount
+  if (st->autok && !windowed) {
+    // predictions, the flat launch with the predicted kernels, the recount:
+    // each may start while the one before ends (each waits for it before
+    // it reads what that one writes)
+    e = launch_chained((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
+    if (e == cudaSuccess)
+      e = launch_chained((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                         flat_smem_bytes<A>(), s);
+    if (e == cudaSuccess)
+      e = launch_chained((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                         kSmemBytes, s);
+  } else if (st->autok) {
+    // predictions, the window's prediction, the flat launch with the
+    // predicted kernels, the window, the recount
     e = cudaLaunchKernel((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
-    if (e == cudaSuccess && windowed)
+    if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)window_predict_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
                            flat_smem_bytes<A>(), s);
-    if (e == cudaSuccess && windowed)
+    if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = cudaLaunchKernel((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
@@ -1486,17 +1547,8 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
   } else {
     // PLAIN or ADAPTIVE at the full budget, window 1: one launch, which may
     // start while the previous launch on `s` finishes (see batch_flat_kernel)
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)st->grid);
-    lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = flat_smem_bytes<A>();
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    e = cudaLaunchKernelExC(&lc, (const void*)batch_flat_kernel<A>, params);
+    e = launch_chained((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                       flat_smem_bytes<A>(), s);
   }
   if (own) free(a);
   if (e != cudaSuccess) return cuda_fail(e);
