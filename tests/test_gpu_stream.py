@@ -424,6 +424,40 @@ def test_auto_recount_list_of_a_1024_chunk_launch(window):
     st.close()
 
 
+@pytest.mark.parametrize("overlap", [False, True])
+def test_auto_pushes_back_to_back_with_recounts(overlap):
+    """Consecutive AUTO pushes (each one's prediction may start while the
+    push before recounts): small chunks of mixed sizes, every fourth one
+    misleading its sample, pushed in six calls of uneven length without a
+    synchronisation between them; every output, the recount total and the
+    state equal the oracle's."""
+    rng = np.random.default_rng(77 + overlap)
+    sizes = [int(x) for x in rng.choice([16, 4096, 40_000, 65_536, 200_000], size=420)]
+    chunks = [_misleading_chunk(sizes[c] - sizes[c] % 4096 or 4096, 30 + c % 150, c) if c % 4 == 1 else
+              synth.host(sizes[c], synth.uniform() if c % 2 else synth.normal(128, 8), SEED + 70, c)
+              for c in range(len(sizes))]
+    sizes = [ch.size for ch in chunks]
+    ref = oracle.StreamOracle(8192)
+    recs = [ref.push(ch) for ch in chunks]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    bd = dev(np.concatenate(chunks))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=hl.MODE_AUTO, overlap=overlap)
+    cuts = [0, 5, 100, 101, 260, 400, len(chunks)]
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        st.push_many(np.uint64(bd.data_ptr()) + offs[lo:hi].astype(np.uint64),
+                     np.array(sizes[lo:hi], dtype=np.uint64),
+                     np.array([outs[j].data_ptr() for j in range(lo, hi)], dtype=np.uint64))
+    s = st.state()
+    _check_state(s, ref, recs[-1])
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    assert s.recounted > 20
+    assert s.status == 0
+    st.close()
+
+
 @pytest.mark.parametrize("window,budget", [(1, 8192), (2, 8192), (1, 960), (2, 2048)])
 def test_auto_recounts_chunks_whose_sample_misled(window, budget):
     # chunks alternate: a misleading degenerate chunk (exact switch ADAPTIVE,
