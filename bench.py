@@ -568,6 +568,33 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     reqs = workloads.serving_schedule(50000, 4000, streams=streams, region=region, seed=synth.SEED_BASE + 7)
     cap = run(reqs, at_zero=True)
     cap["frac_of_hbm"] = round(cap["served_gbs"] / hbm, 4)
+    # the counting kernels' own rate on this mix: each stream's 64 MiB region
+    # counted once by the kernel AUTO gives its law (the adaptive kernel's
+    # full table for the degenerate streams, the per-warp kernel for the
+    # rest), the requests' bytes weighted by it
+    o = hl.empty_hist()
+
+    def t_of(f):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 3 / 1e3
+
+    rate = []
+    for law in laws:
+        x = pool[law.offset:law.offset + region]
+        if law.kind == "degenerate":
+            p = hl.binning_pattern(hl.hist_plain(x, o).clone(), 8192)
+            rate.append(region / t_of(lambda: hl.hist_adaptive(x, p, o)))
+        else:
+            rate.append(region / t_of(lambda: hl.hist_plain(x, o)))
+    nbytes = float(sum(r.n for r in reqs))
+    cap["auto_kernels_alone_gbs"] = round(nbytes / sum(r.n / rate[r.stream] for r in reqs) / 1e9, 1)
     out["capacity"] = cap
     del pool
     return out
@@ -610,6 +637,9 @@ def summary_of(ex, value, hbm):
     if sv:
         sm["serving"] = {k: {"gbs": v.get("served_gbs"), "p50_us": v.get("p50_us"), "p99_us": v.get("p99_us")}
                          for k, v in sv.items() if isinstance(v, dict) and "served_gbs" in v}
+        cap = sv.get("capacity") or {}
+        if "auto_kernels_alone_gbs" in cap:
+            sm["serving"]["capacity"]["auto_kernels_alone_gbs"] = cap["auto_kernels_alone_gbs"]
     return sm
 
 
