@@ -744,3 +744,45 @@ def test_full_size_degenerate_switching():
     kernels = [r.kernel for r in recs]
     expect = [0] + [1 if ((c - 1) // 8) % 2 == 0 else 0 for c in range(1, 64)]
     assert kernels == expect
+
+
+@pytest.mark.parametrize("case", range(32))
+def test_random_pushes(case):
+    """Seeded random streams: chunk sizes from empty to 300 KB (most of them
+    below the groups' 256 KiB, some above), every chunk at its own alignment,
+    laws switching between degenerate, peaked and flat phases, a random mode,
+    budget, window, grid and overlap flag, and the chunks pushed in random
+    cuts; every chunk's output, the totals and the state equal the oracle's."""
+    rng = np.random.default_rng(5000 + case)
+    mode = [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO][case % 3]
+    budget = int(rng.choice([8192, 8192, 2048, 960]))
+    window = int(rng.choice([1, 1, 1, 3]))
+    grid = int(rng.choice([0, 0, 5, 152]))
+    overlap = bool(rng.integers(0, 2))
+    count = int(rng.integers(50, 400))
+    sizes = [int(rng.choice([0, 1, 15, 17, 4096, 30_000, 65_536, 262_144, 262_145, 300_000])) for _ in range(count)]
+    laws = [synth.degenerate(int(rng.integers(0, 256)), 0.95), synth.normal(128, 8), synth.uniform()]
+    chunks = [synth.host(sizes[c], laws[(c // int(rng.integers(2, 9))) % 3], SEED + 3000 + case, c) for c in range(count)]
+    ref = oracle.StreamOracle(budget, mode=mode, window=window)
+    recs = [ref.push(ch) for ch in chunks]
+    offs, pos = [], 0
+    for c in range(count):
+        pos += int(rng.integers(0, 16))
+        offs.append(pos)
+        pos += sizes[c]
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((count, 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=budget, mode=mode, window=window, grid=grid, overlap=overlap)
+    cuts = sorted(set([0, count] + [int(x) for x in rng.integers(1, count, size=int(rng.integers(0, 6)))]))
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        st.push_many(np.uint64(bd.data_ptr()) + np.array(offs[lo:hi], dtype=np.uint64),
+                     np.array(sizes[lo:hi], dtype=np.uint64),
+                     np.array([outs[j].data_ptr() for j in range(lo, hi)], dtype=np.uint64))
+    got = u32(outs.reshape(-1)).reshape(count, 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), (case, j)
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
