@@ -1097,6 +1097,9 @@ __global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_
   __shared__ float smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];  // one group of eight chunks
   const StreamDev* st = a.st;
   const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  // chained after the prediction (see predict_kernel): its samples first
+  pdl_launch_dependents();
+  pdl_wait();
   const unsigned long long W = a.window, g0 = a.first_chunk;
   // the window before the batch: chunks g0-W+1 .. g0-1
   float v = 0.0f;
@@ -1155,6 +1158,9 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
   __shared__ unsigned long long smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];
   StreamDev* st = a.st;
   const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  // chained after the counting launch (AUTO): its chunk histograms first
+  pdl_launch_dependents();
+  pdl_wait();
   const unsigned long long W = a.window, g0 = a.first_chunk;
   unsigned long long v = g0 > 0 ? __ldcg(&st->wmw[b]) : 0ull;
   for (uint32_t j0 = 0; j0 < a.count; j0 += 8) {
@@ -1524,18 +1530,18 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
                          kSmemBytes, s);
   } else if (st->autok) {
     // predictions, the window's prediction, the flat launch with the
-    // predicted kernels, the window, the recount
-    e = cudaLaunchKernel((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
+    // predicted kernels, the window, the recount, chained the same way
+    e = launch_chained((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)window_predict_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = launch_chained((const void*)window_predict_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
-                           flat_smem_bytes<A>(), s);
+      e = launch_chained((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                         flat_smem_bytes<A>(), s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = launch_chained((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
-                           kSmemBytes, s);
+      e = launch_chained((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
+                         kSmemBytes, s);
   } else if (st->flat && (windowed || st->predict)) {
     e = cudaSuccess;
     if (st->predict) e = cudaLaunchKernel((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
