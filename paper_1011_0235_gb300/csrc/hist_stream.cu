@@ -57,6 +57,7 @@ struct StreamDev {
   uint32_t wsn[kChunkRing];                    // pixels in chunk g's sample
   uint32_t wn[kChunkRing];                     // chunk g's size
   unsigned long long wmw[HIST_BINS];
+  uint32_t lwin[kLaunchRing];                  // window switches written, by launch (window_flat_kernel)
   uint32_t lredo[kLaunchRing][kMaxBatch];
   unsigned long long lchunks[kLaunchRing];     // by flat launch number mod kLaunchRing
   hist_pattern lpat[kLaunchRing][2];
@@ -1074,137 +1075,123 @@ __global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constan
 }
 
 // A window of W > 1 chunks on the flat path.  The window histogram after
-// chunk g is the one after chunk g-1 plus chunk g minus chunk g-W, so one
-// CTA runs through the batch's chunks in order, bin b in thread b; per chunk
-// each warp reduces its 32 bins' maximum and sum without a barrier, and the
-// switches of each group of eight chunks follow the group.  Chunks are numbered from the stream's first
-// flat chunk (a resumed stream restarts at 0), and a chunk before number 0
-// counts as empty.
+// chunk g is the sum of the histograms of chunks g-W+1 .. g (chunks before
+// number 0 count as empty; chunks are numbered from the stream's first flat
+// chunk, and a resumed stream restarts at 0).  The histograms of the last
+// kChunkRing chunks stay in rings, so each chunk's window is summed on its
+// own: one CTA per chunk of the batch, bin b in thread b, W loads per thread
+// with eight in flight, then the window's largest bin and total.  (One CTA
+// running through the chunks in order, adding chunk g and subtracting chunk
+// g-W, took 90 us for the predictions and 27 us for the exact switches of a
+// launch of 64 chunks at W = 32.)
 
-// Predicted window switches (AUTO): the same running sum over the chunks'
-// samples, each scaled by its chunk's bytes over its sample's pixels, in
-// FP32 (a prediction: FP64 is slow on this part, and a wrong guess costs a
-// recount, never a wrong result).  The loads of eight chunks are issued
-// before any is added.
-__device__ __forceinline__ float window_est(const StreamDev* st, unsigned long long g, int b) {
-  const uint32_t slot = (uint32_t)(g % kChunkRing);
-  const uint32_t sn = __ldcg(&st->wsn[slot]);
-  return sn ? (float)__ldcg(&st->wsamp[slot][b]) * ((float)__ldcg(&st->wn[slot]) / (float)sn) : 0.0f;
+// Largest bin and total of a 256-bin window held one bin per thread (all
+// threads call; two barriers); returned to every thread.
+template <class T>
+__device__ __forceinline__ void window_max_sum(T v, T* smax, T* ssum, T& mx, T& sm) {
+  const int b = threadIdx.x, w = b >> 5;
+  T m = v, s = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T m2 = __shfl_xor_sync(0xffffffffu, m, o);
+    m = m2 > m ? m2 : m;
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  if ((b & 31) == 0) {
+    smax[w] = m;
+    ssum[w] = s;
+  }
+  __syncthreads();
+  mx = smax[0];
+  sm = ssum[0];
+#pragma unroll
+  for (int i = 1; i < HIST_BINS / 32; ++i) {
+    mx = smax[i] > mx ? smax[i] : mx;
+    sm += ssum[i];
+  }
+  __syncthreads();
 }
 
+// Predicted window switches (AUTO): the same window over the chunks'
+// samples, each scaled by its chunk's bytes over its sample's pixels, in
+// FP32 (a prediction: FP64 is slow on this part, and a wrong guess costs a
+// recount, never a wrong result).  CTA j: chunk g0 + j.
 template <class A>
 __global__ void __launch_bounds__(HIST_BINS) window_predict_kernel(const __grid_constant__ A a) {
-  __shared__ float smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];  // one group of eight chunks
+  __shared__ float scale[HIST_WINDOW_MAX];
+  __shared__ float smax[HIST_BINS / 32], ssum[HIST_BINS / 32];
   const StreamDev* st = a.st;
-  const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  const int b = threadIdx.x;
   // chained after the prediction (see predict_kernel): its samples first
   pdl_launch_dependents();
   pdl_wait();
-  const unsigned long long W = a.window, g0 = a.first_chunk;
-  // the window before the batch: chunks g0-W+1 .. g0-1
+  const unsigned long long W = a.window, g = a.first_chunk + blockIdx.x;
+  const unsigned long long first = g >= W - 1 ? g - (W - 1) : 0ull;
+  const uint32_t len = (uint32_t)(g - first + 1);
+  // each window chunk's scale, one thread per chunk
+  for (uint32_t k = (uint32_t)b; k < len; k += HIST_BINS) {
+    const uint32_t slot = (uint32_t)((first + k) % kChunkRing);
+    const uint32_t sn = __ldcg(&st->wsn[slot]);
+    scale[k] = sn ? (float)__ldcg(&st->wn[slot]) / (float)sn : 0.0f;
+  }
+  __syncthreads();
   float v = 0.0f;
-  const unsigned long long first = g0 >= W - 1 ? g0 - (W - 1) : 0ull;
-  for (unsigned long long g = first; g < g0; g += 8) {
-    float e[8];
+  for (uint32_t k0 = 0; k0 < len; k0 += 8) {
+    uint32_t h[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) e[k] = g + k < g0 ? window_est(st, g + k, b) : 0.0f;
+    for (int k = 0; k < 8; ++k)
+      h[k] = k0 + k < len ? __ldcg(&st->wsamp[(first + k0 + k) % kChunkRing][b]) : 0u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v += e[k];
+    for (int k = 0; k < 8; ++k)
+      if (k0 + k < len) v += (float)h[k] * scale[k0 + k];
   }
-  for (uint32_t j0 = 0; j0 < a.count; j0 += 8) {
-    float add[8], sub[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const unsigned long long g = g0 + j0 + k;
-      add[k] = j0 + k < a.count ? window_est(st, g, b) : 0.0f;
-      sub[k] = j0 + k < a.count && g >= W ? window_est(st, g - W, b) : 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (j0 + k >= a.count) break;
-      v = fmaxf(v + add[k] - sub[k], 0.0f);
-      float m = v, sm = v;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-      }
-      if (lane == 0) {
-        smax[k][w] = m;
-        ssum[k][w] = sm;
-      }
-    }
-    // the group's switches (thread k: chunk j0 + k), then the next group
-    __syncthreads();
-    if (b < 8 && j0 + b < a.count) {
-      float m = 0.0f, sm = 0.0f;
-      for (int i = 0; i < HIST_BINS / 32; ++i) {
-        m = fmaxf(m, smax[b][i]);
-        sm += ssum[b][i];
-      }
-      a.st->rpred[(g0 + j0 + b) % kChunkRing] =
-          (sm > 0.0f && m * 1000.0f >= sm * (float)a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-    }
-    __syncthreads();
-  }
+  float mx, sm;
+  window_max_sum(v, smax, ssum, mx, sm);
+  if (b == 0)
+    a.st->rpred[g % kChunkRing] = (sm > 0.0f && mx * 1000.0f >= sm * (float)a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
 }
 
-// Exact window switches after the flat launch; the stream's switch and last
-// kernel; in AUTO mode the list of chunks whose predicted kernel was not the
-// one their predecessor's window switch chose.
+// Exact window switches after the flat launch, one CTA per chunk; the CTA
+// of the last chunk writes the window after it.  The CTA that completes the
+// launch's count then writes the stream's switch and last kernel and, in
+// AUTO mode, lists the chunks whose predicted kernel was not the one their
+// predecessor's window switch chose.
 template <class A>
 __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_constant__ A a) {
-  // one group of eight chunks
-  __shared__ unsigned long long smax[8][HIST_BINS / 32], ssum[8][HIST_BINS / 32];
+  __shared__ unsigned long long smax[HIST_BINS / 32], ssum[HIST_BINS / 32];
+  __shared__ int last;
   StreamDev* st = a.st;
-  const int b = threadIdx.x, w = b >> 5, lane = b & 31;
+  const int b = threadIdx.x;
   // chained after the counting launch (AUTO): its chunk histograms first
   pdl_launch_dependents();
   pdl_wait();
-  const unsigned long long W = a.window, g0 = a.first_chunk;
-  unsigned long long v = g0 > 0 ? __ldcg(&st->wmw[b]) : 0ull;
-  for (uint32_t j0 = 0; j0 < a.count; j0 += 8) {
-    // the loads of eight chunks before any is added
-    uint32_t add[8], sub[8];
+  const unsigned long long W = a.window, g0 = a.first_chunk, g = g0 + blockIdx.x;
+  const unsigned long long first = g >= W - 1 ? g - (W - 1) : 0ull;
+  const uint32_t len = (uint32_t)(g - first + 1);
+  unsigned long long v = 0;
+  for (uint32_t k0 = 0; k0 < len; k0 += 8) {
+    uint32_t h[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const unsigned long long g = g0 + j0 + k;
-      add[k] = j0 + k < a.count ? __ldcg(&st->whist[g % kChunkRing][b]) : 0u;
-      sub[k] = j0 + k < a.count && g >= W ? __ldcg(&st->whist[(g - W) % kChunkRing][b]) : 0u;
-    }
+    for (int k = 0; k < 8; ++k)
+      h[k] = k0 + k < len ? __ldcg(&st->whist[(first + k0 + k) % kChunkRing][b]) : 0u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (j0 + k >= a.count) break;
-      v += add[k];
-      v -= sub[k];
-      unsigned long long m = v, sm = v;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, m, o);
-        m = m2 > m ? m2 : m;
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-      }
-      if (lane == 0) {
-        smax[k][w] = m;
-        ssum[k][w] = sm;
-      }
-    }
-    // the group's switches (thread k: chunk j0 + k), then the next group
-    __syncthreads();
-    if (b < 8 && j0 + b < a.count) {
-      unsigned long long m = 0, sm = 0;
-      for (int i = 0; i < HIST_BINS / 32; ++i) {
-        m = smax[b][i] > m ? smax[b][i] : m;
-        sm += ssum[b][i];
-      }
-      st->rflag[(g0 + j0 + b) % kChunkRing] = reaches_theta(m, sm, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
-    }
-    __syncthreads();
+    for (int k = 0; k < 8; ++k) v += h[k];
   }
-  st->wmw[b] = v;
-  __threadfence();
-  __syncthreads();
+  unsigned long long mx, sm;
+  window_max_sum(v, smax, ssum, mx, sm);
+  if (b == 0) st->rflag[g % kChunkRing] = reaches_theta(mx, sm, a.theta) ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
+  if (blockIdx.x + 1 == a.count) st->wmw[b] = v;
   const uint32_t ls = (uint32_t)(a.launch % kLaunchRing);
+  __syncthreads();
+  if (b == 0) {
+    // the barrier orders the CTA's writes before this fence
+    __threadfence();
+    last = atomicAdd(&st->lwin[ls], 1u) + 1u == a.count;
+  }
+  __syncthreads();
+  if (!last) return;
+  // every chunk's switch is written (and fenced)
+  __threadfence();
   uint32_t kern = a.mode == HIST_MODE_ADAPTIVE ? HIST_FLAG_ADAPTIVE : HIST_FLAG_PLAIN;
   if (a.mode == HIST_MODE_AUTO) {
     // chunk j's kernel had to be chunk j-1's window switch (chunk 0: the stream's)
@@ -1215,8 +1202,9 @@ __global__ void __launch_bounds__(HIST_BINS) window_flat_kernel(const __grid_con
     }
   }
   if (b == 0) {
-    st->flag = st->rflag[(g0 + a.count - 1) % kChunkRing];
+    st->flag = __ldcg(&st->rflag[(g0 + a.count - 1) % kChunkRing]);
     st->last_kernel = kern;
+    st->lwin[ls] = 0;
   }
 }
 
@@ -1533,12 +1521,12 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
     // predicted kernels, the window, the recount, chained the same way
     e = launch_chained((const void*)predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
-      e = launch_chained((const void*)window_predict_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = launch_chained((const void*)window_predict_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = launch_chained((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
                          flat_smem_bytes<A>(), s);
     if (e == cudaSuccess)
-      e = launch_chained((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = launch_chained((const void*)window_flat_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
     if (e == cudaSuccess)
       e = launch_chained((const void*)auto_redo_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
                          kSmemBytes, s);
@@ -1549,7 +1537,7 @@ int launch_batch(hist_stream* st, uint32_t count, const uint8_t* const* ins, con
       e = cudaLaunchKernel((const void*)batch_flat_kernel<A>, dim3((unsigned)st->grid), dim3(kThreads), params,
                            flat_smem_bytes<A>(), s);
     if (e == cudaSuccess && windowed)
-      e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(1), dim3(HIST_BINS), params, 0, s);
+      e = cudaLaunchKernel((const void*)window_flat_kernel<A>, dim3(count), dim3(HIST_BINS), params, 0, s);
   } else {
     // PLAIN or ADAPTIVE at the full budget, window 1: one launch, which may
     // start while the previous launch on `s` finishes (see batch_flat_kernel)
