@@ -713,10 +713,16 @@ def run_part(args):
         # chunks) through an AUTO stream: 3 pushes of 64 chunks
         xdg = gen_workload_device(torch, synth, 64, synth.SEED_BASE + 3,
                                   lambda c: synth.degenerate(90, 0.95) if (c // 8) % 2 == 0 else synth.uniform())
-        st = hl.Stream(budget=8192, mode=hl.MODE_AUTO)
         ptrs = [xdg.data_ptr() + c * CHUNK for c in range(64)]
-        el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
-        out = {"auto_gbs": round(64 * CHUNK * 2 / el / 1e9, 1), "recounted": st.state().recounted}
+        out = {}
+        # a window of one chunk, then a window of 32 chunks (its window
+        # kernels, one CTA per chunk), both with the chunks declared complete
+        for name, window in (("auto", 1), ("auto_window32", 32)):
+            st = hl.Stream(budget=8192, mode=hl.MODE_AUTO, window=window, overlap=True)
+            el = time_steps(torch, lambda: st.push_many(ptrs, [CHUNK] * 64), 1, 2)
+            out[name + "_gbs"] = round(64 * CHUNK * 2 / el / 1e9, 1)
+            out[name + "_recounted"] = st.state().recounted
+            st.close()
     elif args.profile_part == "smallchunks":
         # 256 MiB of N(128, 8) in 4096 chunks of 64 KiB through an adaptive
         # stream: one push_many, four counting launches of 1024 chunks
