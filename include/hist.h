@@ -188,9 +188,12 @@ int hist_adaptive(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  * the counting launch still starts early and clears its tables, but reads
  * no chunk byte before the work before it on `s` has completed, so a chunk
  * written by the kernel just before the push -- even one that lets its
- * dependents start early -- is read whole.  Only the one-launch paths (PLAIN,
- * or ADAPTIVE at HIST_BUDGET_MAX, with a window of one chunk) overlap at
- * all; the others always run after the work before them. */
+ * dependents start early -- is read whole.  The one-launch paths (PLAIN,
+ * or ADAPTIVE at HIST_BUDGET_MAX, with a window of one chunk) overlap the
+ * counting itself; an AUTO push (prediction, count, recount, chained the
+ * same way) overlaps only its prediction's sampling with the work before
+ * it, since the count needs the prediction; the other paths run after the
+ * work before them. */
 #define HIST_OVERLAP_PUSHES 1u
 
 typedef struct hist_config {
