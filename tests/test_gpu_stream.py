@@ -786,3 +786,28 @@ def test_random_pushes(case):
         assert np.array_equal(got[j], r.hist), (case, j)
     _check_state(st.state(), ref, recs[-1])
     st.close()
+
+
+@pytest.mark.parametrize("grid", [2, 5, 0])
+@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
+def test_large_chunks_among_many_tiny_ones(mode, grid):
+    """A push of mostly tiny chunks with two large ones, counted by 2, 5 or
+    every CTA: with few CTAs a range holds hundreds of tiny chunks (the size
+    reads and the groups' lists run past their 32- and 64-entry windows),
+    beside pieces of the large chunks; empty chunks and 16-byte chunks at
+    the launch's end.  Every output and the state equal the oracle's."""
+    sizes = [24 << 20] + [16] * 600 + [0, 5] + [9 << 20] + [4096] * 300 + [16, 0, 16]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 50, SEED + 400 + mode)
+    ref = oracle.StreamOracle(8192, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    bd = dev(np.concatenate(chunks + [np.zeros(16, np.uint8)]))
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=mode, grid=grid)
+    st.push_many(np.uint64(bd.data_ptr()) + offs[:-1], np.array(sizes, dtype=np.uint64),
+                 np.array([outs[j].data_ptr() for j in range(len(chunks))], dtype=np.uint64))
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
