@@ -78,3 +78,33 @@ def test_chunk_tables_refuse_negative_and_byte_swapped_integers():
         hl._u64_array([3, -1], 2, "x")
     addr, keep = hl._u64_array(np.array([7, 9], dtype="<u8"), 2, "x")
     assert keep[1] == 9
+
+
+def test_chunk_table_address_paths():
+    # the array's own buffer is passed (no copy) when it is writable, and
+    # through numpy's pointer when it is read-only or empty; both give the
+    # same address, and the returned owner keeps the buffer alive
+    import numpy as np
+
+    a = np.arange(6, dtype=np.uint64) * np.uint64(3)
+    addr, keep = hl._u64_array(a, 6, "x")
+    assert addr == a.ctypes.data and keep is a
+    b = a.copy()
+    b.setflags(write=False)
+    addr, keep = hl._u64_array(b, 6, "x")
+    assert addr == b.ctypes.data
+    e = np.zeros(0, dtype=np.uint64)
+    addr, keep = hl._u64_array(e, 0, "x")
+    assert keep.size == 0
+    t = torch.arange(4, dtype=torch.int64)
+    addr, keep = hl._u64_array(t, 4, "x")
+    assert addr == t.data_ptr()
+
+
+def test_stream_handle_of_an_explicit_stream():
+    # a stream passed by the caller is used as it is (no lookup of the
+    # current one)
+    class FakeStream:
+        cuda_stream = 0x1234
+
+    assert hl._stream_ptr(FakeStream()) == 0x1234
