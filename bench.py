@@ -521,7 +521,7 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     torch.cuda.synchronize()
     out = {"streams": streams, "payload_pool_bytes": streams * region, "hbm_budget": 32 << 30}
 
-    def run(reqs, at_zero=False):
+    def run(reqs, at_zero=False, mode=hl.MODE_AUTO):
         count = len(reqs)
         outs = torch.empty((count, 256), dtype=torch.int32, device="cuda")
         R = (_abi.Request * count)()
@@ -530,7 +530,7 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
             R[i].stream, R[i].d_in, R[i].n = r.stream, pool.data_ptr() + r.offset, r.n
             R[i].d_out, R[i].tag = outs.data_ptr() + i * 1024, i
         torch.cuda.synchronize()
-        srv = hl.Server(streams=streams)
+        srv = hl.Server(streams=streams, mode=mode)
         k = min(count, 64)
         srv.replay((_abi.Request * k)(*R[:k]), timeout_ms=60000)  # warm-up: first launches, clocks
         # and a burst at t = 0, which batches more than 32 requests (the large kernel variant)
@@ -539,7 +539,7 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
             burst[i].arrival_ns = 0
         srv.replay(burst, timeout_ms=60000)
         srv.close()
-        srv = hl.Server(streams=streams)
+        srv = hl.Server(streams=streams, mode=mode)
         done = srv.replay(R, timeout_ms=120000)
         st = srv.stats()
         srv.close()
@@ -596,6 +596,12 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     nbytes = float(sum(r.n for r in reqs))
     cap["auto_kernels_alone_gbs"] = round(nbytes / sum(r.n / rate[r.stream] for r in reqs) / 1e9, 1)
     out["capacity"] = cap
+    # the same burst with every stream in ADAPTIVE mode (the full table for
+    # every law): what the serving loop delivers when the switch's choice of
+    # the per-warp kernel does not bound it
+    cad = run(reqs, at_zero=True, mode=hl.MODE_ADAPTIVE)
+    cad["frac_of_hbm"] = round(cad["served_gbs"] / hbm, 4)
+    out["capacity_adaptive"] = cad
     del pool
     return out
 
