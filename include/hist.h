@@ -544,17 +544,19 @@ int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  *   poll    writes one hist_completion per request that has finished since
  *           the last poll -- a request's epilogue on the GPU writes its
  *           completion word in pinned host memory once the request's output
- *           is written (the stream's state is updated right after, before
- *           the batch retires), so a request completes without waiting for
- *           the rest of its batch -- and releases the
+ *           is written, so a request completes without waiting for the rest
+ *           of its batch; it then updates the stream's state and writes the
+ *           request's state word, and poll gives a returned request's stream
+ *           back to admission once that word is seen -- and releases the
  *           batch slots whose completion event has fired (with them, their
- *           streams and their bytes of the budget); then it admits the next
- *           batch if one of max_inflight batch slots is free: in FIFO order,
- *           every queued request whose stream has no request on the GPU and
- *           whose bytes fit the HBM budget (bytes of all requests on the GPU
- *           <= hbm_budget), up to max_batch requests.  The batch is one
- *           kernel on the slot's own CUDA stream, so batches overlap on the
- *           device.
+ *           bytes of the budget); then it admits the next batch if one of
+ *           max_inflight batch slots is free: in FIFO order, every queued
+ *           request whose stream has no request on the GPU and whose bytes
+ *           fit the HBM budget (bytes of all requests on the GPU <=
+ *           hbm_budget), up to max_batch requests.  The batch is one kernel
+ *           on the slot's own CUDA stream, so batches overlap on the device:
+ *           a stream's next request may run in a batch that starts while its
+ *           previous request's batch is still counting.
  *   drain   polls until nothing is queued or in flight (bounded by
  *           timeout_ms; HIST_ETIMEDOUT when it runs out).
  * A request's bytes (d_in, n < 2^32, any alignment) must stay valid and
@@ -605,9 +607,9 @@ typedef struct hist_server hist_server;
 
 void hist_server_config_init(hist_server_config* c);
 /* Allocates the per-stream state, max_inflight batch slots (about 1.1 MiB of
- * device memory each) and their CUDA streams, and 32 KiB of pinned, mapped
- * host memory for the requests' completion words; synchronizes the device.
- * HIST_EINVAL for a bad config. */
+ * device memory each) and their CUDA streams, and 64 KiB of pinned, mapped
+ * host memory for the requests' completion and state words; synchronizes
+ * the device.  HIST_EINVAL for a bad config. */
 int hist_server_create(const hist_server_config* cfg, hist_server** out);
 /* Waits for the GPU, then frees everything. */
 int hist_server_destroy(hist_server* srv);

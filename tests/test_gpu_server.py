@@ -243,6 +243,39 @@ def test_replay_poisson_schedule(pool16):
     srv.close()
 
 
+@pytest.mark.parametrize("streams,max_batch,max_inflight", [(16, 16, 4), (16, 64, 2), (4, 256, 8)])
+def test_burst_of_back_to_back_requests(pool16, streams, max_batch, max_inflight):
+    """Every request of the schedule arrives at t = 0, many per stream: a
+    stream goes back to admission as soon as its request's state is written,
+    so its next request may run in a batch that starts while the first one's
+    batch is still counting.  Outputs and end states against the oracle; a
+    stream's requests complete in its order, and each is admitted only after
+    the stream's previous request has completed."""
+    reqs = workloads.serving_schedule(5000, 320, streams=streams, region=4 << 20, size_lo=4 << 10,
+                                      size_hi=4 << 20, seed=SEED + 60 + streams + max_batch,
+                                      special_sizes=EDGE_SIZES)
+    hists, refs, last = _oracle(pool16, reqs)
+    srv = hl.Server(streams=streams, max_batch=max_batch, max_inflight=max_inflight)
+    out = torch.full((len(reqs), 256), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    R = (_abi.Request * len(reqs))()
+    for i, r in enumerate(reqs):
+        R[i].arrival_ns, R[i].stream, R[i].d_in, R[i].n = 0, r.stream, pool16.ptr(r), r.n
+        R[i].d_out, R[i].tag = out[i].data_ptr(), i
+    done = srv.replay(R, timeout_ms=120000)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), hists)
+    for s in range(streams):
+        mine = [done[i] for i, r in enumerate(reqs) if r.stream == s]
+        assert [c.done_ns for c in mine] == sorted(c.done_ns for c in mine)
+        for a, b in zip(mine, mine[1:]):
+            assert b.admit_ns >= a.done_ns
+    for s in sorted(refs):
+        _check_state(srv.stream_state(s), refs[s], last[s])
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.queued == 0 and st.inflight_bytes == 0
+    srv.close()
+
+
 def test_replay_times_out_on_the_host(pool16):
     """The host loop's own bound: a schedule whose arrivals run to 2 s,
     replayed with a 100 ms limit, returns HIST_ETIMEDOUT after about 100 ms;
