@@ -363,8 +363,10 @@ class Server:
     """Serving loop over many streams, continuously batched (``hist_server_*``).
 
     Each of `streams` streams keeps its adaptive state on the device; a request
-    is the next chunk of one stream.  ``submit`` queues, ``poll`` retires
-    finished batches and admits the next one, ``drain`` runs until idle.  The
+    is the next chunk of one stream.  ``submit`` queues, ``poll`` returns
+    finished requests (giving each one's stream back to admission once its
+    state is written), releases finished batches and admits the next one,
+    ``drain`` runs until idle.  The
     bytes of a request must already be on the device when it is submitted
     (synchronize the stream that wrote them), and stay unchanged, like its
     output buffer, until its completion has been returned.
