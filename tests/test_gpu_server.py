@@ -276,6 +276,37 @@ def test_burst_of_back_to_back_requests(pool16, streams, max_batch, max_inflight
     srv.close()
 
 
+@pytest.mark.parametrize("cap", [1, 3])
+def test_poll_with_a_small_cap(pool16, cap):
+    """poll returns at most `cap` completions; a finished request left for a
+    later poll keeps its stream busy, so a stream's completions still come
+    back in its order and its next request waits for them."""
+    reqs = workloads.serving_schedule(5000, 200, streams=8, region=4 << 20, size_lo=4 << 10, size_hi=1 << 20,
+                                      seed=SEED + 70 + cap, special_sizes=EDGE_SIZES)
+    hists, refs, last = _oracle(pool16, reqs)
+    srv = hl.Server(streams=8, max_batch=8, max_inflight=4)
+    out = torch.full((len(reqs), 256), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for i, r in enumerate(reqs):
+        srv.submit_ptr(r.stream, pool16.ptr(r), r.n, out[i].data_ptr(), tag=i)
+    buf = (_abi.Completion * cap)()
+    n = ctypes.c_uint32()
+    order, t0 = [], time.monotonic()
+    while len(order) < len(reqs):
+        assert time.monotonic() - t0 < 120, "requests did not complete"
+        assert hl.lib().hist_server_poll(srv._h, buf, cap, ctypes.byref(n)) == _abi.OK
+        assert n.value <= cap
+        order += [buf[i].tag for i in range(n.value)]
+    assert sorted(order) == list(range(len(reqs)))
+    for s in range(8):
+        mine = [t for t in order if reqs[t].stream == s]
+        assert mine == sorted(mine)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), hists)
+    for s in sorted(refs):
+        _check_state(srv.stream_state(s), refs[s], last[s])
+    srv.close()
+
+
 def test_replay_times_out_on_the_host(pool16):
     """The host loop's own bound: a schedule whose arrivals run to 2 s,
     replayed with a 100 ms limit, returns HIST_ETIMEDOUT after about 100 ms;
