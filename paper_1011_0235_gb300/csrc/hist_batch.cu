@@ -76,6 +76,23 @@ __device__ void size_prefix(const size_t* sizes, uint32_t count, unsigned long l
   __syncthreads();
 }
 
+// A CTA boundary at position x of the concatenated bytes, moved to a 32 KiB
+// boundary of its image's memory (split_point; not past the image's end).
+// Both CTAs of the cut compute it from the same x.
+__device__ unsigned long long batch_cut(const BatchImgArgs& a, const unsigned long long* pre, unsigned long long x) {
+  if (x >= pre[a.count]) return x;
+  uint32_t i = 0, hi = a.count;  // the last image with pre[i] <= x: x lies inside it
+  while (i + 1 < hi) {
+    const uint32_t mid = (i + hi) >> 1;
+    if (pre[mid] <= x) i = mid;
+    else hi = mid;
+  }
+  const unsigned long long off = x - pre[i], n = pre[i + 1] - pre[i];
+  if (off == 0) return x;
+  const unsigned long long c = split_point(a.ptrs[i], off);
+  return pre[i] + (c < n ? c : n);
+}
+
 template <int UNROLL, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -87,8 +104,8 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgAr
   zero_table(table);
   size_prefix(a.sizes, a.count, pre);
   const unsigned long long total = pre[a.count];
-  const unsigned long long lo0 = total * blockIdx.x / gridDim.x;
-  const unsigned long long hi = total * (blockIdx.x + 1) / gridDim.x;
+  const unsigned long long lo0 = batch_cut(a, pre, total * blockIdx.x / gridDim.x);
+  const unsigned long long hi = batch_cut(a, pre, total * (blockIdx.x + 1) / gridDim.x);
   if (lo0 >= hi) return;
   // first image whose bytes reach past lo0
   uint32_t lo_i = 0, hi_i = a.count;

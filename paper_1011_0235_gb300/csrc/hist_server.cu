@@ -264,11 +264,13 @@ __global__ void __launch_bounds__(kThreads, 1) server_batch_kernel(const __grid_
       }
       continue;
     }
-    // this CTA's bytes of the request: its cost range cut to [0, n); a
-    // request of at most a quarter of a CTA's range is not split (the range
-    // holding its first cost position counts it whole, with no accumulator)
-    unsigned long long b0 = lo > p0 ? lo - p0 : 0ull;
-    unsigned long long e0 = hi - p0 < (unsigned long long)q.n ? hi - p0 : (unsigned long long)q.n;
+    // this CTA's bytes of the request: its cost range cut to [0, n), each
+    // cut moved to a 32 KiB boundary of the request's memory; a request of
+    // at most a quarter of a CTA's range is not split (the range holding
+    // its first cost position counts it whole, with no accumulator)
+    unsigned long long b0 = lo > p0 ? split_point(q.in, lo - p0) : 0ull;
+    unsigned long long e0 = split_point(q.in, hi - p0);
+    if (e0 > (unsigned long long)q.n) e0 = q.n;
     if ((unsigned long long)q.n * 4 <= W / gridDim.x) {
       if (p0 < lo) continue;
       b0 = 0;

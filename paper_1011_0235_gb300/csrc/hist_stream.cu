@@ -156,7 +156,7 @@ __device__ __forceinline__ Geo chunk_geo(const ChunkDesc& d) {
   Geo g;
   g.body = reinterpret_cast<const uint4*>(d.in + sp.head);
   const uint32_t nvec = (uint32_t)sp.nvec;
-  const uint32_t per = (nvec + gridDim.x - 1) / gridDim.x;
+  const uint32_t per = (uint32_t)vecs_per_part(nvec, gridDim.x);
   const uint32_t b = per * blockIdx.x;
   g.end = b + per < nvec ? b + per : nvec;
   g.begin = b < g.end ? b : g.end;
@@ -223,10 +223,11 @@ constexpr unsigned long long kFlatTailCost = 1ull << 20;
 __host__ __device__ __forceinline__ unsigned long long flat_tail(unsigned long long n, uint32_t j, uint32_t count) {
   return j + 2 >= count && n <= kGroupChunkMax ? kFlatTailCost : 0ull;
 }
-// chunk j's cost: n bytes of weight w, the fixed cost, the tail cost
+// chunk j's cost: n bytes of weight w, then the fixed cost and the tail
+// cost in `unit`s per byte (the weight of a byte of the full table)
 __host__ __device__ __forceinline__ unsigned long long flat_cost(unsigned long long n, uint32_t w, uint32_t j,
-                                                                 uint32_t count) {
-  return n * w + kFlatChunkCost + flat_tail(n, j, count);
+                                                                 uint32_t count, uint32_t unit = 1) {
+  return n * w + unit * (kFlatChunkCost + flat_tail(n, j, count));
 }
 
 // Whole small chunks are counted by groups of warps (flat_groups), thread b
@@ -260,15 +261,26 @@ __device__ __forceinline__ uint32_t flat_kernel_of(const A& a, uint32_t j) {
   return j == 0 ? a.st->lk0[a.launch % kLaunchRing] : a.st->rpred[(a.first_chunk + j - 1) % kChunkRing];
 }
 
-// In AUTO mode (the launches whose ranges the host does not plan) a chunk
-// predicted to run the plain kernel
-// costs twice its bytes (the plain kernel's rate on wide data is about half
-// the full table's); wt[j] holds chunk j's weight.
+// In AUTO mode (the launches whose ranges the host does not plan) a byte of
+// a chunk predicted to run the plain kernel weighs kPlainWeight, a byte of
+// the full table kFullWeight, and the fixed costs count kFullWeight per
+// byte-equivalent; every other launch weighs every byte 1.  wt[j] holds
+// chunk j's weight.
 // The chunk table sits in the kernel's parameters, which are read through the
 // constant cache: the distinct addresses of one warp's load are served one
 // after another (4 us per launch when thread t read chunk t's size), so each
 // warp reads its chunks' sizes with a warp-uniform index into shared memory
 // (sz), where the rest of the launch reads them.
+// The plain kernel counts wide data at well under half the full table's
+// rate; on the degenerate workload (8 chunks of one value, 8 uniform, in
+// turn) 5 : 2 measured best: 3.76 TB/s, against 3.54 at 2 : 1, 3.65 at
+// 9 : 4 and 3.41 at 3 : 1.
+constexpr uint32_t kFullWeight = 2, kPlainWeight = 5;
+template <class A>
+__device__ __forceinline__ uint32_t flat_unit(const A& a) {
+  return a.mode == HIST_MODE_AUTO && !a.planned ? kFullWeight : 1u;
+}
+
 template <class A>
 __device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt, uint32_t* sz) {
   __shared__ unsigned long long wsum[kWarps];
@@ -278,10 +290,11 @@ __device__ void flat_prefix(const A& a, unsigned long long* pre, uint32_t* wt, u
     if (lane == 0) sz[j] = n;
   }
   __syncthreads();
-  uint32_t weight = 1;
-  if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = 2;
+  const uint32_t unit = flat_unit(a);
+  uint32_t weight = unit;
+  if (t < (int)a.count && a.mode == HIST_MODE_AUTO && flat_kernel_of(a, t) == HIST_FLAG_PLAIN) weight = kPlainWeight;
   if (t < (int)a.count) wt[t] = weight;
-  const unsigned long long c = t < (int)a.count ? flat_cost(sz[t], weight, t, a.count) : 0ull;
+  const unsigned long long c = t < (int)a.count ? flat_cost(sz[t], weight, t, a.count, unit) : 0ull;
   unsigned long long x = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -698,7 +711,7 @@ __device__ __noinline__ uint32_t flat_sizes(const A& a, uint32_t j0, uint32_t* s
 }
 
 // Count the cost range [x0, x1) of the batch.  Chunk j's byte b sits at
-// cost pre[j] + b wt[j] (after kFlatTailCost for the last two chunks); a
+// cost pre[j] + b wt[j] (after the tail cost for the last two chunks); a
 // range takes the bytes whose cost position it holds.  All threads call.
 template <class A>
 __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const uint32_t* wt,
@@ -706,6 +719,7 @@ __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const 
                                uint32_t* lut, FlatShared<A::kCap>& fs) {
   uint32_t nwl = 0;
   uint32_t j = 0;
+  const uint32_t unit = flat_unit(a);
   unsigned long long p0;  // cost position of chunk j
   if (a.planned) {
     j = a.plan_j[blockIdx.x];
@@ -732,7 +746,7 @@ __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const 
   for (; j < a.count && p0 < x1; ++j, p0 = p1) {
     if (a.planned && j == wend) wend = flat_sizes(a, j, fs.sz);
     const uint32_t n = fs.sz[j], w = a.planned ? 1u : wt[j];
-    p1 = p0 + flat_cost(n, w, j, a.count);
+    p1 = p0 + flat_cost(n, w, j, a.count, unit);
     const uint32_t pn = prev_n;
     prev_n = n;
     if (n == 0) {
@@ -764,10 +778,10 @@ __device__ uint32_t flat_range(const A& a, const unsigned long long* pre, const 
       continue;
     }
     // byte b sits at cost q0 + b w, after the chunk's tail cost
-    const unsigned long long q0 = p0 + flat_tail(n, j, a.count);
+    const unsigned long long q0 = p0 + unit * flat_tail(n, j, a.count);
     if (x1 <= q0) continue;
-    const unsigned long long c0 = x0 > q0 ? (x0 - q0 + w - 1) / w : 0ull;
-    const unsigned long long c1 = (x1 - q0 + w - 1) / w;
+    const unsigned long long c0 = x0 > q0 ? split_point(a.c[j].in, (x0 - q0 + w - 1) / w) : 0ull;
+    const unsigned long long c1 = split_point(a.c[j].in, (x1 - q0 + w - 1) / w);
     const unsigned long long e0 = c1 < (unsigned long long)n ? c1 : (unsigned long long)n;
     if (c0 < e0) flat_piece(a, j, (uint32_t)c0, (uint32_t)e0, table, lut, fs);
   }
@@ -832,8 +846,9 @@ __device__ __noinline__ void flat_groups(const A& a, uint32_t nwl, uint32_t* gta
     uint32_t* out = i < kGroupPrefetch ? fs.gout[i] : a.c[j].out;
     const Split sp = split_bytes(base, n);
     group_count(adaptive, reinterpret_cast<const uint4*>(base + sp.head), sp.nvec, table, gt);
+    const int L = (int)kLineBytes;
     if (gt < (int)sp.head) atomicAdd(&res[base[gt]], 1u);
-    else if (gt >= 16 && gt < 16 + (int)sp.tail) atomicAdd(&res[base[sp.head + sp.nvec * 16 + (gt - 16)]], 1u);
+    else if (gt >= L && gt < L + (int)sp.tail) atomicAdd(&res[base[sp.head + sp.nvec * 16 + (gt - L)]], 1u);
     group_sync(g);
     // reduce the table into res and clear it as it is read
     if (adaptive) {
@@ -1019,7 +1034,9 @@ __global__ void __launch_bounds__(HIST_BINS) predict_kernel(const __grid_constan
   const ChunkDesc d = a.c[blockIdx.x];
   h[t] = 0;
   __syncthreads();
-  const Split sp = split_bytes(d.in, d.n);
+  // the sample's vectors are counted from the chunk's first 16-byte
+  // boundary (a sample of 256 vectors gains nothing from whole lines)
+  const Split sp = split_bytes_at(d.in, d.n, 16);
   const uint4* body = reinterpret_cast<const uint4*>(d.in + sp.head);
   uint32_t sampled;
   if (sp.nvec >= kSampleVecs) {
