@@ -244,9 +244,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   const Split sp = split_bytes(in, n);
   const uint4* body = reinterpret_cast<const uint4*>(in + sp.head);
-  const size_t per = vecs_per_part(sp.nvec, gridDim.x);
-  const size_t end = per * (blockIdx.x + 1) < sp.nvec ? per * (blockIdx.x + 1) : sp.nvec;
-  const size_t begin = per * blockIdx.x < end ? per * blockIdx.x : end;
+  const size_t begin = part_begin(sp.nvec, gridDim.x, blockIdx.x);
+  const size_t end = part_begin(sp.nvec, gridDim.x, blockIdx.x + 1);
   uint32_t acc = 0;
   if (STAGE == 7) {
     __shared__ __align__(8) unsigned long long full[kStageBufs];

@@ -44,9 +44,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   const Split sp = split_bytes(in, n);
   const uint4* body = reinterpret_cast<const uint4*>(in + sp.head);
-  const size_t per = vecs_per_part(sp.nvec, gridDim.x);
-  const size_t end = per * (blockIdx.x + 1) < sp.nvec ? per * (blockIdx.x + 1) : sp.nvec;
-  const size_t begin = per * blockIdx.x < end ? per * blockIdx.x : end;
+  const size_t begin = part_begin(sp.nvec, gridDim.x, blockIdx.x);
+  const size_t end = part_begin(sp.nvec, gridDim.x, blockIdx.x + 1);
   count_range_dispatch<4>(cs.path, cs.lk, body, begin, end, table, lut, threadIdx.x, kThreads);
   flush_table(cs.path, cs.lk, table, cs.pat, lut, cs);
   if (blockIdx.x == 0) {

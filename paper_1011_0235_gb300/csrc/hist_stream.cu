@@ -155,11 +155,8 @@ __device__ __forceinline__ Geo chunk_geo(const ChunkDesc& d) {
   const Split sp = split_bytes(d.in, d.n);
   Geo g;
   g.body = reinterpret_cast<const uint4*>(d.in + sp.head);
-  const uint32_t nvec = (uint32_t)sp.nvec;
-  const uint32_t per = (uint32_t)vecs_per_part(nvec, gridDim.x);
-  const uint32_t b = per * blockIdx.x;
-  g.end = b + per < nvec ? b + per : nvec;
-  g.begin = b < g.end ? b : g.end;
+  g.begin = (uint32_t)part_begin(sp.nvec, gridDim.x, blockIdx.x);
+  g.end = (uint32_t)part_begin(sp.nvec, gridDim.x, blockIdx.x + 1);
   return g;
 }
 
