@@ -85,11 +85,15 @@ def test_loop_group_boundaries(nvec):
 
 
 def test_unaligned_bases():
-    base = synth.host((1 << 20) + 64, synth.degenerate(7, 0.5), SEED + 8)
+    """Bases at every offset of a 16-byte vector and across a 128-byte line
+    (the counting loop's vectors start on a line; a head of up to 127 bytes
+    is counted byte by byte), with sizes inside one head, a few lines and
+    several CTAs' ranges."""
+    base = synth.host((1 << 20) + 256, synth.degenerate(7, 0.5), SEED + 8)
     bd = dev(base)
     pat = pattern_dev(oracle.default_pattern(960))
-    for off in range(17):
-        for n in (5, 100, 40000 + off, (1 << 20) - off):
+    for off in list(range(17)) + [31, 48, 63, 64, 65, 96, 112, 127, 128, 129]:
+        for n in (5, 100, 127, 300, 40000 + off, (1 << 20) - off):
             ref = oracle.hist_u32(base[off:off + n])
             view = bd[off:off + n]
             assert np.array_equal(u32(hl.hist_plain(view)), ref), (off, n)

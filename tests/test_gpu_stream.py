@@ -811,3 +811,36 @@ def test_large_chunks_among_many_tiny_ones(mode, grid):
         assert np.array_equal(got[j], r.hist), j
     _check_state(st.state(), ref, recs[-1])
     st.close()
+
+
+@pytest.mark.parametrize("mode", [hl.MODE_ADAPTIVE, hl.MODE_PLAIN, hl.MODE_AUTO])
+def test_cuts_on_32kib_boundaries(mode):
+    """Chunks of about 1.3 MB cut between all 152 CTAs (a range of about 60
+    KB), their bases at offsets across a 128-byte line and a 256-byte span:
+    each cut moves up to a 32 KiB boundary of the chunk's memory, so two
+    cuts often meet on one boundary (a CTA with an empty piece) or pass the
+    chunk's end; every piece's vectors start on a line after a head of up to
+    127 bytes.  Every output and the state equal the oracle's."""
+    sizes = [(40 << 15) + 1, (40 << 15) - 1, (1 << 20) + 100, 40 << 15, 3, (41 << 15) + 127, 1 << 20, 77]
+    shifts = [1, 7, 64, 127, 128, 200, 255, 16]
+    chunks = _phase_chunks(len(sizes), lambda c: sizes[c], 3, SEED + 900 + mode)
+    ref = oracle.StreamOracle(8192, mode=mode)
+    recs = [ref.push(ch) for ch in chunks]
+    offs, pos = [], 0
+    for c in range(len(sizes)):
+        pos += shifts[c]
+        offs.append(pos)
+        pos += sizes[c]
+    buf = np.zeros(pos + 16, np.uint8)
+    for o, ch in zip(offs, chunks):
+        buf[o:o + ch.size] = ch
+    bd = dev(buf)
+    outs = torch.full((len(chunks), 256), -1, dtype=torch.int32, device="cuda")
+    st = hl.Stream(budget=8192, mode=mode, grid=152)
+    st.push_many(np.uint64(bd.data_ptr()) + np.array(offs, dtype=np.uint64), np.array(sizes, dtype=np.uint64),
+                 np.array([outs[j].data_ptr() for j in range(len(chunks))], dtype=np.uint64))
+    got = u32(outs.reshape(-1)).reshape(len(chunks), 256)
+    for j, r in enumerate(recs):
+        assert np.array_equal(got[j], r.hist), j
+    _check_state(st.state(), ref, recs[-1])
+    st.close()
