@@ -521,13 +521,14 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     torch.cuda.synchronize()
     out = {"streams": streams, "payload_pool_bytes": streams * region, "hbm_budget": 32 << 30}
 
-    def run(reqs, at_zero=False, mode=hl.MODE_AUTO):
+    def run(reqs, at_zero=False, mode=hl.MODE_AUTO, base=None):
         count = len(reqs)
+        base = pool.data_ptr() if base is None else base
         outs = torch.empty((count, 256), dtype=torch.int32, device="cuda")
         R = (_abi.Request * count)()
         for i, r in enumerate(reqs):
             R[i].arrival_ns = 0 if at_zero else r.arrival_ns
-            R[i].stream, R[i].d_in, R[i].n = r.stream, pool.data_ptr() + r.offset, r.n
+            R[i].stream, R[i].d_in, R[i].n = r.stream, base + r.offset, r.n
             R[i].d_out, R[i].tag = outs.data_ptr() + i * 1024, i
         torch.cuda.synchronize()
         srv = hl.Server(streams=streams, mode=mode)
@@ -603,6 +604,26 @@ def serving_extras(torch, np, hl, synth, hbm, rates=SERVE_RATES):
     cad["frac_of_hbm"] = round(cad["served_gbs"] / hbm, 4)
     out["capacity_adaptive"] = cad
     del pool
+    # the host-fed variant: the payloads stay in pinned host memory and the
+    # batch kernels read them over the host link (a 1 GiB pool of 256 streams
+    # with 4 MiB regions; a burst of 2000 requests of 4 KiB .. 4 MiB, AUTO
+    # mode), beside the same burst from a device copy of the pool
+    hregion = 4 * MiB
+    hlaws = workloads.serving_streams(streams, hregion, seed=seed)
+    pool = torch.empty(streams * hregion + 16, dtype=torch.uint8, device="cuda")
+    for law in hlaws:
+        synth.device_fill(pool.data_ptr() + law.offset, hregion, law.thr, seed, law.counter0, cs)
+    hpool = torch.empty(pool.numel(), dtype=torch.uint8, pin_memory=True)
+    hpool.copy_(pool)
+    torch.cuda.synchronize()
+    hreqs = workloads.serving_schedule(50000, 2000, streams=streams, region=hregion, size_hi=hregion,
+                                       seed=synth.SEED_BASE + 8)
+    hf = {"pool_bytes": streams * hregion, "requests": len(hreqs)}
+    for name, base in (("pinned_host", hpool.data_ptr()), ("device", pool.data_ptr())):
+        r = run(hreqs, at_zero=True, base=base)
+        hf[name] = {k: r[k] for k in ("served_gbs", "p50_us", "p99_us", "batches", "sums_equal_sizes")}
+    out["capacity_host_fed"] = hf
+    del pool, hpool
     return out
 
 
@@ -646,6 +667,9 @@ def summary_of(ex, value, hbm):
         cap = sv.get("capacity") or {}
         if "auto_kernels_alone_gbs" in cap:
             sm["serving"]["capacity"]["auto_kernels_alone_gbs"] = cap["auto_kernels_alone_gbs"]
+        hf = sv.get("capacity_host_fed") or {}
+        if "pinned_host" in hf:
+            sm["serving"]["burst_host_fed_gbs"] = {k: hf[k].get("served_gbs") for k in ("pinned_host", "device")}
     return sm
 
 

@@ -561,7 +561,9 @@ int hist_ablation(const uint8_t* d_in, size_t n, const hist_pattern* d_pat, uint
  *           timeout_ms; HIST_ETIMEDOUT when it runs out).
  * A request's bytes (d_in, n < 2^32, any alignment) must stay valid and
  * unchanged, and d_out (uint32_t[256], or null) untouched, until its
- * completion has been returned by poll.  The server owns its device state;
+ * completion has been returned by poll.  d_in is device memory, or pinned
+ * host memory mapped into the device's address space: the batch kernels
+ * then read the bytes over the host link (the host-fed variant).  The server owns its device state;
  * one host thread at a time may call it.  Results are exact: a request's
  * histogram and the stream's state do not depend on what else shares its
  * batch.  Any CUDA error is returned by the poll or drain that sees it. */

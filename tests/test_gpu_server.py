@@ -418,3 +418,28 @@ def test_full_size_serving_workload():
         law = laws[s]
         assert np.array_equal(dev[law.offset:law.offset + region].cpu().numpy(),
                               synth.host(region, law.thr, SEED, law.counter0, threads=8))
+
+
+def test_requests_from_pinned_host_memory():
+    """The host-fed variant of serving: the requests' bytes stay in pinned
+    host memory, which the batch kernels read over the host link, beside
+    requests whose bytes are on the device.  Outputs and end states equal
+    the oracle's, as for device-resident requests."""
+    streams, region = 8, 2 << 20
+    pool = Pool(streams, region)
+    hpool = torch.empty(pool.host.size, dtype=torch.uint8, pin_memory=True)
+    hpool.numpy()[:] = pool.host
+    reqs = workloads.serving_schedule(5000, 160, streams=streams, region=region, size_lo=1, size_hi=region,
+                                      seed=SEED + 80, special_sizes=EDGE_SIZES)
+    hists, refs, last = _oracle(pool, reqs)
+    srv = hl.Server(streams=streams, max_batch=16)
+    out = torch.full((len(reqs), 256), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for i, r in enumerate(reqs):
+        base = hpool.data_ptr() if i % 3 else pool.dev.data_ptr()
+        srv.submit_ptr(r.stream, base + r.offset, r.n, out[i].data_ptr(), tag=i)
+    srv.drain(timeout_ms=120000)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), hists)
+    for s in sorted(refs):
+        _check_state(srv.stream_state(s), refs[s], last[s])
+    srv.close()
