@@ -134,6 +134,15 @@ __device__ __forceinline__ void srv_copy_words(void* dst, const void* src, int w
   for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
 }
 
+// The same from a stream's state in global memory, read at L2: the state is
+// written by another batch's epilogue, possibly while an older batch that
+// read it on this SM is still resident, so no line of it is taken from L1.
+__device__ __forceinline__ void srv_copy_state_words(void* dst, const void* src, int words) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldcg(s + i);
+}
+
 // pre[r] = sum over requests before r of (n + kReqCost); pre[count] = total;
 // ctl[r] = request r's stream ctl word (its load overlaps the scan).  The
 // request table sits in the kernel's parameters, read through the constant
@@ -204,7 +213,7 @@ __device__ __noinline__ void srv_epilogue(const SrvCommon& a, uint32_t r, const 
   if (threadIdx.x == 0) {
     st->ctl = srv_ctl(d.flag, shift ? 1u : 0u, cur ^ 1u, shift ? cs.pat.log2k[0] : 0u);
     st->last_kernel = kernel;
-    st->chunks += 1;
+    atomicAdd(&st->chunks, 1ull);  // at L2, like every other read of the state
   }
   // the stream's state is written: its state word releases the stream to
   // the host's admission, so that its next request may run in a batch that
@@ -219,7 +228,7 @@ __device__ __noinline__ void srv_epilogue(const SrvCommon& a, uint32_t r, const 
 // threads call).
 __device__ __noinline__ void srv_layout_general(const SrvStream* st, uint32_t cur, uint32_t* lut, CtaShared& cs) {
   __syncthreads();
-  srv_copy_words(&cs.pat, &st->pat[cur], (int)(sizeof(hist_pattern) / 4));
+  srv_copy_state_words(&cs.pat, &st->pat[cur], (int)(sizeof(hist_pattern) / 4));
   __syncthreads();
   classify_pattern(cs.pat, lut, cs);
 }
