@@ -2,8 +2,9 @@
 // packets batched into one call that returns many histograms).
 //
 // One kernel takes up to kBatchMaxImages images.  Each CTA computes the
-// images' size prefix in shared memory, then counts an equal contiguous range
-// of the concatenated bytes: the part of each image that falls in its range is
+// images' size prefix in shared memory, then counts a contiguous range of the
+// concatenated bytes, an equal share of the batch's cost (the bytes plus a
+// fixed cost per image): the part of each image that falls in its range is
 // counted into the CTA's table and added into that image's output at the
 // image boundary.  The kernel needs no scratch memory, so a batch is a memset
 // of the outputs plus one kernel, and captures into a CUDA graph as such.
@@ -76,20 +77,30 @@ __device__ void size_prefix(const size_t* sizes, uint32_t count, unsigned long l
   __syncthreads();
 }
 
-// A CTA boundary at position x of the concatenated bytes, moved to a 32 KiB
-// boundary of its image's memory (split_point; not past the image's end).
-// Both CTAs of the cut compute it from the same x.
+// The CTAs split the batch by cost: an image costs kImageCost before its
+// bytes (its table reduction and output adds) plus one per byte, so a CTA
+// whose range holds many small images takes fewer bytes.  The 4096-image
+// batch (9.83 GB, one graph launch): 6.51 TB/s with no fixed cost, 6.63 at
+// 32 KiB, 6.64 - 6.69 at 64 KiB, 6.65 at 128 KiB, 6.49 at 256 KiB.
+constexpr unsigned long long kImageCost = 64ull << 10;
+
+// The cut at cost position x, as a position in the concatenated bytes: the
+// start of the image whose fixed cost holds x, else x's byte moved to a 32
+// KiB boundary of its image's memory (split_point; not past the image's
+// end).  Both CTAs of the cut compute it from the same x.
 __device__ unsigned long long batch_cut(const BatchImgArgs& a, const unsigned long long* pre, unsigned long long x) {
-  if (x >= pre[a.count]) return x;
-  uint32_t i = 0, hi = a.count;  // the last image with pre[i] <= x: x lies inside it
+  const unsigned long long W = pre[a.count] + (unsigned long long)a.count * kImageCost;
+  if (x >= W) return pre[a.count];
+  uint32_t i = 0, hi = a.count;  // the last image whose cost starts at or before x
   while (i + 1 < hi) {
     const uint32_t mid = (i + hi) >> 1;
-    if (pre[mid] <= x) i = mid;
+    if (pre[mid] + (unsigned long long)mid * kImageCost <= x) i = mid;
     else hi = mid;
   }
-  const unsigned long long off = x - pre[i], n = pre[i + 1] - pre[i];
-  if (off == 0) return x;
-  const unsigned long long c = split_point(a.ptrs[i], off);
+  const unsigned long long c0 = pre[i] + (unsigned long long)i * kImageCost + kImageCost;
+  const unsigned long long n = pre[i + 1] - pre[i];
+  if (x <= c0) return pre[i];
+  const unsigned long long c = split_point(a.ptrs[i], x - c0);
   return pre[i] + (c < n ? c : n);
 }
 
@@ -103,9 +114,9 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_images_kernel(BatchImgAr
 
   zero_table(table);
   size_prefix(a.sizes, a.count, pre);
-  const unsigned long long total = pre[a.count];
-  const unsigned long long lo0 = batch_cut(a, pre, total * blockIdx.x / gridDim.x);
-  const unsigned long long hi = batch_cut(a, pre, total * (blockIdx.x + 1) / gridDim.x);
+  const unsigned long long W = pre[a.count] + (unsigned long long)a.count * kImageCost;
+  const unsigned long long lo0 = batch_cut(a, pre, W * blockIdx.x / gridDim.x);
+  const unsigned long long hi = batch_cut(a, pre, W * (blockIdx.x + 1) / gridDim.x);
   if (lo0 >= hi) return;
   // first image whose bytes reach past lo0
   uint32_t lo_i = 0, hi_i = a.count;
